@@ -1,0 +1,436 @@
+"""Pins for the CPU oracle: values and properties fixed by the paper or by the
+mathematics, none of them obtained by re-running the oracle's own formulas.
+
+Each test names the passage it pins.  A plausible slip in the oracle (a
+dropped term of Eq. 6, a wrong sign, a transposed twiddle index, a missing
+conjugate, a wrong recursion split) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import literal
+from paper_1402_0532_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _hand():
+    with open(os.path.join(GOLDEN, "hand_cases.json")) as f:
+        return json.load(f)
+
+
+def _c(pairs):
+    return np.array([complex(a, b) for a, b in pairs])
+
+
+def _tw(N):
+    """Twiddle matrix built independently with numpy's fft of unit impulses:
+    column n of the DFT matrix is fft(e_n); axis values are snapped exactly."""
+    F = np.fft.fft(np.eye(N), axis=0)  # F[k, n] = exp(-j 2 pi k n / N)
+    k = np.arange(N)[:, None]
+    n = np.arange(N)[None, :]
+    m = (k * n) % N
+    re = np.where((4 * m == N) | (4 * m == 3 * N), 0.0, F.real)
+    im = np.where((m == 0) | (2 * m == N), 0.0, F.imag)
+    return re + 1j * im
+
+
+def _sig(v):
+    return np.sign(v.real) + 1j * np.sign(v.imag)
+
+
+# --------------------------------------------------------------------------
+# Eq. 1-2: the sign cases, including zeros and negative zero.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("a,b,want", [
+    (2.0, 3.0, 5.0), (-2.0, 3.0, -5.0), (2.0, -3.0, -5.0), (-2.0, -3.0, 5.0),
+    (0.0, 3.0, 0.0), (3.0, 0.0, 0.0), (0.0, 0.0, 0.0), (-0.0, 3.0, 0.0), (3.0, -0.0, 0.0),
+    (-0.0, -7.5, 0.0), (1.5, -0.25, -1.75), (-1e-300, 1e300, -1e300),
+])
+def test_sign_cases_eq2(oracle, a, b, want):
+    got = oracle.otimes(a, b)
+    assert got == want
+    if want == 0.0:
+        assert math.copysign(1.0, got) == 1.0, "the 'otherwise' case returns +0"
+    assert oracle.otimes(b, a) == got  # commutative
+    assert literal.ox(a, b) == want
+
+
+def test_real_identity_bit_exact(oracle):
+    """a (x) b = sgn(b) a + sgn(a) b exactly (both addends are exact in IEEE)."""
+    rng = np.random.default_rng(10)
+    v = rng.standard_normal(4000) * 10.0 ** rng.integers(-3, 4, 4000)
+    v[::17] = 0.0
+    for a, b in zip(v[:2000], v[2000:]):
+        want = np.sign(b) * a + np.sign(a) * b
+        assert oracle.otimes(a, b) == want
+
+
+# --------------------------------------------------------------------------
+# Eq. 3 and Eq. 5: <x (.) x> = 2 ||x||_1.
+# --------------------------------------------------------------------------
+def test_l1_norm_eq5(oracle):
+    rng = np.random.default_rng(11)
+    x = rng.integers(-50, 51, 1000).astype(np.float64)  # integer-valued: sums exact
+    assert oracle.vecprod(x, x) == 2.0 * np.abs(x).sum()
+    y = rng.standard_normal(100000)
+    l1 = math.fsum(np.abs(y))
+    assert abs(oracle.vecprod(y, y) - 2.0 * l1) <= 1e-12 * l1
+
+
+def test_vecprod_eq3_small(oracle):
+    x = np.array([1.0, -2.0, 0.0, 3.0])
+    y = np.array([4.0, 5.0, -6.0, -0.5])
+    # 1(x)4 = 5, -2(x)5 = -7, 0(x)-6 = 0, 3(x)-0.5 = -3.5
+    assert oracle.vecprod(x, y) == 5.0 - 7.0 + 0.0 - 3.5
+
+
+# --------------------------------------------------------------------------
+# Eq. 6: the complex operator.
+# --------------------------------------------------------------------------
+def test_complex_operator_eq6_terms(oracle):
+    # a = 1+2j, b = 3-4j: 1(x)3 - 2(x)(-4) + j(2(x)3 + (-4)(x)1) = 4 + 6 + j(5 - 5)
+    assert oracle.cotimes(1 + 2j, 3 - 4j) == complex(10.0, 0.0)
+    # a = -1+0.5j, b = 2+2j: (-1)(x)2 - 0.5(x)2 + j(0.5(x)2 + 2(x)(-1)) = -3 - 2.5 + j(2.5 - 3)
+    assert oracle.cotimes(-1 + 0.5j, 2 + 2j) == complex(-5.5, -0.5)
+    assert oracle.cotimes(0j, 2 + 2j) == 0j
+
+
+def test_complex_identity_and_symmetries(oracle):
+    rng = np.random.default_rng(12)
+    a = rng.standard_normal(500) + 1j * rng.standard_normal(500)
+    b = rng.standard_normal(500) + 1j * rng.standard_normal(500)
+    a[::7] = a[::7].real  # exact zero imaginary parts
+    b[::11] = 1j * b[::11].imag
+    for u, v in zip(a, b):
+        got = oracle.cotimes(u, v)
+        want = _sig(u) * v + u * _sig(v)  # sigma(a) b + a sigma(b)
+        assert abs(got - want) <= 4e-16 * (abs(u) + abs(v)) * 4
+        assert oracle.cotimes(v, u) == got  # commutative
+        assert oracle.cotimes(-u, v) == -got  # odd
+        assert oracle.cotimes(np.conj(u), np.conj(v)) == np.conj(got)
+        # a (x) conj(a) = 2(|a_r| + |a_i|) + 0j exactly (complex analogue of Eq. 5)
+        assert oracle.cotimes(u, np.conj(u)) == complex(2 * (abs(u.real) + abs(u.imag)), 0.0)
+        assert oracle.cotimes(u, v) == complex(*literal.cox((u.real, u.imag), (v.real, v.imag)))
+
+
+# --------------------------------------------------------------------------
+# Twiddles: W^m with exact axis values.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 6, 7, 8, 12, 64, 1000, 1024, 65536])
+def test_twiddles(oracle, N):
+    ms = np.unique(np.concatenate([np.arange(min(N, 64)), np.arange(N - min(N, 64), N),
+                                   np.array([N // 4, N // 2, 3 * N // 4]) % N]))
+    for m in ms:
+        w = oracle.twiddle(N, int(m))
+        ang = -2.0 * np.pi * m / N
+        assert abs(w - complex(np.cos(ang), np.sin(ang))) < 1e-15 * max(1, m)
+        if (4 * m) % N == 0:
+            # on an axis: both components in {0, +-1}, exactly, zeros positive
+            assert w.real in (0.0, 1.0, -1.0) and w.imag in (0.0, 1.0, -1.0)
+            for v in (w.real, w.imag):
+                assert v != 0 or math.copysign(1.0, v) == 1.0
+        assert w == complex(*literal.twiddle(N, int(m)))
+        if N % 2 == 0:
+            assert oracle.twiddle(N, int(m) + N // 2) == -w or w == 0
+    assert oracle.twiddle(4, 1) == complex(0.0, -1.0)
+    assert oracle.twiddle(8, 2) == complex(0.0, -1.0)
+
+
+def test_twiddle_q14(oracle):
+    assert oracle.twiddle_q14(4, 0) == (16384, 0)
+    assert oracle.twiddle_q14(4, 1) == (0, -16384)
+    assert oracle.twiddle_q14(8, 1) == (11585, -11585)  # round(2^14 / sqrt 2) = 11585
+    assert oracle.twiddle_q14(6, 1) == (8192, -14189)   # 2^14 (1/2, -sqrt(3)/2)
+
+
+# --------------------------------------------------------------------------
+# Eq. 8: NDFT worked examples, closed forms and invariants.
+# --------------------------------------------------------------------------
+def test_hand_cases_ndft_nfft(oracle):
+    h = _hand()
+    for case in h["cases"]:
+        x = _c(case["x"])
+        nd = oracle.ndft(x)
+        nf = oracle.nfft(x)
+        np.testing.assert_array_equal(nd, _c(case["ndft"]))
+        np.testing.assert_array_equal(nf, _c(case["nfft"]))
+        np.testing.assert_array_equal(oracle.nfft_f32(x.astype(np.complex64)), _c(case["nfft"]))
+        assert not np.array_equal(nd, nf)  # Sec. 3: NFFT != NDFT
+    d = h["ndft_of_delta"]
+    x = np.zeros(d["N"], complex)
+    x[0] = 1
+    np.testing.assert_array_equal(oracle.ndft(x), np.full(d["N"], complex(*d["value"])))
+    d = h["nfft_of_delta"]
+    np.testing.assert_array_equal(oracle.nfft(x), np.full(d["N"], complex(*d["value"])))
+
+
+def test_tone_peak_fig1_eq9(oracle):
+    """Eq. 9 / Fig. 1: N = 64, k0 = 7, the NDFT of exp(j 2 pi 7 n / 64) peaks at k = 7.
+    At the peak every term is conj(x) (x) x = 2(|cos| + |sin|), so
+    X[7] = 4 sum_m |cos(2 pi m / 64)| = 8 cot(pi / 64)."""
+    x = scenes.exact_tone(64, 7)
+    X = oracle.ndft(x)
+    mag = np.abs(X)
+    assert int(np.argmax(mag)) == 7
+    assert abs(X[7].real - 8.0 / math.tan(math.pi / 64)) < 1e-12 * 163
+    assert abs(X[7].imag) < 1e-12
+    assert abs(X[7].real - 162.8437409998975) < 1e-9
+    others = np.delete(mag, 7)
+    assert others.max() < 0.2 * mag[7]  # "slightly scattered" but clearly peaked
+
+
+@pytest.mark.parametrize("N,k0", [(8, 3), (12, 5), (16, 1), (32, 9), (128, 45), (1024, 333)])
+def test_tone_closed_form_and_eq9(oracle, N, k0):
+    X = oracle.ndft(scenes.exact_tone(N, k0))
+    assert abs(X[k0] - 8.0 / math.tan(math.pi / N)) < 1e-11 * N
+    assert np.all(np.abs(X) <= np.abs(X[k0]) + 1e-9)  # Eq. 9
+
+
+def test_identity_decomposition(oracle):
+    """X = S x + F sigma(x), S = sigma(F): F sigma(x) is a plain DFT of a ternary
+    sequence (numpy FFT); S x is a dense product with the sign matrix."""
+    rng = np.random.default_rng(13)
+    for N in (3, 5, 8, 12, 16, 48):
+        x = scenes.cn(rng, (4, N))
+        x[:, ::5] = x[:, ::5].real  # some exact zeros in the imaginary part
+        F = _tw(N)
+        S = _sig(F)
+        want = x @ S.T + np.fft.fft(_sig(x), axis=1)
+        got = oracle.ndft(x)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * N)
+
+
+def test_ndft_invariants(oracle):
+    rng = np.random.default_rng(14)
+    N = 40
+    x = scenes.cn(rng, (3, N))
+    X = oracle.ndft(x)
+    S = _sig(_tw(N))
+    # (ii) scaling by c > 0 changes only the S x part
+    c = 3.5
+    np.testing.assert_allclose(oracle.ndft(c * x) - X, (c - 1) * x @ S.T, atol=1e-11)
+    # (iii) odd
+    np.testing.assert_array_equal(oracle.ndft(-x), -X)
+    # (iv) conjugation flips the bin
+    Xc = oracle.ndft(np.conj(x))
+    np.testing.assert_allclose(Xc, np.conj(X[:, (-np.arange(N)) % N]), atol=1e-12)
+    # (v) bin 0: W^0 = 1, so each term is (x_r + sgn x_r) + j (x_i + sgn x_i)
+    want0 = (x.real + np.sign(x.real)).sum(1) + 1j * (x.imag + np.sign(x.imag)).sum(1)
+    np.testing.assert_allclose(X[:, 0], want0, atol=1e-12)
+    # bins p0..p0+nbins-1 with a negative start are the same columns
+    np.testing.assert_array_equal(oracle.ndft(x, p0=-5, nbins=11), X[:, (np.arange(-5, 6)) % N])
+
+
+def test_ndft_brute_force_literal(oracle):
+    rng = np.random.default_rng(15)
+    for N in (1, 2, 3, 4, 5, 7, 8, 16):
+        x = scenes.cn(rng, (N,))
+        if N > 2:
+            x[1] = 0.0
+            x[2] = 1j * x[2].imag
+        got = oracle.ndft(x)
+        want = _c(literal.ndft(literal.as_pairs(x)))
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3: the NFFT.
+# --------------------------------------------------------------------------
+def test_nfft_brute_force_literal(oracle):
+    rng = np.random.default_rng(16)
+    for N in (1, 2, 4, 8, 16):
+        x = scenes.cn(rng, (N,))
+        got = oracle.nfft(x)
+        want = _c(literal.nfft(literal.as_pairs(x)))
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+def test_nfft_sparse_input_structure(oracle):
+    """Sec. 3 recursion on an input that is nonzero only at n = 0 and n = N/2:
+    every odd half is all-zero, W (x) 0 = 0 (Eq. 2), so each stage copies E and
+    the output is the 2-point NFFT of (x[0], x[N/2]) repeated."""
+    N = 16
+    x = np.zeros(N, complex)
+    x[0] = 2 + 1j
+    x[N // 2] = -1 + 3j
+    X = oracle.nfft(x)
+    # 2-point NFFT of (x0, x_{N/2}) at the first stage, then copied by zero odd halves
+    t = oracle.cotimes(1 + 0j, x[N // 2])
+    want = np.array([x[0] + t if k % 2 == 0 else x[0] - t for k in range(N)])
+    np.testing.assert_array_equal(X, want)
+
+
+def test_nfft_tone_fig2(oracle):
+    """Fig. 2: the NFFT of the N = 64, k0 = 7 tone also peaks at k = 7."""
+    X = oracle.nfft(scenes.exact_tone(64, 7))
+    assert int(np.argmax(np.abs(X))) == 7
+    assert not np.allclose(X, oracle.ndft(scenes.exact_tone(64, 7)))
+
+
+def test_nfft_f32_matches_f64_when_exact(oracle):
+    rng = np.random.default_rng(17)
+    for N in (2, 4):
+        x = (rng.integers(-20, 21, N) + 1j * rng.integers(-20, 21, N)).astype(np.complex64)
+        np.testing.assert_array_equal(oracle.nfft_f32(x), oracle.nfft(x.astype(complex)))
+    x = scenes.cn(rng, (8, 256)).astype(np.complex64)
+    a = oracle.nfft_f32(x)
+    b = oracle.nfft(x.astype(complex))
+    assert np.max(np.abs(a - b)) < 1e-4 * np.max(np.abs(b))
+
+
+# --------------------------------------------------------------------------
+# Eq. 12a: lag product and CAF.
+# --------------------------------------------------------------------------
+def test_lagprod_and_caf_literal(oracle):
+    rng = np.random.default_rng(18)
+    N = 12
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    ss[3] = 0
+    for lag in (-2, 0, 1, 5, 11, 13):
+        np.testing.assert_allclose(oracle.lagprod(ss, sr, lag), _c(literal.lagprod(
+            literal.as_pairs(ss), literal.as_pairs(sr), lag)), atol=1e-14)
+    A = oracle.caf(ss, sr, -1, 5, -4, 9)
+    L = _c([v for row in literal.caf(literal.as_pairs(ss), literal.as_pairs(sr), -1, 5, -4, 9)
+            for v in row]).reshape(5, 9)
+    np.testing.assert_allclose(A, L, atol=1e-12)
+    # the CAF row of lag l is the NDFT of the lag product (left-associative reading)
+    for a in range(5):
+        np.testing.assert_array_equal(A[a], oracle.ndft(oracle.lagprod(ss, sr, a - 1), p0=-4, nbins=9))
+    cells = oracle.caf_cells(ss, sr, [0, 2, 3], [3, -4, 4])
+    np.testing.assert_array_equal(cells, [A[1, 7], A[3, 0], A[4, 8]])
+
+
+def test_caf_autoambiguity_invariant(oracle):
+    """s_surv = s_ref with no zero components: z_0 = s (x) conj(s) = 2(|s_r| + |s_i|)
+    and A[0, 0] = sum (z_0 (x) 1) = 2 ||s||_1 + N."""
+    rng = np.random.default_rng(19)
+    N = 300
+    s = scenes.cn(rng, (N,))
+    A = oracle.caf(s, s, 0, 3, 0, 2)
+    l1 = np.sum(np.abs(s.real) + np.abs(s.imag))
+    assert abs(A[0, 0] - (2 * l1 + N)) < 1e-10 * N
+
+
+def test_caf_boundary_zero_and_conjugate(oracle):
+    """Lags beyond the signal give z = 0 and A = 0 exactly; with the conjugate the
+    zero-lag auto-ambiguity is real at bin 0, without it (ablation flag) it is not."""
+    rng = np.random.default_rng(20)
+    N = 32
+    s = scenes.cn(rng, (N,))
+    A = oracle.caf(s, s, N, 2, 0, 4)
+    assert np.all(A == 0)
+    A0 = oracle.caf(s, s, 0, 1, 0, 1)[0, 0]
+    assert A0.imag == 0.0
+    Anc = oracle.caf(s, s, 0, 1, 0, 1, flags=oracle.F_NO_CONJ_REF)[0, 0]
+    assert Anc.imag != 0.0
+    # circular lag: lag N is lag 0
+    np.testing.assert_array_equal(oracle.caf(s, s, N, 1, 0, 4, flags=oracle.F_CIRCULAR_LAG),
+                                  oracle.caf(s, s, 0, 1, 0, 4))
+
+
+def test_caf_z32_gate(oracle):
+    """Forming the lag product in fp32 changes A by no more than fp32 rounding."""
+    sc = scenes.radar_scene(N=2048, nlags=8, nbins=16, seed=21)
+    a = oracle.caf(sc.s_surv, sc.s_ref, 0, 8, -8, 16)
+    b = oracle.caf(sc.s_surv, sc.s_ref, 0, 8, -8, 16, z32=True)
+    assert np.max(np.abs(a - b)) < 1e-4 * np.max(np.abs(a))
+
+
+# --------------------------------------------------------------------------
+# Q1.14 integers.
+# --------------------------------------------------------------------------
+def test_q14_exact_small(oracle):
+    """For N <= 4 every twiddle is exact, so Q1.14 = 2^14 x the real transform."""
+    rng = np.random.default_rng(22)
+    for N in (2, 4):
+        x = (rng.integers(-3000, 3001, N) + 1j * rng.integers(-3000, 3001, N)) / 16384.0
+        q = scenes.quantize_q14(x)
+        Xq, novf = oracle.ndft_q14(q[None])
+        X = oracle.ndft(x) * 16384
+        assert novf == 0
+        np.testing.assert_array_equal(Xq[0, :, 0], X.real.astype(np.int64))
+        np.testing.assert_array_equal(Xq[0, :, 1], X.imag.astype(np.int64))
+
+
+def test_q14_within_twiddle_rounding(oracle):
+    """Larger N: each real (x) moves by at most the Q1.14 twiddle rounding (2^-15)."""
+    rng = np.random.default_rng(23)
+    N = 96
+    x = scenes.cn(rng, (2, N)) * 0.5
+    q = scenes.quantize_q14(x)
+    xd = (q[..., 0] + 1j * q[..., 1]) / 16384.0
+    Xq, novf = oracle.ndft_q14(q)
+    X = oracle.ndft(xd)
+    err = np.abs(Xq[..., 0] / 16384.0 - X.real) + np.abs(Xq[..., 1] / 16384.0 - X.imag)
+    assert novf == 0
+    assert err.max() <= 4 * N * 2.0 ** -15
+
+
+def test_q14_wraps_modulo_2_32(oracle):
+    """Saturated inputs overflow int32; the result is the exact sum modulo 2^32,
+    checked against Python big integers cell by cell."""
+    N = 16384
+    ss = np.full((N, 2), 32767, np.int16)
+    sr = np.full((N, 2), -32768, np.int16)
+    A, novf = oracle.caf_q14(ss, sr, 0, 2, 0, 2)
+    assert novf > 0
+    tw = {p: [oracle.twiddle_q14(N, i * p) for i in range(N)] for p in (0, 1)}
+
+    def exact(l, p):
+        re = im = 0
+        for i in range(N):
+            j = i - l
+            c = (int(sr[j, 0]), -int(sr[j, 1])) if 0 <= j < N else (0, 0)
+            z = literal.cox((int(ss[i, 0]), int(ss[i, 1])), c)
+            t = literal.cox(z, tw[p][i])
+            re += t[0]
+            im += t[1]
+        return re, im
+
+    for l in (0, 1):
+        for p in (0, 1):
+            re, im = exact(l, p)
+            wrap = lambda v: ((v + 2 ** 31) % 2 ** 32) - 2 ** 31
+            assert (int(A[l, p, 0]), int(A[l, p, 1])) == (wrap(re), wrap(im))
+    assert abs(exact(0, 0)[0]) >= 2 ** 31  # it really overflowed
+
+
+# --------------------------------------------------------------------------
+# Adjoint: central finite differences of the FP64 forward.
+# --------------------------------------------------------------------------
+def test_adjoint_finite_differences(oracle):
+    rng = np.random.default_rng(24)
+    N, lag0, nlags, p0, nbins = 48, 0, 6, -4, 8
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    A = oracle.caf(ss, sr, lag0, nlags, p0, nbins)
+    mask = np.zeros(A.shape, bool)
+    mask[1:5, 2:7] = True
+    L, gA = oracle.masked_abs_loss_grad(A, mask)
+    ds = oracle.caf_adjoint(ss, sr, lag0, nlags, p0, nbins, gA)
+    # step below the distance of every touched quantity to a zero crossing
+    zs = np.stack([oracle.lagprod(ss, sr, l) for l in range(lag0, lag0 + nlags)])
+    checked = 0
+    for i in range(N):
+        margin = min(abs(ss[i].real), abs(ss[i].imag), np.min(np.abs(zs[:, i].real[zs[:, i] != 0])),
+                     np.min(np.abs(zs[:, i].imag[zs[:, i] != 0])))
+        h = min(0.25 * margin, 1e-4)
+        if h < 1e-7:
+            continue
+        for comp, unit in ((0, 1.0), (1, 1j)):
+            sp, sm = ss.copy(), ss.copy()
+            sp[i] += h * unit
+            sm[i] -= h * unit
+            Lp = np.sum(np.abs(oracle.caf(sp, sr, lag0, nlags, p0, nbins))[mask])
+            Lm = np.sum(np.abs(oracle.caf(sm, sr, lag0, nlags, p0, nbins))[mask])
+            fd = (Lp - Lm) / (2 * h)
+            an = ds[i].real if comp == 0 else ds[i].imag
+            assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (i, comp, fd, an)
+            checked += 1
+    assert checked >= 40
