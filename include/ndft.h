@@ -1,0 +1,193 @@
+/*
+ * ndft.h -- C ABI of the GB300 (sm_103a) library for the multiplication-free
+ * nonlinear DFT of Bozkurt et al., arXiv 1402.0532.
+ *
+ * The operator (Eq. 1-2):  a (x) b = sgn(a b) (|a| + |b|), 0 if a or b is 0.
+ * Complex extension (Eq. 6): a (x) b = a_r(x)b_r - a_i(x)b_i + j(a_i(x)b_r + b_i(x)a_r).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every data pointer is a DEVICE pointer (cudaMalloc'd or equivalent) owned
+ *    by the caller, unless a parameter says "host".  The library never frees,
+ *    keeps or reallocates caller memory.
+ *  - complex64 data is interleaved float2 {re, im}, the layout of
+ *    torch.complex64 / std::complex<float>.  Q1.14 data is interleaved int16
+ *    pairs (value = q / 2^14) in, interleaved int32 pairs out.
+ *  - Arrays are dense and row-major as stated per call; base pointers must be
+ *    16-byte aligned, otherwise NDFT_E_INVALID.
+ *  - Argument errors are returned synchronously and launch nothing.  CUDA
+ *    launch errors are returned as NDFT_E_CUDA.  Errors detected inside a
+ *    kernel (a bounded wait that ran out, an internal check) are recorded in
+ *    the plan's device error word and returned by ndft_query_error().
+ *  - Exec calls allocate nothing and never synchronise the stream; all
+ *    memory they need is allocated by the plan.  One plan may serve one stream
+ *    at a time.
+ *  - Twiddles W^m = exp(-j 2 pi m / N) (defined under Eq. 8) are computed once
+ *    per plan in fp64 from the angle reduced to a quadrant in integer
+ *    arithmetic: values on the axes (m = 0, N/4, N/2, 3N/4) are exactly
+ *    0 and +-1, and their signs are exact.
+ */
+#ifndef NDFT_H_
+#define NDFT_H_
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NDFT_OK = 0,
+    NDFT_E_INVALID = 1,      /* bad argument: null/misaligned pointer, size, combination */
+    NDFT_E_UNSUPPORTED = 2,  /* valid request this build does not provide */
+    NDFT_E_CUDA = 3,         /* a CUDA runtime call or launch failed */
+    NDFT_E_NOMEM = 4,        /* device allocation at plan time failed */
+    NDFT_E_TIMEOUT = 5,      /* a bounded device-side wait ran out (see ndft_query_error) */
+    NDFT_E_OVERFLOW = 6      /* reserved: fixed-point range report */
+} ndft_status;
+
+typedef enum {
+    NDFT_FORM_DIRECT = 0,       /* (x) evaluated term by term on the CUDA cores */
+    NDFT_FORM_TERNARY_GEMM = 1  /* a (x) b = sgn(b) a + sgn(a) b as two dense contractions on tcgen05 */
+} ndft_form;
+
+typedef enum {
+    NDFT_PREC_FP32 = 0,    /* complex64 in/out, fp32 arithmetic (DIRECT form, NFFT)          */
+    NDFT_PREC_BF16X2 = 1,  /* complex64 in/out; bf16 hi+lo operands, exact ternary sign
+                              matrices, fp32 accumulation (TERNARY_GEMM form)                */
+    NDFT_PREC_Q14 = 2      /* int16 pairs (Q1.14) in, int32 pairs out; integer (x), sums
+                              modulo 2^32 (DIRECT form)                                      */
+} ndft_prec;
+
+/* CAF options (Eq. 12a): the default conjugates s_ref and treats s_ref[j] as 0
+ * outside [0, N) (linear correlation). */
+#define NDFT_F_NO_CONJ_REF 0x1u  /* ablation: use s_ref[i-l] without the conjugate */
+#define NDFT_F_CIRCULAR_LAG 0x2u /* index s_ref modulo N instead of zero padding    */
+
+/* Plan descriptor.  Output bins are k = p0 .. p0 + nbins - 1 (signed, taken
+ * modulo N); nbins = 0 means N bins starting at p0. */
+typedef struct {
+    int32_t n;          /* transform / CPI length N >= 1 (NFFT: power of two, 2..2^20) */
+    int32_t p0;         /* first output bin */
+    int32_t nbins;      /* number of output bins, 0 -> N */
+    int32_t max_lags;   /* largest nlags a caf_exec / caf_backward call will pass (0: no CAF) */
+    int64_t max_batch;  /* largest batch an ndft_exec / nfft_exec call will pass */
+    int32_t form;       /* ndft_form */
+    int32_t prec;       /* ndft_prec */
+    uint32_t flags;     /* NDFT_F_* */
+    int32_t reserved[3];/* must be 0 */
+} ndft_desc;
+
+typedef struct ndft_plan_s *ndft_plan_t;
+
+/* One coherent processing interval (CPI) of a batched CAF: its s_surv / s_ref
+ * start at element offsets off_surv / off_ref (complex elements, or int16
+ * pairs for Q1.14) of the base pointers passed to caf_exec_batched, and its
+ * surface A[nlags][nbins] at element offset off_out of the output base. */
+typedef struct {
+    int64_t off_surv, off_ref, off_out;
+    int32_t n, lag0, nlags, p0, nbins;
+    int32_t reserved;
+} ndft_cpi;
+
+/* ---- plan lifecycle ------------------------------------------------------ */
+
+/* Creates a plan: validates d, allocates the twiddle tables (fp32, bf16 hi/lo
+ * quarter table, Q1.14), the workspace for max_batch / max_lags and the device
+ * error word, and builds the tables on `stream` (fp64 on the GPU).  The plan
+ * is ready once `stream` has reached this point.  Errors: NDFT_E_INVALID,
+ * NDFT_E_UNSUPPORTED (form/prec pair not provided), NDFT_E_NOMEM, NDFT_E_CUDA. */
+ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream);
+
+/* Creates a plan for caf_exec_batched over the `ncpi` CPIs listed in the HOST
+ * array `cpis` (copied; the caller may free it on return).  form/prec/flags
+ * as in ndft_desc.  The work list, per-CPI tables and workspace are built
+ * here, once.  Each CPI: n >= 1, nlags >= 1, 1 <= nbins. */
+ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t ncpi, int32_t form,
+                              int32_t prec, uint32_t flags, cudaStream_t stream);
+
+/* Releases everything the plan owns (synchronises the device first). */
+ndft_status ndft_plan_destroy(ndft_plan_t plan);
+
+/* ---- transforms ------------------------------------------------------------ */
+
+/* NDFT, Eq. 8 (Sec. 2): X[b][k] = sum_n W^(((p0+k) n) mod N) (x) x[b][n].
+ * x: [batch][N], X: [batch][nbins]; complex64 (FP32, BF16X2) or Q1.14.
+ * 0 <= batch <= max_batch. */
+ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream);
+
+/* NFFT, Sec. 3: radix-2 decimation in time with every twiddle product
+ * replaced by (x) (also W^0 = 1); the 1-point NFFT is the identity; output
+ * in natural order.  Per butterfly: t = W (x) O[k], X[k] = E[k] + t,
+ * X[k + N/2] = E[k] - t, evaluated in fp32 in exactly that order, so results
+ * are reproducible bit for bit.  Requires N a power of two, nbins = N, p0 = 0,
+ * prec FP32.  x, X: [batch][N] complex64; X may equal x (in place). */
+ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream);
+
+/* Nonlinear cross-ambiguity surface, Eq. 12a (Sec. 4), read left to right:
+ *   A[a][k] = sum_i ( s_surv[i] (x) conj(s_ref[i - l]) ) (x) W^((i p) mod N),
+ *   l = lag0 + a (0 <= a < nlags), p = p0 + k (0 <= k < nbins),
+ * s_ref[j] = 0 outside [0, N) unless NDFT_F_CIRCULAR_LAG.
+ * s_surv, s_ref: [N]; A: [nlags][nbins]; 1 <= nlags <= max_lags. */
+ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
+                     int32_t nlags, void *A, cudaStream_t stream);
+
+/* Batched CAF over the plan's CPI list, all CPIs in one persistent launch
+ * sequence: CPI c reads surv_base + off_surv, ref_base + off_ref and writes
+ * out_base + off_out.  Offsets are in elements of the plan's precision. */
+ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void *ref_base,
+                             void *out_base, cudaStream_t stream);
+
+/* Adjoint of caf_exec with respect to s_surv (complex64 plans).  Given
+ * dA = dL/dRe A + j dL/dIm A ([nlags][nbins]) returns
+ *   ds[i] = dL/dRe s_surv[i] + j dL/dIm s_surv[i]
+ *         = sum_l conj(sigma(c_l[i])) sum_p conj(S[p][i]) dA[l][p],
+ * with c_l[i] = conj(s_ref[i-l]), S[p][i] = sigma(W^(i p)), sigma(v) =
+ * sgn(v_r) + j sgn(v_i): the derivative d(a (x) b)/da = sgn(b) of Eq. 1-2
+ * (valid where no operand is 0), chained through Eq. 6 and Eq. 12a.
+ * ds: [N].  s_surv is not read (the derivative does not depend on it a.e.). */
+ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
+                         int32_t nlags, const void *dA, void *ds, cudaStream_t stream);
+
+/* ---- epilogue helpers -------------------------------------------------------- */
+
+/* Per row of X ([rows][cols] complex64): the index of the largest |X|^2
+ * (re*re + im*im rounded in fp32), lowest index on ties -> idx[rows] (int64),
+ * and that |X|^2 -> val[rows] (float, may be NULL).  The peak reading of
+ * Eq. 9 / Fig. 1.  Needs no plan. */
+ndft_status ndft_argmax(const void *X, int64_t rows, int64_t cols, int64_t *idx, float *val,
+                        cudaStream_t stream);
+
+/* ---- diagnostics ------------------------------------------------------------- */
+
+/* Synchronises `stream`, returns the plan's device error word as a status
+ * (NDFT_OK if none) and clears it. */
+ndft_status ndft_query_error(ndft_plan_t plan, cudaStream_t stream);
+
+/* Copies the plan's twiddle table to caller memory: which = 0 -> fp32 [N]
+ * float2, 1 -> Q1.14 [N] int16 pairs, 2 -> bf16 hi/lo quarter table
+ * [N/g + 1] uint32 (hi in the low half), g = gcd(4, N).  Single-CPI plans. */
+ndft_status ndft_get_twiddles(ndft_plan_t plan, int32_t which, void *dst, cudaStream_t stream);
+
+/* Bytes of device memory the plan holds (tables + workspace). */
+ndft_status ndft_plan_bytes(ndft_plan_t plan, int64_t *bytes);
+
+/* Kernel-launch count of the plan's last exec call (for accounting). */
+ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
+
+/* Tile / split choice for the plan's kernels: key 0 = split count along the
+ * sample axis (0 = automatic), key 1 = ternary-GEMM columns per tile (128 or
+ * 256; 0 = automatic).  Used by the autotuner; affects speed, not results
+ * beyond fp32 summation order. */
+ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
+
+const char *ndft_status_string(ndft_status s);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t ndft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDFT_H_ */

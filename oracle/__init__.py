@@ -69,6 +69,7 @@ def _load():
             lib.oracle_twiddle.argtypes = [i64, i64, P]
             lib.oracle_twiddle_q14.argtypes = [i64, i64, P]
             lib.oracle_twiddle_table_f32.argtypes = [i64, P]
+            lib.oracle_twiddle_table_q14.argtypes = [i64, P]
             lib.oracle_ndft.argtypes = [P, i64, i64, i64, i64, P]
             lib.oracle_nfft.argtypes = [P, i64, i64, P]
             lib.oracle_nfft_f32.argtypes = [P, i64, i64, P]
@@ -145,6 +146,12 @@ def twiddle_q14(N: int, m: int) -> tuple[int, int]:
 def twiddle_table_f32(N: int) -> np.ndarray:
     out = np.zeros(N, np.complex64)
     _load().oracle_twiddle_table_f32(N, _ptr(out))
+    return out
+
+
+def twiddle_table_q14(N: int) -> np.ndarray:
+    out = np.zeros((N, 2), np.int16)
+    _load().oracle_twiddle_table_q14(N, _ptr(out))
     return out
 
 

@@ -145,6 +145,16 @@ void oracle_twiddle_q14(int64_t N, int64_t m, int32_t *out) {
     out[1] = (int32_t)nearbyint(w[1] * 16384.0);
 }
 
+/* Q1.14 copy of the whole table (int16 pairs). */
+void oracle_twiddle_table_q14(int64_t N, int16_t *out) {
+    for (int64_t m = 0; m < N; ++m) {
+        int32_t w[2];
+        oracle_twiddle_q14(N, m, w);
+        out[2 * m] = (int16_t)w[0];
+        out[2 * m + 1] = (int16_t)w[1];
+    }
+}
+
 static double *twiddle_table64(int64_t N) {
     double *t = (double *)malloc(sizeof(double) * 2 * (size_t)N);
     if (!t) return NULL;

@@ -1,0 +1,91 @@
+"""ctypes declarations of the C ABI in include/ndft.h (argument marshalling only).
+
+Every function of the header is declared here under the same name.  Loading
+fails loudly if libndft.so is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libndft.so")
+
+OK, E_INVALID, E_UNSUPPORTED, E_CUDA, E_NOMEM, E_TIMEOUT, E_OVERFLOW = range(7)
+FORM_DIRECT, FORM_TERNARY_GEMM = 0, 1
+PREC_FP32, PREC_BF16X2, PREC_Q14 = 0, 1, 2
+F_NO_CONJ_REF, F_CIRCULAR_LAG = 0x1, 0x2
+
+# every symbol include/ndft.h declares
+EXPORTS = ("ndft_plan", "ndft_plan_batched", "ndft_plan_destroy", "ndft_exec", "nfft_exec", "caf_exec",
+           "caf_exec_batched", "caf_backward", "ndft_argmax", "ndft_query_error", "ndft_get_twiddles",
+           "ndft_plan_bytes", "ndft_last_launches", "ndft_set_tuning", "ndft_status_string", "ndft_version")
+
+
+class NdftDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("p0", ctypes.c_int32), ("nbins", ctypes.c_int32),
+                ("max_lags", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("form", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class NdftCpi(ctypes.Structure):
+    _fields_ = [("off_surv", ctypes.c_int64), ("off_ref", ctypes.c_int64), ("off_out", ctypes.c_int64),
+                ("n", ctypes.c_int32), ("lag0", ctypes.c_int32), ("nlags", ctypes.c_int32),
+                ("p0", ctypes.c_int32), ("nbins", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class NdftError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libndft.so (built by ``paper_1402_0532_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_1402_0532_gb300.build.build() "
+                          "(nvcc, sm_103a) before using the library; there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "ndft_plan": (i32, [ctypes.POINTER(P), ctypes.POINTER(NdftDesc), P]),
+        "ndft_plan_batched": (i32, [ctypes.POINTER(P), ctypes.POINTER(NdftCpi), i32, i32, i32, u32, P]),
+        "ndft_plan_destroy": (i32, [P]),
+        "ndft_exec": (i32, [P, P, P, i64, P]),
+        "nfft_exec": (i32, [P, P, P, i64, P]),
+        "caf_exec": (i32, [P, P, P, i32, i32, P, P]),
+        "caf_exec_batched": (i32, [P, P, P, P, P]),
+        "caf_backward": (i32, [P, P, P, i32, i32, P, P, P]),
+        "ndft_argmax": (i32, [P, i64, i64, P, P, P]),
+        "ndft_query_error": (i32, [P, P]),
+        "ndft_get_twiddles": (i32, [P, i32, P, P]),
+        "ndft_plan_bytes": (i32, [P, ctypes.POINTER(i64)]),
+        "ndft_last_launches": (i32, [P, ctypes.POINTER(i32)]),
+        "ndft_set_tuning": (i32, [P, i32, i32]),
+        "ndft_status_string": (ctypes.c_char_p, [i32]),
+        "ndft_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().ndft_status_string(int(status)).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def check(status: int, what: str):
+    if status != OK:
+        raise NdftError(status, what)

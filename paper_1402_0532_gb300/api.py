@@ -1,0 +1,240 @@
+"""Thin PyTorch binding over the C ABI (include/ndft.h).
+
+PyTorch provides device memory and the current stream; every step of the
+transforms runs in the library's CUDA kernels.  Each method marshals tensor
+pointers into the C call of the same name and raises ``NdftError`` on a
+non-OK status.  Inputs must be CUDA tensors: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+_FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM}
+_PRECS = {"fp32": L.PREC_FP32, "bf16x2": L.PREC_BF16X2, "q14": L.PREC_Q14}
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, what: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A single-transform plan: ``ndft``, ``nfft``, ``caf``, ``caf_backward``.
+
+    form: "direct" (CUDA cores) or "ternary" (tcgen05 tensor cores);
+    prec: "fp32" / "q14" (direct) or "bf16x2" (ternary).
+    Bins are p0 .. p0 + nbins - 1 (nbins = 0 -> N)."""
+
+    def __init__(self, n: int, *, p0: int = 0, nbins: int = 0, max_lags: int = 0, max_batch: int = 0,
+                 form: str = "direct", prec: str = "fp32", flags: int = 0, device=None):
+        self.lib = L.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.n, self.p0 = int(n), int(p0)
+        self.nbins = int(nbins) if nbins else int(n)
+        self.max_lags, self.max_batch = int(max_lags), int(max_batch)
+        self.form, self.prec, self.flags = form, prec, int(flags)
+        d = L.NdftDesc(n=self.n, p0=self.p0, nbins=int(nbins), max_lags=self.max_lags,
+                       max_batch=self.max_batch, form=_FORMS[form], prec=_PRECS[prec], flags=self.flags)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.ndft_plan(ctypes.byref(h), ctypes.byref(d), _stream(self.device)), "ndft_plan")
+        self.handle = h
+
+    # -- helpers -----------------------------------------------------------------
+    @property
+    def _in_dtype(self):
+        return torch.int16 if self.prec == "q14" else torch.complex64
+
+    @property
+    def _out_dtype(self):
+        return torch.int32 if self.prec == "q14" else torch.complex64
+
+    def _row_shape(self, n):
+        return (n, 2) if self.prec == "q14" else (n,)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.check(self.lib.ndft_plan_destroy(self.handle), "ndft_plan_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_launches(self) -> int:
+        c = ctypes.c_int32()
+        L.check(self.lib.ndft_last_launches(self.handle, ctypes.byref(c)), "ndft_last_launches")
+        return c.value
+
+    def nbytes(self) -> int:
+        b = ctypes.c_int64()
+        L.check(self.lib.ndft_plan_bytes(self.handle, ctypes.byref(b)), "ndft_plan_bytes")
+        return b.value
+
+    def set_tuning(self, key: int, value: int):
+        L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
+
+    def query_error(self):
+        L.check(self.lib.ndft_query_error(self.handle, _stream(self.device)), "ndft_query_error")
+
+    def twiddles(self, which: int = 0) -> torch.Tensor:
+        """The plan's table: 0 fp32 [N] complex64, 1 Q1.14 [N, 2] int16, 2 bf16 hi/lo quarter table (int32)."""
+        n = self.n
+        g = 4 if n % 4 == 0 else (2 if n % 2 == 0 else 1)
+        if which == 0:
+            out = torch.empty(n, dtype=torch.complex64, device=self.device)
+        elif which == 1:
+            out = torch.empty(n, 2, dtype=torch.int16, device=self.device)
+        else:
+            out = torch.empty(n // g + 1, dtype=torch.int32, device=self.device)
+        L.check(self.lib.ndft_get_twiddles(self.handle, int(which), _ptr(out), _stream(self.device)),
+                "ndft_get_twiddles")
+        return out
+
+    # -- transforms ----------------------------------------------------------------
+    def ndft(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Eq. 8 over the rows of x ([batch, N] complex64, or [batch, N, 2] int16 for q14)."""
+        _need(x, self._in_dtype, "x")
+        batch = x.shape[0]
+        if out is None:
+            out = torch.empty((batch,) + self._row_shape(self.nbins), dtype=self._out_dtype, device=x.device)
+        _need(out, self._out_dtype, "out")
+        L.check(self.lib.ndft_exec(self.handle, _ptr(x), _ptr(out), batch, _stream(x.device)), "ndft_exec")
+        return out
+
+    def nfft(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Sec. 3 NFFT over the rows of x ([batch, N] complex64); out may be x."""
+        _need(x, torch.complex64, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        _need(out, torch.complex64, "out")
+        L.check(self.lib.nfft_exec(self.handle, _ptr(x), _ptr(out), x.shape[0], _stream(x.device)), "nfft_exec")
+        return out
+
+    def caf(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int,
+            out: torch.Tensor | None = None) -> torch.Tensor:
+        """Eq. 12a surface [nlags, nbins] (complex64, or [nlags, nbins, 2] int32 for q14)."""
+        _need(s_surv, self._in_dtype, "s_surv")
+        _need(s_ref, self._in_dtype, "s_ref")
+        if out is None:
+            out = torch.empty((nlags,) + self._row_shape(self.nbins), dtype=self._out_dtype, device=s_surv.device)
+        _need(out, self._out_dtype, "out")
+        L.check(self.lib.caf_exec(self.handle, _ptr(s_surv), _ptr(s_ref), int(lag0), int(nlags), _ptr(out),
+                                  _stream(s_surv.device)), "caf_exec")
+        return out
+
+    def caf_backward(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int, dA: torch.Tensor,
+                     out: torch.Tensor | None = None) -> torch.Tensor:
+        """dL/ds_surv (dRe + j dIm) given dA = dL/dRe A + j dL/dIm A ([nlags, nbins] complex64)."""
+        _need(s_ref, torch.complex64, "s_ref")
+        _need(dA, torch.complex64, "dA")
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.complex64, device=s_ref.device)
+        _need(out, torch.complex64, "out")
+        L.check(self.lib.caf_backward(self.handle, _ptr(s_surv), _ptr(s_ref), int(lag0), int(nlags), _ptr(dA),
+                                      _ptr(out), _stream(s_ref.device)), "caf_backward")
+        return out
+
+
+class BatchedPlan:
+    """caf_exec_batched over a fixed list of CPIs (one persistent launch sequence).
+
+    cpis: list of dicts with keys off_surv, off_ref, off_out, n, lag0, nlags, p0, nbins."""
+
+    def __init__(self, cpis, *, form: str = "direct", prec: str = "fp32", flags: int = 0):
+        self.lib = L.load()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        arr = (L.NdftCpi * len(cpis))()
+        for i, c in enumerate(cpis):
+            arr[i] = L.NdftCpi(off_surv=c["off_surv"], off_ref=c["off_ref"], off_out=c["off_out"], n=c["n"],
+                               lag0=c["lag0"], nlags=c["nlags"], p0=c["p0"], nbins=c["nbins"])
+        self.prec = prec
+        h = ctypes.c_void_p()
+        L.check(self.lib.ndft_plan_batched(ctypes.byref(h), arr, len(cpis), _FORMS[form], _PRECS[prec], int(flags),
+                                           _stream(self.device)), "ndft_plan_batched")
+        self.handle = h
+
+    def __call__(self, surv: torch.Tensor, ref: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        dt_in = torch.int16 if self.prec == "q14" else torch.complex64
+        dt_out = torch.int32 if self.prec == "q14" else torch.complex64
+        _need(surv, dt_in, "surv")
+        _need(ref, dt_in, "ref")
+        _need(out, dt_out, "out")
+        L.check(self.lib.caf_exec_batched(self.handle, _ptr(surv), _ptr(ref), _ptr(out), _stream(surv.device)),
+                "caf_exec_batched")
+        return out
+
+    def last_launches(self) -> int:
+        c = ctypes.c_int32()
+        L.check(self.lib.ndft_last_launches(self.handle, ctypes.byref(c)), "ndft_last_launches")
+        return c.value
+
+    def set_tuning(self, key: int, value: int):
+        L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
+
+    def query_error(self):
+        L.check(self.lib.ndft_query_error(self.handle, _stream(self.device)), "ndft_query_error")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.check(self.lib.ndft_plan_destroy(self.handle), "ndft_plan_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def argmax(X: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    """Per-row index of the largest |X|^2 (lowest index on ties) and that value; X [rows, cols] complex64."""
+    _need(X, torch.complex64, "X")
+    X2 = X.reshape(X.shape[0], -1) if X.dim() > 1 else X.reshape(1, -1)
+    rows, cols = X2.shape
+    idx = torch.empty(rows, dtype=torch.int64, device=X.device)
+    val = torch.empty(rows, dtype=torch.float32, device=X.device)
+    L.check(L.load().ndft_argmax(_ptr(X2), rows, cols, _ptr(idx), _ptr(val), _stream(X.device)), "ndft_argmax")
+    return idx, val
+
+
+class CafFunction(torch.autograd.Function):
+    """A = CAF(s_surv; s_ref) (Eq. 12a) with the hand-written adjoint as its backward.
+
+    Gradient convention is PyTorch's for complex inputs: s_surv.grad = dL/dRe + j dL/dIm."""
+
+    @staticmethod
+    def forward(ctx, s_surv, s_ref, plan: Plan, lag0: int, nlags: int):
+        A = plan.caf(s_surv.detach().contiguous(), s_ref.detach().contiguous(), lag0, nlags)
+        ctx.save_for_backward(s_surv, s_ref)
+        ctx.plan, ctx.lag0, ctx.nlags = plan, lag0, nlags
+        return A
+
+    @staticmethod
+    def backward(ctx, dA):
+        s_surv, s_ref = ctx.saved_tensors
+        ds = ctx.plan.caf_backward(s_surv.detach().contiguous(), s_ref.detach().contiguous(), ctx.lag0, ctx.nlags,
+                                   dA.contiguous())
+        return ds, None, None, None, None
+
+
+def caf_autograd(s_surv: torch.Tensor, s_ref: torch.Tensor, plan: Plan, lag0: int, nlags: int) -> torch.Tensor:
+    return CafFunction.apply(s_surv, s_ref, plan, lag0, nlags)

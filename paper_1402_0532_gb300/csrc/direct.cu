@@ -1,0 +1,393 @@
+// direct.cu -- the plain form: (x) evaluated term by term on the CUDA cores.
+//
+// Computes out[col][k] = sum_n W^((p n) mod N) (x) v[col][n], p = p0 + k, for
+//   * the NDFT of Eq. 8: v = x (one column per input vector), and
+//   * the nonlinear ambiguity surface of Eq. 12a: v = z_l with
+//     z_l[n] = s_surv[n] (x) conj(s_ref[n - l]), one column per lag l.
+//
+// Each block owns 64 bins x 64 columns and walks the sample axis in chunks of
+// 16.  Per chunk it stages, in shared memory, the 16 x 64 twiddles of its bins
+// (gathered from the plan's fp32 table at (p n) mod N, the index advanced
+// incrementally) and the 16 x 64 data values, both already split into the
+// pieces (x) needs: magnitude, sign word and nonzero mask.  Each thread then
+// accumulates a 4 x 4 register tile; one real (x) is an add of magnitudes, a
+// three-way XOR of the sign words and an AND with the two nonzero masks
+// (Eq. 1-2 with the zero case explicit), one complex (x) four of those (Eq. 6).
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace ndft {
+
+namespace {
+
+constexpr int BP = 64;   // bins per block
+constexpr int BC = 64;   // columns per block
+constexpr int KC = 16;   // samples per chunk
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint32_t nzmask_f(float v) { return (__float_as_uint(v) << 1) ? 0xffffffffu : 0u; }
+
+// ---- precision traits ---------------------------------------------------------
+struct PrecF32 {
+    using In = float2;
+    using Tw = float2;
+    using V = float2;
+    using Mag = float2;
+    using Acc = float2;
+    __device__ static V load(const In *p, int64_t i) { return p[i]; }
+    __device__ static V zero() { return make_float2(0.f, 0.f); }
+    __device__ static V conj_(V v) { return make_float2(v.x, -v.y); }
+    __device__ static V cox(V a, V b) { return cox_f32(a, b); }
+    __device__ static void ready(V v, Mag &m, uint4 &s) {
+        m = make_float2(fabsf(v.x), fabsf(v.y));
+        s = make_uint4(__float_as_uint(v.x) & kSignBit, __float_as_uint(v.y) & kSignBit, nzmask_f(v.x),
+                       nzmask_f(v.y));
+    }
+    __device__ static Acc acc0() { return make_float2(0.f, 0.f); }
+    // acc += w (x) v, Eq. 6: re += w_r(x)v_r - w_i(x)v_i, im += w_i(x)v_r + v_i(x)w_r
+    __device__ static void mac(Acc &acc, const Mag &wm, const uint4 &ws, const Mag &vm, const uint4 &vs) {
+        const float t1 = ox_ready(wm.x, ws.x, ws.z, vm.x, vs.x, vs.z);
+        const float t2 = ox_ready(wm.y, ws.y, ws.w, vm.y, vs.y, vs.w);
+        const float t3 = ox_ready(wm.y, ws.y, ws.w, vm.x, vs.x, vs.z);
+        const float t4 = ox_ready(vm.y, vs.y, vs.w, wm.x, ws.x, ws.z);
+        acc.x = __fsub_rn(__fadd_rn(acc.x, t1), t2);
+        acc.y = __fadd_rn(__fadd_rn(acc.y, t3), t4);
+    }
+    __device__ static float2 out(const Acc &a) { return a; }
+    using Out = float2;
+};
+
+struct PrecQ14 {
+    using In = short2;
+    using Tw = short2;
+    using V = int2;
+    using Mag = int2;
+    using Acc = uint2;  // two's complement wrap
+    __device__ static V load(const In *p, int64_t i) {
+        const short2 v = p[i];
+        return make_int2(v.x, v.y);
+    }
+    __device__ static V zero() { return make_int2(0, 0); }
+    __device__ static V conj_(V v) { return make_int2(v.x, -v.y); }
+    __device__ static V cox(V a, V b) { return cox_i32(a, b); }
+    __device__ static void ready(V v, Mag &m, uint4 &s) {
+        m = make_int2(abs(v.x), abs(v.y));
+        s = make_uint4(v.x < 0 ? 0xffffffffu : 0u, v.y < 0 ? 0xffffffffu : 0u, v.x ? 0xffffffffu : 0u,
+                       v.y ? 0xffffffffu : 0u);
+    }
+    __device__ static Acc acc0() { return make_uint2(0u, 0u); }
+    __device__ static uint32_t ox(int am, uint32_t as, uint32_t az, int bm, uint32_t bs, uint32_t bz) {
+        const uint32_t m = (uint32_t)(am + bm);
+        const uint32_t sx = as ^ bs;
+        return ((m ^ sx) - sx) & az & bz;
+    }
+    __device__ static void mac(Acc &acc, const Mag &wm, const uint4 &ws, const Mag &vm, const uint4 &vs) {
+        const uint32_t t1 = ox(wm.x, ws.x, ws.z, vm.x, vs.x, vs.z);
+        const uint32_t t2 = ox(wm.y, ws.y, ws.w, vm.y, vs.y, vs.w);
+        const uint32_t t3 = ox(wm.y, ws.y, ws.w, vm.x, vs.x, vs.z);
+        const uint32_t t4 = ox(vm.y, vs.y, vs.w, wm.x, ws.x, ws.z);
+        acc.x += t1 - t2;
+        acc.y += t3 + t4;
+    }
+    using Out = uint2;
+    __device__ static uint2 out(const Acc &a) { return a; }
+};
+
+template <class P>
+__device__ __forceinline__ typename P::V load_tw(const typename P::Tw *tw, int64_t m) {
+    return P::load(tw, m);
+}
+
+// ---- data sources ------------------------------------------------------------
+template <class P>
+struct NdftSrc {
+    const typename P::In *x;
+    int64_t ld;  // row stride (= N)
+    __device__ typename P::V operator()(int64_t col, int64_t n) const { return P::load(x, col * ld + n); }
+};
+
+template <class P>
+struct CafSrc {
+    const typename P::In *ss;
+    const typename P::In *sr;
+    int N;
+    int lag0;
+    uint32_t flags;
+    __device__ typename P::V operator()(int64_t col, int64_t n) const {
+        int64_t j = n - (lag0 + col);
+        typename P::V ref = P::zero();
+        if (flags & NDFT_F_CIRCULAR_LAG) {
+            j %= N;
+            if (j < 0) j += N;
+        }
+        if (j >= 0 && j < N) {
+            ref = P::load(sr, j);
+            if (!(flags & NDFT_F_NO_CONJ_REF)) ref = P::conj_(ref);
+        }
+        return P::cox(P::load(ss, n), ref);  // lag product of Eq. 12a
+    }
+};
+
+struct Smem {
+    // [KC][BP + 2] magnitudes and [KC][BP + 1] sign/zero words, twiddles then data.
+    static constexpr int kMagStride = BP + 2;
+    static constexpr int kSgnStride = BP + 1;
+    static constexpr size_t bytes(size_t mag_size) {
+        return 2 * (KC * kMagStride * mag_size + KC * kSgnStride * sizeof(uint4));
+    }
+};
+
+// One 64 x 64 tile over samples [n_begin, n_end).  out points at the tile's
+// [col][bin] destination with row stride ldo.
+template <class P, class Src>
+__device__ __forceinline__ void direct_tile(unsigned char *smem, const typename P::Tw *__restrict__ tw, int N,
+                                            int p0, int nbins, int ncols, int bin0, int col0, int64_t n_begin,
+                                            int64_t n_end, const Src &src, typename P::Out *__restrict__ out,
+                                            int64_t ldo) {
+    using Mag = typename P::Mag;
+    Mag *tM = reinterpret_cast<Mag *>(smem);
+    uint4 *tS = reinterpret_cast<uint4 *>(tM + KC * Smem::kMagStride);
+    Mag *vM = reinterpret_cast<Mag *>(tS + KC * Smem::kSgnStride);
+    uint4 *vS = reinterpret_cast<uint4 *>(vM + KC * Smem::kMagStride);
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+
+    // twiddle staging: fixed bin b, samples kk = (tid >> 6) + 4 j
+    const int sb = tid & 63;
+    const int bin = bin0 + sb;
+    const bool bin_ok = bin < nbins;
+    int64_t pm = ((int64_t)p0 + bin) % N;
+    if (pm < 0) pm += N;
+    int64_t m[4];
+    const int kk0 = tid >> 6;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m[j] = (pm * ((n_begin + kk0 + 4 * j) % N)) % N;
+    const int64_t step = (pm * KC) % N;
+
+    // data staging: fixed sample kk = tid & 15, columns c = (tid >> 4) + 16 j
+    const int dk = tid & 15, dc0 = tid >> 4;
+
+    typename P::Acc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = P::acc0();
+
+    for (int64_t n0 = n_begin; n0 < n_end; n0 += KC) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kk = kk0 + 4 * j;
+            const bool ok = bin_ok && (n0 + kk < n_end);
+            typename P::V w = ok ? load_tw<P>(tw, m[j]) : P::zero();
+            Mag mg;
+            uint4 sg;
+            P::ready(w, mg, sg);
+            tM[kk * Smem::kMagStride + sb] = mg;
+            tS[kk * Smem::kSgnStride + sb] = sg;
+            m[j] += step;
+            if (m[j] >= N) m[j] -= N;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = dc0 + 16 * j;
+            const int64_t n = n0 + dk;
+            typename P::V v = (n < n_end && col0 + c < ncols) ? src(col0 + c, n) : P::zero();
+            Mag mg;
+            uint4 sg;
+            P::ready(v, mg, sg);
+            vM[dk * Smem::kMagStride + c] = mg;
+            vS[dk * Smem::kSgnStride + c] = sg;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int kk = 0; kk < KC; ++kk) {
+            Mag wm[4], vm[4];
+            uint4 ws[4], vs[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                wm[i] = tM[kk * Smem::kMagStride + ty * 4 + i];
+                ws[i] = tS[kk * Smem::kSgnStride + ty * 4 + i];
+                vm[i] = vM[kk * Smem::kMagStride + tx * 4 + i];
+                vs[i] = vS[kk * Smem::kSgnStride + tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) P::mac(acc[i][j], wm[i], ws[i], vm[j], vs[j]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = col0 + tx * 4 + j;
+        if (col >= ncols) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int b = bin0 + ty * 4 + i;
+            if (b < nbins) out[(int64_t)col * ldo + b] = P::out(acc[i][j]);
+        }
+    }
+}
+
+template <class P, class Src>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_direct(const typename P::Tw *__restrict__ tw, int N, int p0, int nbins, int ncols, Src src,
+             int64_t samples_per_split, typename P::Out *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int bin0 = blockIdx.x * BP;
+    const int col0 = blockIdx.y * BC;
+    const int64_t n_begin = (int64_t)blockIdx.z * samples_per_split;
+    const int64_t n_end = min((int64_t)N, n_begin + samples_per_split);
+    typename P::Out *o = out + (int64_t)blockIdx.z * ncols * nbins;
+    direct_tile<P, Src>(smem, tw, N, p0, nbins, ncols, bin0, col0, n_begin, n_end, src, o, nbins);
+}
+
+// Persistent kernel over the CPI work list of a batched plan.  Unit u of the
+// list encodes (cpi, bin tile, lag tile); units are fetched with an atomic
+// counter, longest CPIs first, and each writes its tile of that CPI's surface.
+template <class P>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_direct_batched(const CpiDev *__restrict__ cpis, const int32_t *__restrict__ work, int64_t nwork,
+                     int32_t *__restrict__ counter, const unsigned char *__restrict__ tab_arena,
+                     const typename P::In *__restrict__ surv, const typename P::In *__restrict__ ref,
+                     typename P::Out *__restrict__ outb, uint32_t flags) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int32_t s_unit;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int32_t u = s_unit;
+        __syncthreads();
+        if (u >= nwork) break;
+        const int32_t c = work[3 * u], bt = work[3 * u + 1], lt = work[3 * u + 2];
+        const CpiDev cp = cpis[c];
+        const typename P::Tw *tw = reinterpret_cast<const typename P::Tw *>(tab_arena) + cp.tw_off;
+        CafSrc<P> src{surv + cp.off_surv, ref + cp.off_ref, cp.n, cp.lag0, flags};
+        direct_tile<P, CafSrc<P>>(smem, tw, cp.n, cp.p0, cp.nbins, cp.nlags, bt * BP, lt * BC, 0, cp.n, src,
+                                  outb + cp.off_out, cp.nbins);
+    }
+}
+
+template <class K>
+cudaError_t prep_kernel(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune) {
+    if (tune > 0) return std::max(1, std::min(tune, std::max(1, N / KC)));
+    const int64_t tiles = (int64_t)((nbins + BP - 1) / BP) * ((nlags + BC - 1) / BC);
+    int64_t s = (8LL * sm_count + tiles - 1) / tiles;
+    s = std::min<int64_t>(s, std::max(1, N / 256));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(s, 16));
+}
+
+size_t direct_ws_bytes(const ndft_desc &d, int sm_count) {
+    if (d.max_lags <= 0) return 0;
+    const int nb = d.nbins ? d.nbins : d.n;
+    const int s = 16;  // upper bound of direct_caf_splits
+    (void)sm_count;
+    return (size_t)s * d.max_lags * nb * sizeof(float2);
+}
+
+cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
+                               int *launches) {
+    const int N = p.d.n, nb = p.d.nbins ? p.d.nbins : N;
+    if (batch == 0) return cudaSuccess;
+    dim3 grid((nb + BP - 1) / BP, (unsigned)((batch + BC - 1) / BC), 1);
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+    if (p.d.prec == NDFT_PREC_FP32) {
+        const size_t sm = Smem::bytes(sizeof(float2));
+        auto k = k_direct<PrecF32, NdftSrc<PrecF32>>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, (int)batch,
+                                     NdftSrc<PrecF32>{static_cast<const float2 *>(x), N}, N,
+                                     static_cast<float2 *>(X));
+    } else {
+        const size_t sm = Smem::bytes(sizeof(int2));
+        auto k = k_direct<PrecQ14, NdftSrc<PrecQ14>>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, (int)batch,
+                                     NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, N,
+                                     static_cast<uint2 *>(X));
+    }
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
+                              void *A, cudaStream_t s, int *launches) {
+    const int N = p.d.n, nb = p.d.nbins ? p.d.nbins : N;
+    const int nsplit = direct_caf_splits(N, nlags, nb, p.sm_count, p.tune_split);
+    const int64_t per = ((int64_t)N + nsplit - 1) / nsplit;
+    const int64_t per_al = ((per + KC - 1) / KC) * KC;
+    const int ns = (int)((N + per_al - 1) / per_al);
+    dim3 grid((nb + BP - 1) / BP, (nlags + BC - 1) / BC, ns);
+    cudaError_t e;
+    const bool direct_out = (ns == 1);
+    if (p.d.prec == NDFT_PREC_FP32) {
+        const size_t sm = Smem::bytes(sizeof(float2));
+        auto k = k_direct<PrecF32, CafSrc<PrecF32>>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        float2 *dst = direct_out ? static_cast<float2 *>(A) : static_cast<float2 *>(p.ws);
+        CafSrc<PrecF32> src{static_cast<const float2 *>(s_surv), static_cast<const float2 *>(s_ref), N, lag0,
+                            p.d.flags};
+        k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, nlags, src, per_al, dst);
+        *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (!direct_out) {
+            *launches += 1;
+            return launch_reduce_splits(static_cast<const float *>(p.ws), ns, (int64_t)nlags * nb * 2,
+                                        static_cast<float *>(A), s);
+        }
+    } else {
+        const size_t sm = Smem::bytes(sizeof(int2));
+        auto k = k_direct<PrecQ14, CafSrc<PrecQ14>>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        uint2 *dst = direct_out ? static_cast<uint2 *>(A) : static_cast<uint2 *>(p.ws);
+        CafSrc<PrecQ14> src{static_cast<const short2 *>(s_surv), static_cast<const short2 *>(s_ref), N, lag0,
+                            p.d.flags};
+        k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, nlags, src, per_al, dst);
+        *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (!direct_out) {
+            *launches += 1;
+            return launch_reduce_splits_i32(static_cast<const uint32_t *>(p.ws), ns, (int64_t)nlags * nb * 2,
+                                            static_cast<uint32_t *>(A), s);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
+                                  int *launches) {
+    cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int grid = p.sm_count * 2;
+    if (p.d.prec == NDFT_PREC_FP32) {
+        const size_t sm = Smem::bytes(sizeof(float2));
+        auto k = k_direct_batched<PrecF32>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
+                                     static_cast<const unsigned char *>(p.tab_arena),
+                                     static_cast<const float2 *>(surv), static_cast<const float2 *>(ref),
+                                     static_cast<float2 *>(out), p.d.flags);
+    } else {
+        const size_t sm = Smem::bytes(sizeof(int2));
+        auto k = k_direct_batched<PrecQ14>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
+                                     static_cast<const unsigned char *>(p.tab_arena),
+                                     static_cast<const short2 *>(surv), static_cast<const short2 *>(ref),
+                                     static_cast<uint2 *>(out), p.d.flags);
+    }
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace ndft

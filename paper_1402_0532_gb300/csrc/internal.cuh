@@ -1,0 +1,149 @@
+// internal.cuh -- plan object, device helpers and launcher declarations shared
+// by the library's translation units.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/ndft.h"
+
+namespace ndft {
+
+constexpr uint32_t kSignBit = 0x80000000u;
+
+// Device error codes written to the plan's error word (first writer wins).
+enum DevErr : int32_t { kDevOk = 0, kDevTimeout = 5, kDevBadIndex = 7 };
+
+// One CPI of a batched plan, as the kernels see it (device copy).
+struct CpiDev {
+    int64_t off_surv, off_ref, off_out;
+    int32_t n, lag0, nlags, p0, nbins;
+    int32_t tab;        // index of this CPI's twiddle tables in the table arena
+    int64_t tw_off;     // element offset of its fp32 / Q1.14 full table
+    int64_t qt_off;     // element offset of its bf16 quarter table
+    int64_t b_off;      // element offset (bf16) of its packed B operand in the workspace
+    int64_t ws_off;     // element offset (float) of its split-K partials
+    int32_t nsplit;     // sample-axis splits
+    int32_t kblocks;    // 64-wide K blocks (ternary form)
+};
+
+struct Plan {
+    ndft_desc d{};
+    bool batched = false;
+    int device = 0;
+    int sm_count = 0;
+    int g4 = 1;                  // gcd(4, N)
+    // tables (single-CPI plans)
+    float2 *tw32 = nullptr;      // [N]
+    short2 *twq = nullptr;       // [N]
+    uint32_t *qtab = nullptr;    // [N/g4 + 1] bf16 hi | lo << 16
+    // workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int32_t *err = nullptr;      // device error word
+    size_t table_bytes = 0;
+    // batched
+    int32_t ncpi = 0;
+    CpiDev *cpis_dev = nullptr;
+    CpiDev *cpis_host = nullptr;
+    void *tab_arena = nullptr;   // per-CPI tables
+    int32_t *work_dev = nullptr; // work list (ternary / direct units)
+    int64_t nwork = 0;
+    int32_t *counter = nullptr;  // persistent-kernel tile counter
+    // tuning
+    int tune_split = 0;
+    int tune_cols = 0;
+    int last_launches = 0;
+    // ternary GEMM: TMA descriptor storage (host copy + device copy)
+    void *tmap_host = nullptr;
+    void *tmap_dev = nullptr;
+    size_t b_bytes = 0;          // packed-B region of the workspace
+    size_t part_bytes = 0;       // split-K partials region of the workspace
+};
+
+// ---- the operator on device ------------------------------------------------------
+
+// An operand component prepared for (x): magnitude, sign word, nonzero mask.
+// Eq. 1: |a| + |b| rounded once; Eq. 2: the sign of the product is the XOR of
+// the sign bits, and the result is 0 when either operand is 0.
+__device__ __forceinline__ float ox_ready(float am, uint32_t as, uint32_t az, float bm, uint32_t bs,
+                                          uint32_t bz) {
+    uint32_t r = (__float_as_uint(am + bm) ^ as ^ bs) & az & bz;
+    return __uint_as_float(r);
+}
+
+// The same on raw fp32 values (sign and zero read off the operands).
+__device__ __forceinline__ float ox_f32(float a, float b) {
+    uint32_t ua = __float_as_uint(a), ub = __float_as_uint(b);
+    uint32_t za = (ua << 1) ? 0xffffffffu : 0u;   // +-0 -> 0 mask
+    uint32_t zb = (ub << 1) ? 0xffffffffu : 0u;
+    return ox_ready(fabsf(a), ua & kSignBit, za, fabsf(b), ub & kSignBit, zb);
+}
+
+// Eq. 6 on raw fp32 values: (a_r(x)b_r - a_i(x)b_i, a_i(x)b_r + b_i(x)a_r),
+// each real (x) rounded once, then one subtraction / addition.
+__device__ __forceinline__ float2 cox_f32(float2 a, float2 b) {
+    float t1 = ox_f32(a.x, b.x);
+    float t2 = ox_f32(a.y, b.y);
+    float t3 = ox_f32(a.y, b.x);
+    float t4 = ox_f32(b.y, a.x);
+    return make_float2(__fsub_rn(t1, t2), __fadd_rn(t3, t4));
+}
+
+// Integer (x) (Q1.14 units): sgn(a) sgn(b) (|a| + |b|), 0 if either is 0.
+__device__ __forceinline__ int32_t ox_i32(int32_t a, int32_t b) {
+    int32_t m = abs(a) + abs(b);
+    int32_t s = (a ^ b) >> 31;             // -1 if the signs differ
+    int32_t r = (m ^ s) - s;
+    return (a != 0 && b != 0) ? r : 0;
+}
+
+__device__ __forceinline__ int2 cox_i32(int2 a, int2 b) {
+    return make_int2(ox_i32(a.x, b.x) - ox_i32(a.y, b.y), ox_i32(a.y, b.x) + ox_i32(b.y, a.x));
+}
+
+__device__ __forceinline__ void dev_set_error(int32_t *err, int32_t code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ---- launchers (defined in the .cu files) --------------------------------------
+
+// tables.cu
+cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, uint32_t *qtab, cudaStream_t s);
+
+// direct.cu
+cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
+                               int *launches);
+cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
+                              void *A, cudaStream_t s, int *launches);
+cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *ref, void *out,
+                                  cudaStream_t s, int *launches);
+size_t direct_ws_bytes(const ndft_desc &d, int sm_count);
+int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune);
+
+// nfft.cu
+cudaError_t launch_nfft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s, int *launches);
+
+// epilogue.cu
+cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s);
+cudaError_t launch_reduce_splits_i32(const uint32_t *ws, int nsplit, int64_t count, uint32_t *out,
+                                     cudaStream_t s);
+cudaError_t launch_argmax(const float2 *X, int64_t rows, int64_t cols, int64_t *idx, float *val,
+                          cudaStream_t s);
+
+// adjoint.cu
+cudaError_t launch_caf_backward(const Plan &p, const void *s_ref, int lag0, int nlags, const void *dA,
+                                void *ds, cudaStream_t s, int *launches);
+
+// ternary.cu
+bool ternary_supported(const ndft_desc &d);
+size_t ternary_ws_bytes(const ndft_desc &d, int sm_count);
+cudaError_t ternary_plan_init(Plan &p, cudaStream_t s);
+cudaError_t launch_ternary_ndft(Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
+                                int *launches);
+cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
+                               void *A, cudaStream_t s, int *launches);
+
+}  // namespace ndft

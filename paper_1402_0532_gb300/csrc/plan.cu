@@ -1,0 +1,370 @@
+// plan.cu -- the C ABI of include/ndft.h: argument checks, plan lifecycle,
+// dispatch to the kernels.  Exec calls allocate nothing and never synchronise.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace ndft;
+
+struct ndft_plan_s {
+    Plan p;
+};
+
+namespace {
+
+bool aligned16(const void *ptr) { return ptr && ((uintptr_t)ptr & 15u) == 0; }
+
+ndft_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return NDFT_OK;
+    if (e == cudaErrorMemoryAllocation) return NDFT_E_NOMEM;
+    return NDFT_E_CUDA;
+}
+
+bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+bool valid_pair(int form, int prec) {
+    if (form == NDFT_FORM_DIRECT) return prec == NDFT_PREC_FP32 || prec == NDFT_PREC_Q14;
+    if (form == NDFT_FORM_TERNARY_GEMM) return prec == NDFT_PREC_BF16X2;
+    return false;
+}
+
+constexpr uint32_t kKnownFlags = NDFT_F_NO_CONJ_REF | NDFT_F_CIRCULAR_LAG;
+constexpr int32_t kMaxN = 1 << 22;
+
+void free_plan(Plan &p) {
+    cudaFree(p.tw32);
+    cudaFree(p.twq);
+    cudaFree(p.qtab);
+    cudaFree(p.ws);
+    cudaFree(p.err);
+    cudaFree(p.cpis_dev);
+    cudaFree(p.tab_arena);
+    cudaFree(p.work_dev);
+    cudaFree(p.counter);
+    cudaFree(p.tmap_dev);
+    std::free(p.tmap_host);
+    delete[] p.cpis_host;
+}
+
+template <class T>
+cudaError_t alloc(T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(ptr), count * sizeof(T));
+}
+
+size_t backward_ws_bytes(const ndft_desc &d) {
+    if (d.max_lags <= 0) return 0;
+    return (size_t)((d.max_lags + 63) / 64) * d.n * sizeof(float2);
+}
+
+int sm_count_now(int *dev) {
+    int sm = 0;
+    cudaGetDevice(dev);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, *dev);
+    return sm > 0 ? sm : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ndft_status_string(ndft_status s) {
+    switch (s) {
+        case NDFT_OK: return "ok";
+        case NDFT_E_INVALID: return "invalid argument";
+        case NDFT_E_UNSUPPORTED: return "unsupported request";
+        case NDFT_E_CUDA: return "CUDA error";
+        case NDFT_E_NOMEM: return "out of device memory";
+        case NDFT_E_TIMEOUT: return "device-side wait timed out";
+        case NDFT_E_OVERFLOW: return "fixed-point overflow";
+    }
+    return "unknown status";
+}
+
+int32_t ndft_version(void) { return 100; }
+
+ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream) {
+    if (!out || !d) return NDFT_E_INVALID;
+    *out = nullptr;
+    if (d->n < 1 || d->n > kMaxN || d->nbins < 0 || d->nbins > d->n || d->max_lags < 0 || d->max_batch < 0)
+        return NDFT_E_INVALID;
+    if (d->max_lags > (1 << 20) || (d->flags & ~kKnownFlags) || d->reserved[0] || d->reserved[1] ||
+        d->reserved[2])
+        return NDFT_E_INVALID;
+    if (!valid_pair(d->form, d->prec)) {
+        const bool known = (d->form == 0 || d->form == 1) && (d->prec >= 0 && d->prec <= 2);
+        return known ? NDFT_E_UNSUPPORTED : NDFT_E_INVALID;
+    }
+    auto *h = new (std::nothrow) ndft_plan_s();
+    if (!h) return NDFT_E_NOMEM;
+    Plan &p = h->p;
+    p.d = *d;
+    if (p.d.nbins == 0) p.d.nbins = d->n;
+    p.sm_count = sm_count_now(&p.device);
+    const int N = p.d.n;
+    p.g4 = (N % 4 == 0) ? 4 : (N % 2 == 0 ? 2 : 1);
+    cudaError_t e = cudaSuccess;
+    const bool tern = p.d.form == NDFT_FORM_TERNARY_GEMM;
+    if ((e = alloc(&p.tw32, N)) != cudaSuccess) goto fail;
+    if (p.d.prec == NDFT_PREC_Q14 && (e = alloc(&p.twq, N)) != cudaSuccess) goto fail;
+    if (tern && (e = alloc(&p.qtab, N / p.g4 + 1)) != cudaSuccess) goto fail;
+    if ((e = alloc(&p.err, 1)) != cudaSuccess) goto fail;
+    if ((e = cudaMemsetAsync(p.err, 0, sizeof(int32_t), stream)) != cudaSuccess) goto fail;
+    p.table_bytes = (size_t)N * (sizeof(float2) + (p.twq ? sizeof(short2) : 0)) +
+                    (p.qtab ? (size_t)(N / p.g4 + 1) * 4 : 0);
+    {
+        size_t ws = std::max(direct_ws_bytes(p.d, p.sm_count), backward_ws_bytes(p.d));
+        if (tern) ws = std::max(ws, ternary_ws_bytes(p.d, p.sm_count));
+        p.ws_bytes = ws;
+        if (ws && (e = cudaMalloc(&p.ws, ws)) != cudaSuccess) goto fail;
+    }
+    if ((e = launch_tables(N, p.tw32, p.twq, p.qtab, stream)) != cudaSuccess) goto fail;
+    if (tern && (e = ternary_plan_init(p, stream)) != cudaSuccess) goto fail;
+    *out = h;
+    return NDFT_OK;
+fail:
+    free_plan(p);
+    delete h;
+    return from_cuda(e);
+}
+
+ndft_status ndft_plan_destroy(ndft_plan_t plan) {
+    if (!plan) return NDFT_E_INVALID;
+    cudaDeviceSynchronize();
+    free_plan(plan->p);
+    delete plan;
+    return NDFT_OK;
+}
+
+ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream) {
+    if (!plan || plan->p.batched || batch < 0 || batch > plan->p.d.max_batch) return NDFT_E_INVALID;
+    if (batch == 0) return NDFT_OK;
+    if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    p.last_launches = 0;
+    cudaError_t e;
+    if (p.d.form == NDFT_FORM_DIRECT) {
+        if (batch > 65535LL * 64) return NDFT_E_UNSUPPORTED;
+        e = launch_direct_ndft(p, x, X, batch, stream, &p.last_launches);
+    } else {
+        e = launch_ternary_ndft(p, x, X, batch, stream, &p.last_launches);
+    }
+    return from_cuda(e);
+}
+
+ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream) {
+    if (!plan || plan->p.batched || batch < 0 || batch > plan->p.d.max_batch) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    if (p.d.prec != NDFT_PREC_FP32 || !pow2(p.d.n) || p.d.n < 2 || p.d.n > (1 << 20) || p.d.nbins != p.d.n ||
+        p.d.p0 % p.d.n != 0)
+        return NDFT_E_INVALID;
+    if (batch == 0) return NDFT_OK;
+    if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
+    p.last_launches = 0;
+    return from_cuda(launch_nfft(p, x, X, batch, stream, &p.last_launches));
+}
+
+ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags, void *A,
+                     cudaStream_t stream) {
+    if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
+    if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(A)) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    p.last_launches = 0;
+    cudaError_t e;
+    if (p.d.form == NDFT_FORM_DIRECT)
+        e = launch_direct_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
+    else
+        e = launch_ternary_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
+    return from_cuda(e);
+}
+
+ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags,
+                         const void *dA, void *ds, cudaStream_t stream) {
+    (void)s_surv;
+    if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    if (p.d.prec == NDFT_PREC_Q14) return NDFT_E_UNSUPPORTED;
+    if (!aligned16(s_ref) || !aligned16(dA) || !aligned16(ds)) return NDFT_E_INVALID;
+    p.last_launches = 0;
+    return from_cuda(launch_caf_backward(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches));
+}
+
+ndft_status ndft_argmax(const void *X, int64_t rows, int64_t cols, int64_t *idx, float *val, cudaStream_t stream) {
+    if (rows < 0 || cols < 1 || (rows > 0 && (!X || !idx))) return NDFT_E_INVALID;
+    if (((uintptr_t)X & 7u) || ((uintptr_t)idx & 7u) || ((uintptr_t)val & 3u)) return NDFT_E_INVALID;
+    return from_cuda(launch_argmax(static_cast<const float2 *>(X), rows, cols, idx, val, stream));
+}
+
+ndft_status ndft_query_error(ndft_plan_t plan, cudaStream_t stream) {
+    if (!plan) return NDFT_E_INVALID;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return NDFT_E_CUDA;
+    int32_t v = 0;
+    if ((e = cudaMemcpy(&v, plan->p.err, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess) return NDFT_E_CUDA;
+    if (v != 0 && (e = cudaMemset(plan->p.err, 0, sizeof(int32_t))) != cudaSuccess) return NDFT_E_CUDA;
+    if (v == 0) return NDFT_OK;
+    if (v == kDevTimeout) return NDFT_E_TIMEOUT;
+    return NDFT_E_CUDA;
+}
+
+ndft_status ndft_get_twiddles(ndft_plan_t plan, int32_t which, void *dst, cudaStream_t stream) {
+    if (!plan || plan->p.batched || !dst) return NDFT_E_INVALID;
+    const Plan &p = plan->p;
+    const int N = p.d.n;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    if (which == 0) {
+        src = p.tw32;
+        bytes = (size_t)N * sizeof(float2);
+    } else if (which == 1) {
+        src = p.twq;
+        bytes = (size_t)N * sizeof(short2);
+    } else if (which == 2) {
+        src = p.qtab;
+        bytes = (size_t)(N / p.g4 + 1) * sizeof(uint32_t);
+    } else {
+        return NDFT_E_INVALID;
+    }
+    if (!src) return NDFT_E_UNSUPPORTED;
+    return from_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream));
+}
+
+ndft_status ndft_plan_bytes(ndft_plan_t plan, int64_t *bytes) {
+    if (!plan || !bytes) return NDFT_E_INVALID;
+    *bytes = (int64_t)(plan->p.table_bytes + plan->p.ws_bytes);
+    return NDFT_OK;
+}
+
+ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count) {
+    if (!plan || !count) return NDFT_E_INVALID;
+    *count = plan->p.last_launches;
+    return NDFT_OK;
+}
+
+ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
+    if (!plan || value < 0) return NDFT_E_INVALID;
+    if (key == 0) {
+        if (value > 4096) return NDFT_E_INVALID;
+        plan->p.tune_split = value;
+    } else if (key == 1) {
+        if (value != 0 && value != 128 && value != 256) return NDFT_E_INVALID;
+        plan->p.tune_cols = value;
+    } else {
+        return NDFT_E_INVALID;
+    }
+    return NDFT_OK;
+}
+
+// ---- batched plans -----------------------------------------------------------------
+
+ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t ncpi, int32_t form, int32_t prec,
+                              uint32_t flags, cudaStream_t stream) {
+    if (!out || !cpis || ncpi < 1 || ncpi > (1 << 20) || (flags & ~kKnownFlags)) return NDFT_E_INVALID;
+    *out = nullptr;
+    if (!valid_pair(form, prec)) return NDFT_E_UNSUPPORTED;
+    if (form != NDFT_FORM_DIRECT) return NDFT_E_UNSUPPORTED;
+    for (int c = 0; c < ncpi; ++c) {
+        const ndft_cpi &q = cpis[c];
+        if (q.n < 1 || q.n > kMaxN || q.nlags < 1 || q.nlags > (1 << 20) || q.nbins < 1 || q.nbins > q.n ||
+            q.off_surv < 0 || q.off_ref < 0 || q.off_out < 0 || q.reserved)
+            return NDFT_E_INVALID;
+        // 16-byte alignment of each CPI's rows: offsets in elements of 8 bytes (complex64) or 4 (Q1.14)
+        const int esz = prec == NDFT_PREC_Q14 ? 4 : 8;
+        if ((q.off_surv * esz) % 16 || (q.off_ref * esz) % 16) return NDFT_E_INVALID;
+    }
+    auto *h = new (std::nothrow) ndft_plan_s();
+    if (!h) return NDFT_E_NOMEM;
+    Plan &p = h->p;
+    p.batched = true;
+    p.d = ndft_desc{};
+    p.d.form = form;
+    p.d.prec = prec;
+    p.d.flags = flags;
+    p.ncpi = ncpi;
+    p.sm_count = sm_count_now(&p.device);
+    cudaError_t e = cudaSuccess;
+    std::vector<int32_t> work;
+    p.cpis_host = new (std::nothrow) CpiDev[ncpi];
+    if (!p.cpis_host) {
+        delete h;
+        return NDFT_E_NOMEM;
+    }
+    {
+        const size_t tsz = prec == NDFT_PREC_Q14 ? sizeof(short2) : sizeof(float2);
+        int64_t tw_total = 0;
+        for (int c = 0; c < ncpi; ++c) {
+            CpiDev &q = p.cpis_host[c];
+            std::memset(&q, 0, sizeof(q));
+            q.off_surv = cpis[c].off_surv;
+            q.off_ref = cpis[c].off_ref;
+            q.off_out = cpis[c].off_out;
+            q.n = cpis[c].n;
+            q.lag0 = cpis[c].lag0;
+            q.nlags = cpis[c].nlags;
+            q.p0 = cpis[c].p0;
+            q.nbins = cpis[c].nbins;
+            q.tab = c;
+            q.tw_off = tw_total;
+            tw_total += (q.n + 3) & ~3;  // keep every table 16-byte aligned
+        }
+        if ((e = cudaMalloc(&p.tab_arena, std::max<size_t>(16, tw_total * tsz))) != cudaSuccess) goto fail;
+        p.table_bytes = tw_total * tsz;
+        for (int c = 0; c < ncpi; ++c) {
+            const CpiDev &q = p.cpis_host[c];
+            float2 *t32 = prec == NDFT_PREC_Q14 ? nullptr : static_cast<float2 *>(p.tab_arena) + q.tw_off;
+            short2 *tq = prec == NDFT_PREC_Q14 ? static_cast<short2 *>(p.tab_arena) + q.tw_off : nullptr;
+            if ((e = launch_tables(q.n, t32, tq, nullptr, stream)) != cudaSuccess) goto fail;
+        }
+        // work list: (cpi, bin tile, lag tile), longest CPIs first
+        std::vector<int> order(ncpi);
+        for (int c = 0; c < ncpi; ++c) order[c] = c;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (int64_t)p.cpis_host[a].n > (int64_t)p.cpis_host[b].n;
+        });
+        for (int c : order) {
+            const CpiDev &q = p.cpis_host[c];
+            for (int bt = 0; bt < (q.nbins + 63) / 64; ++bt)
+                for (int lt = 0; lt < (q.nlags + 63) / 64; ++lt) {
+                    work.push_back(c);
+                    work.push_back(bt);
+                    work.push_back(lt);
+                }
+        }
+        p.nwork = (int64_t)work.size() / 3;
+        if ((e = alloc(&p.work_dev, work.size())) != cudaSuccess) goto fail;
+        if ((e = cudaMemcpyAsync(p.work_dev, work.data(), work.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 stream)) != cudaSuccess)
+            goto fail;
+        if ((e = alloc(&p.cpis_dev, ncpi)) != cudaSuccess) goto fail;
+        if ((e = cudaMemcpyAsync(p.cpis_dev, p.cpis_host, ncpi * sizeof(CpiDev), cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess)
+            goto fail;
+        if ((e = alloc(&p.counter, 1)) != cudaSuccess) goto fail;
+        if ((e = alloc(&p.err, 1)) != cudaSuccess) goto fail;
+        if ((e = cudaMemsetAsync(p.err, 0, sizeof(int32_t), stream)) != cudaSuccess) goto fail;
+        // the host vector must outlive the async copy
+        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) goto fail;
+    }
+    *out = h;
+    return NDFT_OK;
+fail:
+    free_plan(p);
+    delete h;
+    return from_cuda(e);
+}
+
+ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void *ref_base, void *out_base,
+                             cudaStream_t stream) {
+    if (!plan || !plan->p.batched) return NDFT_E_INVALID;
+    if (!aligned16(surv_base) || !aligned16(ref_base) || !aligned16(out_base)) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    p.last_launches = 0;
+    return from_cuda(launch_direct_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));
+}
+
+}  // extern "C"
