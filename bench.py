@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the nonlinear cross-ambiguity function (Eq. 12a) on one GB300.
+
+Workload: the passive-radar surface with N = 65536 samples, 1024 lags x 1024
+Doppler bins (-512..511), band-limited reference and echoes at delays
+37/120/301, Doppler bins 5/-12/40 (seed 2); the chosen tensor-core form
+(ternary GEMM) is timed per step, the plain direct form beside it.
+
+One step = one pass of the path over one surface: lag products + bf16 split
+(packing), the ternary contraction on tcgen05, the split-K reduction and the
+peak search.  Inputs are resident in HBM; L2 is flushed (256 MiB write)
+between steps outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own surface
+(weak scaling, no collective on the data path; max time over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NDFT-CAF cells/s: ternary-GEMM vs direct-⊗, % roofline, max err vs FP64"
+N, NLAGS, NBINS, P0 = 65536, 1024, 1024, -512
+WORKLOAD = "passive-radar nonlinear CAF (Eq. 12a), N=65536, 1024 lags x 1024 Doppler bins, fp32 scene"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_BF16_TFLOPS = 1900.0
+GEMM_PROFILE = os.path.join(ROOT, "profiles", "ternary_gemm_caf_n65536.md")
+GEMM_SOURCE = os.path.join(ROOT, "paper_1402_0532_gb300", "csrc", "ternary.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--direct-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_BF16_TFLOPS, 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gemm_traffic():
+    """dram bytes per launch of the contraction kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    try:
+        txt = open(GEMM_PROFILE).read()
+        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        h = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", txt)
+        if not m or not h:
+            return None
+        cur = hashlib.sha1(open(GEMM_SOURCE, "rb").read()).hexdigest()
+        return float(m.group(1)) if cur == h.group(1) else None
+    except OSError:
+        return None
+
+
+def cpu_baseline(scene, budget_cells: int):
+    """The oracle as it stands on a bounded sample: lags 0.. of the same surface, all 1024 bins."""
+    import numpy as np
+
+    import oracle
+    nl = max(1, budget_cells // NBINS)
+    lags = np.repeat(np.arange(nl), NBINS)
+    bins = np.tile(np.arange(P0, P0 + NBINS), nl)
+    t0 = time.perf_counter()
+    oracle.caf_cells(scene.s_surv, scene.s_ref, lags, bins)
+    dt = time.perf_counter() - t0
+    return {"value": lags.size / dt, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nl} lags x {NBINS} bins of the same surface ({lags.size} cells, fp64 literal (x), "
+                      f"{dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1402_0532_gb300 import scenes
+    oracle.build()
+    scene = scenes.radar_scene()
+    rate_guess = 2000.0  # cells/s, sizes the per-step sample so the run stays within minutes
+    per_step = int(max(16, min(NBINS, 90.0 * rate_guess / max(1, args.steps + args.warmup))))
+    rng = np.random.default_rng(7)
+
+    def step():
+        lags = rng.integers(0, NLAGS, per_step)
+        bins = rng.integers(P0, P0 + NBINS, per_step)
+        oracle.caf_cells(scene.s_surv, scene.s_ref, lags, bins)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "nlags": NLAGS, "nbins": NBINS,
+                       "sample_per_step": f"{per_step} random cells of the surface"},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step} cells per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_0532_gb300 import api, scenes
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    scene = scenes.radar_scene()
+    ss = torch.from_numpy(scene.s_surv).to(dev)
+    sr = torch.from_numpy(scene.s_ref).to(dev)
+    plan = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="ternary", prec="bf16x2", device=dev)
+    A = torch.empty(NLAGS, NBINS, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    cells = NLAGS * NBINS
+
+    def step():
+        plan.caf(ss, sr, 0, NLAGS, out=A)
+        idx, val = api.argmax(A)
+        return idx
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    launches_per_step = plan.last_launches() + 1  # + the peak search
+    torch.cuda.synchronize()
+    plan.query_error()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    plan.timer_start(K)
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    gemm_ms, gemm_n = plan.timer_read()
+    t_total = sum(step_ms)
+    if dist:
+        t = torch.tensor([t_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    plan.query_error()
+    value = world * cells * K / (t_total / 1000.0)
+
+    # the dominant kernel against its roofline
+    bf16_peak, hbm_peak, peak_src = peaks()
+    gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1000.0
+    alg_flops = 16.0 * NBINS * N * NLAGS          # 16 real flop per (bin, sample, lag)
+    issued_flops = 2.0 * (2 * NBINS) * (8 * N) * NLAGS  # the bf16 hi+lo contraction as issued
+    achieved = alg_flops / gemm_avg_s / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": achieved / bf16_peak, "traffic": gemm_traffic(), "kernel": "k_ternary_gemm",
+                "peak_source": f"{peak_src} bf16 dense (burst)",
+                "issued_tflops": issued_flops / gemm_avg_s / 1e12,
+                "issued_frac": issued_flops / gemm_avg_s / 1e12 / bf16_peak,
+                "kernel_ms": gemm_avg_s * 1000.0}
+
+    # the plain direct form, same surface
+    pd = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="direct", prec="fp32", device=dev)
+    Ad = torch.empty_like(A)
+    pd.caf(ss, sr, 0, NLAGS, out=Ad)
+    torch.cuda.synchronize()
+    dms = []
+    for _ in range(max(1, args.direct_steps)):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pd.caf(ss, sr, 0, NLAGS, out=Ad)
+        e1.record()
+        torch.cuda.synchronize()
+        dms.append(e0.elapsed_time(e1))
+    direct = {"value": cells / (statistics.mean(dms) / 1000.0), "unit": "cells/s",
+              "ms_per_step": statistics.mean(dms)}
+
+    # end to end through the public API: pinned host inputs in, surface out
+    hss = torch.from_numpy(scene.s_surv).pin_memory()
+    hsr = torch.from_numpy(scene.s_ref).pin_memory()
+    hA = torch.empty(NLAGS, NBINS, dtype=torch.complex64).pin_memory()
+    staging = {}
+    plan.caf_from_host(hss, hsr, 0, NLAGS, hA, staging)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.caf_from_host(hss, hsr, 0, NLAGS, hA, staging)
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": world * cells * args.e2e_steps / e2e_dt, "unit": "cells/s",
+           "h2d_bytes_per_step": hss.numel() * 8 + hsr.numel() * 8, "d2h_bytes_per_step": hA.numel() * 8}
+
+    # error against the fp64 oracle on sampled cells (outside every timed region)
+    err = None
+    base = None
+    if rank == 0:
+        import oracle
+        rng = np.random.default_rng(11)
+        lags = np.concatenate([[0, 37, 120, 301], rng.integers(0, NLAGS, 60)])
+        bins = np.concatenate([[0, 5, -12, 40], rng.integers(P0, P0 + NBINS, 60)])
+        ref = oracle.caf_cells(scene.s_surv, scene.s_ref, lags, bins)
+        ref32 = oracle.caf_cells(scene.s_surv, scene.s_ref, lags, bins, z32=True)
+        At, Adn = A.cpu().numpy(), Ad.cpu().numpy()
+        amax = float(np.abs(At).max())
+        gt, gd = At[lags, bins - P0], Adn[lags, bins - P0]
+        err = {"ternary": float(np.max(np.abs(gt - ref)) / amax), "direct": float(np.max(np.abs(gd - ref)) / amax),
+               "ternary_vs_fp32_lagproduct": float(np.max(np.abs(gt - ref32)) / amax),
+               "direct_vs_fp32_lagproduct": float(np.max(np.abs(gd - ref32)) / amax),
+               "normalised_by": "max |A| of the surface", "cells": int(lags.size)}
+        if not args.no_cpu_baseline and world == 1:
+            base = cpu_baseline(scene, budget_cells=16 * NBINS)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": K,
+                "warmup": max(3, args.warmup), "ms_per_step": t_total / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N, "nlags": NLAGS, "nbins": NBINS, "p0": P0,
+                           "form": "ternary GEMM (tcgen05, bf16 hi+lo operands, exact ternary signs, fp32 accum)",
+                           "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                           "parallelism": f"{world} independent surface(s), one per GPU"},
+                "roofline": roofline, "direct": direct, "speedup_vs_direct": value / world / direct["value"],
+                "max_err_vs_fp64": err, "e2e": e2e, "gpu_launches": launches_per_step * K,
+                "clocks": clocks, "cpu_baseline": base}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -93,9 +93,10 @@ typedef struct {
 
 /* ---- plan lifecycle ------------------------------------------------------ */
 
-/* Creates a plan: validates d, allocates the twiddle tables (fp32, bf16 hi/lo
- * quarter table, Q1.14), the workspace for max_batch / max_lags and the device
- * error word, and builds the tables on `stream` (fp64 on the GPU).  The plan
+/* Creates a plan: validates d, allocates the twiddle tables (fp32; Q1.14 or the
+ * ternary form's angle table), the workspace for max_batch / max_lags and the device
+ * error word, and builds the tables on `stream` (fp64 on the GPU).
+ * The ternary form accepts 1 <= N <= 2^18.  The plan
  * is ready once `stream` has reached this point.  Errors: NDFT_E_INVALID,
  * NDFT_E_UNSUPPORTED (form/prec pair not provided), NDFT_E_NOMEM, NDFT_E_CUDA. */
 ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream);
@@ -165,9 +166,11 @@ ndft_status ndft_argmax(const void *X, int64_t rows, int64_t cols, int64_t *idx,
  * (NDFT_OK if none) and clears it. */
 ndft_status ndft_query_error(ndft_plan_t plan, cudaStream_t stream);
 
-/* Copies the plan's twiddle table to caller memory: which = 0 -> fp32 [N]
- * float2, 1 -> Q1.14 [N] int16 pairs, 2 -> bf16 hi/lo quarter table
- * [N/g + 1] uint32 (hi in the low half), g = gcd(4, N).  Single-CPI plans. */
+/* Copies one of the plan's tables to caller memory: which = 0 -> fp32
+ * twiddles W^m, [N] float2; 1 -> Q1.14 twiddles, [N] int16 pairs (Q1.14
+ * plans); 2 -> the ternary form's two-level angle table, [nth + 256] float2:
+ * (cos, sin)((pi/2) 256 j / N) for j < nth = (N-1)/256 + 1, then
+ * (cos, sin)((pi/2) j / N) for j < 256 (ternary plans).  Single-CPI plans. */
 ndft_status ndft_get_twiddles(ndft_plan_t plan, int32_t which, void *dst, cudaStream_t stream);
 
 /* Bytes of device memory the plan holds (tables + workspace). */
@@ -181,6 +184,16 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * 256; 0 = automatic).  Used by the autotuner; affects speed, not results
  * beyond fp32 summation order. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
+
+/* Device timing of the plan's main contraction kernel (the tensor-core GEMM,
+ * the direct tile kernel, the NFFT or the adjoint kernel).  ndft_timer_start
+ * creates `capacity` CUDA event pairs (0 disarms and frees them); every later
+ * exec call then records one pair on its stream immediately around that kernel,
+ * until capacity pairs are used.  ndft_timer_read synchronises on the recorded
+ * events, returns the summed elapsed milliseconds and the number of timed
+ * launches, and rearms the pairs.  Exec calls stay allocation-free. */
+ndft_status ndft_timer_start(ndft_plan_t plan, int32_t capacity);
+ndft_status ndft_timer_read(ndft_plan_t plan, double *ms_total, int32_t *count);
 
 const char *ndft_status_string(ndft_status s);
 

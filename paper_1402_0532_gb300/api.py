@@ -92,19 +92,29 @@ class Plan:
     def set_tuning(self, key: int, value: int):
         L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
 
+    def timer_start(self, capacity: int):
+        """Arm device timing of the main kernel for the next `capacity` exec calls."""
+        L.check(self.lib.ndft_timer_start(self.handle, int(capacity)), "ndft_timer_start")
+
+    def timer_read(self) -> tuple[float, int]:
+        """(summed milliseconds, launches timed) of the main kernel since timer_start / the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_int32()
+        L.check(self.lib.ndft_timer_read(self.handle, ctypes.byref(ms), ctypes.byref(n)), "ndft_timer_read")
+        return ms.value, n.value
+
     def query_error(self):
         L.check(self.lib.ndft_query_error(self.handle, _stream(self.device)), "ndft_query_error")
 
     def twiddles(self, which: int = 0) -> torch.Tensor:
-        """The plan's table: 0 fp32 [N] complex64, 1 Q1.14 [N, 2] int16, 2 bf16 hi/lo quarter table (int32)."""
+        """The plan's table: 0 fp32 twiddles [N] complex64, 1 Q1.14 twiddles [N, 2] int16,
+        2 the ternary form's two-level (cos, sin) table [(N-1)//256 + 1 + 256] complex64."""
         n = self.n
-        g = 4 if n % 4 == 0 else (2 if n % 2 == 0 else 1)
         if which == 0:
             out = torch.empty(n, dtype=torch.complex64, device=self.device)
         elif which == 1:
             out = torch.empty(n, 2, dtype=torch.int16, device=self.device)
         else:
-            out = torch.empty(n // g + 1, dtype=torch.int32, device=self.device)
+            out = torch.empty((n - 1) // 256 + 1 + 256, dtype=torch.complex64, device=self.device)
         L.check(self.lib.ndft_get_twiddles(self.handle, int(which), _ptr(out), _stream(self.device)),
                 "ndft_get_twiddles")
         return out
@@ -140,6 +150,23 @@ class Plan:
         L.check(self.lib.caf_exec(self.handle, _ptr(s_surv), _ptr(s_ref), int(lag0), int(nlags), _ptr(out),
                                   _stream(s_surv.device)), "caf_exec")
         return out
+
+    def caf_from_host(self, s_surv_host: torch.Tensor, s_ref_host: torch.Tensor, lag0: int, nlags: int,
+                      out_host: torch.Tensor, staging: dict | None = None) -> torch.Tensor:
+        """caf() for host (ideally pinned) buffers: copies the inputs to the device, runs
+        caf_exec and copies the surface back, all on the current stream; synchronises.
+        `staging` (optional dict) keeps the device buffers between calls."""
+        st = {} if staging is None else staging
+        if "ss" not in st:
+            st["ss"] = torch.empty_like(s_surv_host, device=self.device)
+            st["sr"] = torch.empty_like(s_ref_host, device=self.device)
+            st["A"] = torch.empty((nlags,) + self._row_shape(self.nbins), dtype=self._out_dtype, device=self.device)
+        st["ss"].copy_(s_surv_host, non_blocking=True)
+        st["sr"].copy_(s_ref_host, non_blocking=True)
+        self.caf(st["ss"], st["sr"], lag0, nlags, out=st["A"])
+        out_host.copy_(st["A"], non_blocking=True)
+        torch.cuda.current_stream(self.device).synchronize()
+        return out_host
 
     def caf_backward(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int, dA: torch.Tensor,
                      out: torch.Tensor | None = None) -> torch.Tensor:

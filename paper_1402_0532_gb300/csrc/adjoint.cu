@@ -119,8 +119,10 @@ cudaError_t launch_caf_backward(const Plan &p, const void *s_ref, int lag0, int 
     const int ltiles = (nlags + TL - 1) / TL;
     dim3 grid((N + TI - 1) / TI, ltiles);
     float2 *part = (ltiles == 1) ? static_cast<float2 *>(ds) : static_cast<float2 *>(p.ws);
+    timer_begin(p, s);
     k_caf_backward<<<grid, 256, 0, s>>>(p.tw32, static_cast<const float2 *>(s_ref), N, p.d.p0, nb, lag0, nlags,
                                         p.d.flags, static_cast<const float2 *>(dA), part);
+    timer_end(p, s);
     *launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || ltiles == 1) return e;

@@ -305,16 +305,20 @@ cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t ba
         const size_t sm = Smem::bytes(sizeof(float2));
         auto k = k_direct<PrecF32, NdftSrc<PrecF32>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, (int)batch,
                                      NdftSrc<PrecF32>{static_cast<const float2 *>(x), N}, N,
                                      static_cast<float2 *>(X));
+        timer_end(p, s);
     } else {
         const size_t sm = Smem::bytes(sizeof(int2));
         auto k = k_direct<PrecQ14, NdftSrc<PrecQ14>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, (int)batch,
                                      NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, N,
                                      static_cast<uint2 *>(X));
+        timer_end(p, s);
     }
     *launches += 1;
     return cudaGetLastError();
@@ -337,7 +341,9 @@ cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_r
         float2 *dst = direct_out ? static_cast<float2 *>(A) : static_cast<float2 *>(p.ws);
         CafSrc<PrecF32> src{static_cast<const float2 *>(s_surv), static_cast<const float2 *>(s_ref), N, lag0,
                             p.d.flags};
+        timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, nlags, src, per_al, dst);
+        timer_end(p, s);
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (!direct_out) {
@@ -352,7 +358,9 @@ cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_r
         uint2 *dst = direct_out ? static_cast<uint2 *>(A) : static_cast<uint2 *>(p.ws);
         CafSrc<PrecQ14> src{static_cast<const short2 *>(s_surv), static_cast<const short2 *>(s_ref), N, lag0,
                             p.d.flags};
+        timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, nlags, src, per_al, dst);
+        timer_end(p, s);
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (!direct_out) {
@@ -373,18 +381,22 @@ cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *r
         const size_t sm = Smem::bytes(sizeof(float2));
         auto k = k_direct_batched<PrecF32>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
                                      static_cast<const unsigned char *>(p.tab_arena),
                                      static_cast<const float2 *>(surv), static_cast<const float2 *>(ref),
                                      static_cast<float2 *>(out), p.d.flags);
+        timer_end(p, s);
     } else {
         const size_t sm = Smem::bytes(sizeof(int2));
         auto k = k_direct_batched<PrecQ14>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
                                      static_cast<const unsigned char *>(p.tab_arena),
                                      static_cast<const short2 *>(surv), static_cast<const short2 *>(ref),
                                      static_cast<uint2 *>(out), p.d.flags);
+        timer_end(p, s);
     }
     *launches += 1;
     return cudaGetLastError();

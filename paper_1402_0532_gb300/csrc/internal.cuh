@@ -38,7 +38,7 @@ struct Plan {
     // tables (single-CPI plans)
     float2 *tw32 = nullptr;      // [N]
     short2 *twq = nullptr;       // [N]
-    uint32_t *qtab = nullptr;    // [N/g4 + 1] bf16 hi | lo << 16
+    float2 *ang = nullptr;       // ternary form: two-level (cos, sin) table
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -56,6 +56,10 @@ struct Plan {
     int tune_split = 0;
     int tune_cols = 0;
     int last_launches = 0;
+    // optional timing of the main contraction kernel (event pairs, see ndft_timer_start)
+    mutable cudaEvent_t *tev = nullptr;
+    mutable int tcap = 0;
+    mutable int tcount = 0;
     // ternary GEMM: TMA descriptor storage (host copy + device copy)
     void *tmap_host = nullptr;
     void *tmap_dev = nullptr;
@@ -108,10 +112,22 @@ __device__ __forceinline__ void dev_set_error(int32_t *err, int32_t code) {
     if (err) atomicCAS(err, 0, code);
 }
 
+// Event pair around the main contraction kernel of an exec call (no-ops unless
+// ndft_timer_start armed the plan; recording an event allocates nothing).
+inline void timer_begin(const Plan &p, cudaStream_t s) {
+    if (p.tev && p.tcount < p.tcap) cudaEventRecord(p.tev[2 * p.tcount], s);
+}
+inline void timer_end(const Plan &p, cudaStream_t s) {
+    if (p.tev && p.tcount < p.tcap) {
+        cudaEventRecord(p.tev[2 * p.tcount + 1], s);
+        ++p.tcount;
+    }
+}
+
 // ---- launchers (defined in the .cu files) --------------------------------------
 
 // tables.cu
-cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, uint32_t *qtab, cudaStream_t s);
+cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, cudaStream_t s);
 
 // direct.cu
 cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,

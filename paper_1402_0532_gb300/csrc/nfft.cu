@@ -104,7 +104,9 @@ cudaError_t launch_nfft(const Plan &p, const void *x, void *X, int64_t batch, cu
         const int threads = (V * N / 2) >= 512 ? 512 : (V * N / 2 >= 32 ? V * N / 2 : 32);
         const int64_t blocks = (batch + V - 1) / V;
         if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+        timer_begin(p, s);
         k_nfft_smem<<<(unsigned)blocks, threads, smem, s>>>(xi, Xo, p.tw32, N, logN, V, batch);
+        timer_end(p, s);
         *launches += 1;
         return cudaGetLastError();
     }

@@ -38,7 +38,7 @@ constexpr int32_t kMaxN = 1 << 22;
 void free_plan(Plan &p) {
     cudaFree(p.tw32);
     cudaFree(p.twq);
-    cudaFree(p.qtab);
+    cudaFree(p.ang);
     cudaFree(p.ws);
     cudaFree(p.err);
     cudaFree(p.cpis_dev);
@@ -48,6 +48,10 @@ void free_plan(Plan &p) {
     cudaFree(p.tmap_dev);
     std::free(p.tmap_host);
     delete[] p.cpis_host;
+    if (p.tev) {
+        for (int i = 0; i < 2 * p.tcap; ++i) cudaEventDestroy(p.tev[i]);
+        delete[] p.tev;
+    }
 }
 
 template <class T>
@@ -100,6 +104,7 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
         const bool known = (d->form == 0 || d->form == 1) && (d->prec >= 0 && d->prec <= 2);
         return known ? NDFT_E_UNSUPPORTED : NDFT_E_INVALID;
     }
+    if (d->form == NDFT_FORM_TERNARY_GEMM && !ternary_supported(*d)) return NDFT_E_UNSUPPORTED;
     auto *h = new (std::nothrow) ndft_plan_s();
     if (!h) return NDFT_E_NOMEM;
     Plan &p = h->p;
@@ -112,18 +117,16 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
     const bool tern = p.d.form == NDFT_FORM_TERNARY_GEMM;
     if ((e = alloc(&p.tw32, N)) != cudaSuccess) goto fail;
     if (p.d.prec == NDFT_PREC_Q14 && (e = alloc(&p.twq, N)) != cudaSuccess) goto fail;
-    if (tern && (e = alloc(&p.qtab, N / p.g4 + 1)) != cudaSuccess) goto fail;
     if ((e = alloc(&p.err, 1)) != cudaSuccess) goto fail;
     if ((e = cudaMemsetAsync(p.err, 0, sizeof(int32_t), stream)) != cudaSuccess) goto fail;
-    p.table_bytes = (size_t)N * (sizeof(float2) + (p.twq ? sizeof(short2) : 0)) +
-                    (p.qtab ? (size_t)(N / p.g4 + 1) * 4 : 0);
+    p.table_bytes = (size_t)N * (sizeof(float2) + (p.twq ? sizeof(short2) : 0));
     {
         size_t ws = std::max(direct_ws_bytes(p.d, p.sm_count), backward_ws_bytes(p.d));
         if (tern) ws = std::max(ws, ternary_ws_bytes(p.d, p.sm_count));
         p.ws_bytes = ws;
         if (ws && (e = cudaMalloc(&p.ws, ws)) != cudaSuccess) goto fail;
     }
-    if ((e = launch_tables(N, p.tw32, p.twq, p.qtab, stream)) != cudaSuccess) goto fail;
+    if ((e = launch_tables(N, p.tw32, p.twq, stream)) != cudaSuccess) goto fail;
     if (tern && (e = ternary_plan_init(p, stream)) != cudaSuccess) goto fail;
     *out = h;
     return NDFT_OK;
@@ -225,8 +228,8 @@ ndft_status ndft_get_twiddles(ndft_plan_t plan, int32_t which, void *dst, cudaSt
         src = p.twq;
         bytes = (size_t)N * sizeof(short2);
     } else if (which == 2) {
-        src = p.qtab;
-        bytes = (size_t)(N / p.g4 + 1) * sizeof(uint32_t);
+        src = p.ang;
+        bytes = (size_t)((N - 1) / 256 + 1 + 256) * sizeof(float2);
     } else {
         return NDFT_E_INVALID;
     }
@@ -243,6 +246,49 @@ ndft_status ndft_plan_bytes(ndft_plan_t plan, int64_t *bytes) {
 ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count) {
     if (!plan || !count) return NDFT_E_INVALID;
     *count = plan->p.last_launches;
+    return NDFT_OK;
+}
+
+ndft_status ndft_timer_start(ndft_plan_t plan, int32_t capacity) {
+    if (!plan || capacity < 0 || capacity > (1 << 20)) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    if (p.tev) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i < 2 * p.tcap; ++i) cudaEventDestroy(p.tev[i]);
+        delete[] p.tev;
+        p.tev = nullptr;
+        p.tcap = p.tcount = 0;
+    }
+    if (capacity == 0) return NDFT_OK;
+    p.tev = new (std::nothrow) cudaEvent_t[2 * capacity];
+    if (!p.tev) return NDFT_E_NOMEM;
+    for (int i = 0; i < 2 * capacity; ++i) {
+        if (cudaEventCreate(&p.tev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(p.tev[j]);
+            delete[] p.tev;
+            p.tev = nullptr;
+            return NDFT_E_CUDA;
+        }
+    }
+    p.tcap = capacity;
+    p.tcount = 0;
+    return NDFT_OK;
+}
+
+ndft_status ndft_timer_read(ndft_plan_t plan, double *ms_total, int32_t *count) {
+    if (!plan || !ms_total || !count) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    double tot = 0.0;
+    for (int i = 0; i < p.tcount; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.tev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, p.tev[2 * i], p.tev[2 * i + 1]) != cudaSuccess)
+            return NDFT_E_CUDA;
+        tot += ms;
+    }
+    *ms_total = tot;
+    *count = p.tcount;
+    p.tcount = 0;
     return NDFT_OK;
 }
 
@@ -318,7 +364,7 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
             const CpiDev &q = p.cpis_host[c];
             float2 *t32 = prec == NDFT_PREC_Q14 ? nullptr : static_cast<float2 *>(p.tab_arena) + q.tw_off;
             short2 *tq = prec == NDFT_PREC_Q14 ? static_cast<short2 *>(p.tab_arena) + q.tw_off : nullptr;
-            if ((e = launch_tables(q.n, t32, tq, nullptr, stream)) != cudaSuccess) goto fail;
+            if ((e = launch_tables(q.n, t32, tq, stream)) != cudaSuccess) goto fail;
         }
         // work list: (cpi, bin tile, lag tile), longest CPIs first
         std::vector<int> order(ncpi);

@@ -8,8 +8,7 @@
 
 namespace ndft {
 
-__global__ void k_tables(int N, int g4, float2 *__restrict__ tw32, short2 *__restrict__ twq,
-                         uint32_t *__restrict__ qtab) {
+__global__ void k_tables(int N, float2 *__restrict__ tw32, short2 *__restrict__ twq) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double half_pi = 1.5707963267948966;
     if (m < N) {
@@ -29,22 +28,13 @@ __global__ void k_tables(int N, int g4, float2 *__restrict__ tw32, short2 *__res
         if (tw32) tw32[m] = make_float2(__double2float_rn(wr), __double2float_rn(wi));
         if (twq) twq[m] = make_short2((short)rint(wr * 16384.0), (short)rint(wi * 16384.0));
     }
-    // Quarter-wave table for the tensor-core operand generator: entry j holds
-    // cos((pi/2) j g / N) split into bf16 hi + lo (hi = RN(c), lo = RN(c - hi)).
-    if (qtab && m * g4 <= N) {
-        const double cj = (m * g4 == N) ? 0.0 : cos(half_pi * ((double)(m * g4) / (double)N));
-        const __nv_bfloat16 hi = __double2bfloat16(cj);
-        const __nv_bfloat16 lo = __double2bfloat16(cj - (double)__bfloat162float(hi));
-        qtab[m] = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
-    }
 }
 
-cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, uint32_t *qtab, cudaStream_t s) {
-    const int g4 = (N % 4 == 0) ? 4 : (N % 2 == 0 ? 2 : 1);
-    const int64_t count = (int64_t)N + 1;
+cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, cudaStream_t s) {
+    const int64_t count = N;
     const int threads = 256;
     const int blocks = (int)((count + threads - 1) / threads);
-    k_tables<<<blocks, threads, 0, s>>>(N, g4, tw32, twq, qtab);
+    k_tables<<<blocks, threads, 0, s>>>(N, tw32, twq);
     return cudaGetLastError();
 }
 

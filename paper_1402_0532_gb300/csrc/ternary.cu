@@ -1,14 +1,667 @@
-// ternary.cu -- placeholder until the tensor-core form lands.
+// ternary.cu -- the tensor-core form of the NDFT / nonlinear CAF.
+//
+// Real a (x) b = sgn(a b)(|a| + |b|) equals sgn(b) a + sgn(a) b exactly (both
+// addends are exact), so through Eq. 6 a complex (x) is sigma(a) b + a sigma(b)
+// with sigma(v) = sgn(v_r) + j sgn(v_i).  The NDFT of Eq. 8 (and the CAF of
+// Eq. 12a, the NDFT of each lag product) becomes two dense contractions:
+//     X = S v + F sigma(v),   F[p][i] = W^(p i),   S = sigma(F)  (ternary).
+// As one real GEMM, row 2p (Re X[p]) and row 2p+1 (Im X[p]) of the operand A
+// hold, per sample i, eight K entries that pair with the eight B entries
+//     B = [v_hi_r, v_lo_r, v_hi_i, v_lo_i, s_r, s_r, s_i, s_i]      (s = sigma(v))
+//     A(re) = [S_r, S_r, -S_i, -S_i, F_hi_r, F_lo_r, -F_hi_i, -F_lo_i]
+//     A(im) = [S_i, S_i,  S_r,  S_r, F_hi_i, F_lo_i,  F_hi_r,  F_lo_r]
+// with v = v_hi + v_lo and F = F_hi + F_lo split into bf16 pairs; the ternary
+// entries are exact in bf16 and the products accumulate in fp32 (TMEM).
+//
+// Kernel layout (one persistent CTA per SM, 448 threads):
+//   warp 0      TMA producer: B tiles (256 columns x 64 K) from the packed
+//               buffer, 128-byte swizzle, one mbarrier per stage;
+//   warp 1      TMEM allocator and single-thread tcgen05.mma issuer;
+//   warps 2-9   A producers: generate the 256 x 64 A tile of each stage in
+//               shared memory from a 2-level cos/sin table (the sign pattern
+//               S comes from integer quadrant arithmetic, so its zeros are
+//               exact), then fence.proxy.async and arrive;
+//   warps 10-13 epilogue: tcgen05.ld the two 128 x 256 fp32 accumulators and
+//               store them (coalesced) to the output or split-K partials.
+// Every mbarrier wait is bounded; a timeout records NDFT_E_TIMEOUT in the
+// plan's error word and the CTA drains and exits.
 #include "internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
+
 namespace ndft {
-bool ternary_supported(const ndft_desc &) { return false; }
-size_t ternary_ws_bytes(const ndft_desc &, int) { return 0; }
-cudaError_t ternary_plan_init(Plan &, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_ternary_ndft(Plan &, const void *, void *, int64_t, cudaStream_t, int *) {
-    return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int TM = 256;            // A rows per tile: 128 bins x (re, im)
+constexpr int TN = 256;            // columns per tile
+constexpr int KB = 64;             // bf16 K per stage = 8 samples x 8 entries
+constexpr int STAGES = 3;
+constexpr int A_BYTES = TM * 128;  // 32 KiB
+constexpr int B_BYTES = TN * 128;  // 32 KiB
+constexpr int R_LO = 256;          // angle split r = r_hi * 256 + r_lo
+constexpr int kMaxN = 1 << 18;
+constexpr int kMaxThi = kMaxN / R_LO + 2;
+constexpr int kGenWarps = 8;
+constexpr int kEpiWarp0 = 2 + kGenWarps;  // warps 10..13 -> TMEM lane quarters 2, 3, 0, 1
+constexpr int kThreads = (2 + kGenWarps + 4) * 32;
+constexpr int kMaxSplit = 32;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+constexpr size_t kSmemA = 0;
+constexpr size_t kSmemB = kSmemA + (size_t)STAGES * A_BYTES;
+constexpr size_t kSmemTab = kSmemB + (size_t)STAGES * B_BYTES;
+constexpr size_t kSmemBar = kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2);
+constexpr size_t kSmemTotal = kSmemBar + 128 + 1024;  // barriers, flags, alignment slack
+
+// One problem: the single transform of a plan, or one CPI of a batched plan.
+struct Problem {
+    int32_t N, p0, nbins, ncols;
+    int32_t kblocks, nsplit, mtiles, ntiles;
+    int64_t b_row0;        // first 128-byte row of this problem's packed B
+    float *out;            // output (nsplit == 1) or split-K partials, fp32 view
+    int64_t ld;            // floats per column of out (= 2 * nbins)
+    int64_t split_stride;  // floats between split partials
+    const float2 *ang;     // two-level table: [nth] (r_hi) then [256] (r_lo)
+    int32_t nth;
+    int32_t pad;
+};
+
+struct Unit {
+    int32_t prob, mt, nt, split;
+};
+
+// ---- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-cudaError_t launch_ternary_caf(Plan &, const void *, const void *, int, int, void *, cudaStream_t, int *) {
-    return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the barrier did not complete within kWaitCycles or
+// another role already gave up (abort flag).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int32_t *abort_flag,
+                                          int32_t *err) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            dev_set_error(err, kDevTimeout);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_b(uint32_t dst, const CUtensorMap *map, int32_t row, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+    // K-major, 128-byte swizzle: start >> 4, LBO (unused) = 1, SBO = 1024 B, version 1, layout 2
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16, D fp32, A/B bf16, both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory"); }
+
+// ---- unit decoding -------------------------------------------------------------
+struct Work {
+    Problem P;
+    int mt, nt, kb0, kb1;
+    float *out;
+};
+
+__device__ __forceinline__ Work decode(int64_t u, const Problem &single, const Problem *probs, const Unit *units) {
+    Work w;
+    if (units) {
+        const Unit un = units[u];
+        w.P = probs[un.prob];
+        w.mt = un.mt;
+        w.nt = un.nt;
+        w.kb0 = (int)((int64_t)un.split * w.P.kblocks / w.P.nsplit);
+        w.kb1 = (int)((int64_t)(un.split + 1) * w.P.kblocks / w.P.nsplit);
+        w.out = w.P.out + (int64_t)un.split * w.P.split_stride;
+    } else {
+        w.P = single;
+        const int64_t tiles = (int64_t)single.mtiles * single.ntiles;
+        const int split = (int)(u / tiles);
+        const int64_t t = u - (int64_t)split * tiles;
+        w.mt = (int)(t % single.mtiles);
+        w.nt = (int)(t / single.mtiles);
+        w.kb0 = (int)((int64_t)split * single.kblocks / single.nsplit);
+        w.kb1 = (int)((int64_t)(split + 1) * single.kblocks / single.nsplit);
+        w.out = single.out + (int64_t)split * single.split_stride;
+    }
+    return w;
+}
+
+// ---- A generation: one (bin, sample) pair -> rows 2 pl and 2 pl + 1 ------------
+// u = 4 m, m = (p i) mod N; theta = 2 pi m / N = q pi/2 + a with q = floor(u / N),
+// a = (pi/2) r / N, r = u - q N.  cos a, sin a from the two-level table.
+__device__ __forceinline__ void gen_pair(uint32_t a_stage, int pl, int t, uint32_t u, uint32_t N,
+                                         const float2 *__restrict__ thi, const float2 *__restrict__ tlo) {
+    const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
+    const uint32_t r = u - q * N;
+    const float2 h = thi[r >> 8];
+    const float2 l = tlo[r & (R_LO - 1)];
+    const float c = fmaf(h.x, l.x, -(h.y * l.y));  // cos a >= 0
+    const float s = fmaf(h.y, l.x, h.x * l.y);     // sin a >= 0, 0 only for r = 0
+    // W = cos(theta) - j sin(theta):
+    //   q0: ( c, -s)   q1: (-s, -c)   q2: (-c,  s)   q3: ( s,  c)
+    const bool odd = q & 1u;
+    const float mr = odd ? s : c;
+    const float mi = odd ? c : s;
+    const uint32_t neg_r = (q == 1u || q == 2u) ? 0x80008000u : 0u;
+    const uint32_t neg_i = (q <= 1u) ? 0x80008000u : 0u;
+    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(mr, mi);
+    const float hr = __low2float(hi2), hii = __high2float(hi2);
+    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(mr - hr, mi - hii);
+    const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi2);
+    const uint32_t ul = *reinterpret_cast<const uint32_t *>(&lo2);
+    const uint32_t wr = __byte_perm(uh, ul, 0x5410) ^ neg_r;  // [F_hi_r, F_lo_r]
+    const uint32_t wi = __byte_perm(uh, ul, 0x7632) ^ neg_i;  // [F_hi_i, F_lo_i]
+    // ternary sign pattern, exact: 0 where the magnitude is exactly 0
+    const uint32_t sr = (mr == 0.f) ? 0u : (0x3F803F80u ^ neg_r);  // [S_r, S_r]
+    const uint32_t si = (mi == 0.f) ? 0u : (0x3F803F80u ^ neg_i);  // [S_i, S_i]
+    const uint32_t row_re = 2u * pl, row_im = row_re + 1u;
+    const uint32_t base_re = a_stage + row_re * 128u + (((uint32_t)t ^ (row_re & 7u)) << 4);
+    const uint32_t base_im = a_stage + row_im * 128u + (((uint32_t)t ^ (row_im & 7u)) << 4);
+    sts128(base_re, sr, si ^ 0x80008000u, wr, wi ^ 0x80008000u);
+    sts128(base_im, si, sr, wi, wr);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, Problem single, const Problem *__restrict__ probs,
+                   const Unit *__restrict__ units, int64_t nunits, int32_t *err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float2 *s_thi = reinterpret_cast<float2 *>(smem + kSmemTab);
+    float2 *s_tlo = s_thi + kMaxThi;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSmemBar);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *tmem_empty = tmem_full + 1;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tmem_empty + 1);
+    volatile int32_t *s_abort = reinterpret_cast<volatile int32_t *>(s_tmem + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t a_base = smem_u32(smem + kSmemA), b_base = smem_u32(smem + kSmemB);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1 + kGenWarps);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tmem_full, 1);
+        mbar_init(tmem_empty, 4);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                    mbar_arrive_tx(&full[stage], B_BYTES);
+                    const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN;
+                    tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, tphase = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
+                if (!(ok = mbar_wait(tmem_empty, tphase ^ 1u, s_abort, err))) break;
+                tc_fence_after();
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!(ok = mbar_wait(&full[stage], phase, s_abort, err))) break;
+                    tc_fence_after();
+                    const uint32_t a_st = a_base + stage * A_BYTES, b_st = b_base + stage * B_BYTES;
+#pragma unroll
+                    for (int k = 0; k < KB / 16; ++k) {
+                        const uint64_t bd = umma_desc(b_st + k * 32);
+                        const uint32_t acc = (kb > w.kb0 || k > 0) ? 1u : 0u;
+                        umma(tmem, umma_desc(a_st + k * 32), bd, acc);
+                        umma(tmem + TN, umma_desc(a_st + 128 * 128 + k * 32), bd, acc);
+                    }
+                    umma_commit(&empty[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(tmem_full);
+                tphase ^= 1u;
+            }
+        }
+        __syncwarp();
+    } else if (warp < kEpiWarp0) {
+        // ---------------- A producers ----------------
+        const int g = threadIdx.x - 64;  // 0..255
+        const int t = g & 7, pg = g >> 3;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const Work w = decode(u, single, probs, units);
+            gen_bar();  // every producer is done with the previous table
+            for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
+                const float2 v = w.P.ang[e];
+                if (e < w.P.nth) s_thi[e] = v;
+                else s_tlo[e - w.P.nth] = v;
+            }
+            gen_bar();
+            if (!ok) continue;
+            const uint32_t N = (uint32_t)w.P.N;
+            uint32_t uu[4], dd[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = w.mt * (TM / 2) + pg + 32 * j;  // bin index
+                int64_t pm = ((int64_t)w.P.p0 + k) % (int64_t)N;
+                if (pm < 0) pm += N;
+                const int64_t i0 = (int64_t)w.kb0 * 8 + t;
+                uu[j] = 4u * (uint32_t)((pm * (i0 % (int64_t)N)) % (int64_t)N);
+                dd[j] = 4u * (uint32_t)((8 * pm) % (int64_t)N);
+            }
+            for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                const uint32_t a_st = a_base + stage * A_BYTES;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    gen_pair(a_st, pg + 32 * j, t, uu[j], N, s_thi, s_tlo);
+                    uu[j] += dd[j];
+                    if (uu[j] >= 4u * N) uu[j] -= 4u * N;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[stage]);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;
+        uint32_t tphase = 0;
+        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const Work w = decode(u, single, probs, units);
+            if (!mbar_wait(tmem_full, tphase, s_abort, err)) break;
+            tc_fence_after();
+            const int64_t limit_m = 2LL * w.P.nbins;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int64_t m = (int64_t)w.mt * TM + 128 * h + 32 * quarter + lane;
+#pragma unroll 1
+                for (int c0 = 0; c0 < TN; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(h * TN + c0), r);
+                    tmem_wait_ld();
+                    const int64_t col0 = (int64_t)w.nt * TN + c0;
+                    if (m < limit_m) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < w.P.ncols) w.out[(col0 + j) * w.P.ld + m] = __uint_as_float(r[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_empty);
+            tphase ^= 1u;
+        }
+    }
+
+    __syncthreads();
+    if (*s_abort) {
+        // give any copy or MMA still in flight time to land before the memory goes away
+        const long long t0 = clock64();
+        while (clock64() - t0 < 200000) {
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// ---- packing of the B operand ------------------------------------------------------
+// Row (kb, col) of the packed buffer holds samples i = 8 kb .. 8 kb + 7 of column
+// col, 16 bytes each: [v_hi_r, v_lo_r, v_hi_i, v_lo_i, s_r, s_r, s_i, s_i] (bf16).
+__device__ __forceinline__ uint4 pack_entry(float2 v) {
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x - __low2float(hi), v.y - __high2float(hi));
+    const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi);
+    const uint32_t ul = *reinterpret_cast<const uint32_t *>(&lo);
+    const uint32_t sr = (v.x > 0.f) ? 0x3F803F80u : ((v.x < 0.f) ? 0xBF80BF80u : 0u);
+    const uint32_t si = (v.y > 0.f) ? 0x3F803F80u : ((v.y < 0.f) ? 0xBF80BF80u : 0u);
+    return make_uint4(__byte_perm(uh, ul, 0x5410), __byte_perm(uh, ul, 0x7632), sr, si);
+}
+
+struct PackProb {
+    const float2 *a;  // x (NDFT) or s_surv (CAF)
+    const float2 *r;  // s_ref (CAF) or null
+    int32_t N, lag0, ncols, kblocks;
+    int64_t ldx;      // row stride of x
+    int64_t row0;     // first packed row
+};
+
+__device__ __forceinline__ float2 lag_product(const PackProb &P, int64_t col, int64_t i, uint32_t flags) {
+    int64_t j = i - (P.lag0 + col);
+    float2 ref = make_float2(0.f, 0.f);
+    if (flags & NDFT_F_CIRCULAR_LAG) {
+        j %= P.N;
+        if (j < 0) j += P.N;
+    }
+    if (j >= 0 && j < P.N) {
+        ref = P.r[j];
+        if (!(flags & NDFT_F_NO_CONJ_REF)) ref.y = -ref.y;
+    }
+    return cox_f32(P.a[i], ref);
+}
+
+// Packs nprob problems; thread e handles entry t = e & 7 of row e >> 3 of the
+// problem that row falls in (prefix[] holds each problem's first flat row).
+__global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__restrict__ prefix, int nprob,
+                       PackProb single, int64_t total_rows, uint32_t flags, bool caf, uint4 *__restrict__ B) {
+    const int64_t total = total_rows * 8;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e & 7);
+        const int64_t frow = e >> 3;
+        PackProb P = single;
+        int64_t local = frow;
+        if (probs) {
+            int lo = 0, hi = nprob - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= frow) lo = mid;
+                else hi = mid - 1;
+            }
+            P = probs[lo];
+            local = frow - prefix[lo];
+        }
+        const int64_t kb = local / P.ncols;
+        const int64_t col = local - kb * P.ncols;
+        const int64_t i = kb * 8 + t;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < P.N) v = caf ? lag_product(P, col, i, flags) : P.a[col * P.ldx + i];
+        B[(P.row0 + local) * 8 + t] = pack_entry(v);
+    }
+}
+
+// Two-level angle table: entry j < nth is (cos, sin)((pi/2) 256 j / N), entry
+// nth + j (j < 256) is (cos, sin)((pi/2) j / N); fp64, rounded to fp32.
+__global__ void k_angles(int N, int nth, float2 *__restrict__ ang) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nth + R_LO) return;
+    const int64_t r = e < nth ? (int64_t)e * R_LO : (int64_t)(e - nth);
+    const double a = 1.5707963267948966 * ((double)r / (double)N);
+    ang[e] = (r == 0) ? make_float2(1.f, 0.f) : make_float2(__double2float_rn(cos(a)), __double2float_rn(sin(a)));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+cudaError_t make_tmap(void *base, int64_t rows, CUtensorMap *map) {
+    auto enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {128};
+    cuuint32_t box[2] = {64, (cuuint32_t)TN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int nth_for(int N) { return (N - 1) / R_LO + 1; }
+
+int max_cols(const ndft_desc &d) { return (int)std::max<int64_t>(d.max_lags, d.max_batch); }
+
+// Splits along the sample axis: none when the tiles alone fill two waves;
+// otherwise between 2 and 4 waves of units, preferring a whole number of
+// waves.  split * tiles <= 4 * sm bounds the partials buffer.
+int choose_split(int64_t tiles, int kblocks, int sm, int tune) {
+    const int cap = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (4LL * sm) / tiles));
+    int s;
+    if (tune > 0) {
+        s = std::min(tune, cap);
+    } else if (tiles >= 2LL * sm) {
+        s = 1;
+    } else {
+        const int lo = (int)std::min<int64_t>((2LL * sm + tiles - 1) / tiles, cap);
+        s = lo;
+        for (int c = lo; c <= cap; ++c)
+            if ((tiles * c) % sm == 0) {
+                s = c;
+                break;
+            }
+    }
+    return std::max(1, std::min(s, std::max(1, kblocks / 4)));
+}
+
+cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob, const PackProb &single,
+                        int64_t rows, uint32_t flags, bool caf, void *B, int sm, cudaStream_t s) {
+    const int threads = 256;
+    const int64_t want = (rows * 8 + threads - 1) / threads;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)sm * 32);
+    k_pack<<<std::max(blocks, 1), threads, 0, s>>>(probs, prefix, nprob, single, rows, flags, caf,
+                                                   static_cast<uint4 *>(B));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
+                        int64_t nunits, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
+    const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
+    timer_begin(p, s);
+    k_ternary_gemm<<<grid, kThreads, kSmemTotal, s>>>(*map, single, probs, units, nunits, p.err);
+    timer_end(p, s);
+    return cudaGetLastError();
+}
+
+struct TernLayout {
+    int kblocks;
+    int64_t b_rows;
+    size_t b_bytes;
+    size_t part_bytes;
+};
+
+TernLayout layout_for(const ndft_desc &d, int sm) {
+    TernLayout L;
+    L.kblocks = (d.n + 7) / 8;
+    const int cols = max_cols(d);
+    L.b_rows = (int64_t)L.kblocks * cols;
+    L.b_bytes = (size_t)L.b_rows * 128;
+    L.part_bytes = (size_t)4 * sm * TM * TN * sizeof(float);  // split * tiles <= 4 sm
+    return L;
+}
+
+}  // namespace
+
+bool ternary_supported(const ndft_desc &d) {
+    return d.form == NDFT_FORM_TERNARY_GEMM && d.prec == NDFT_PREC_BF16X2 && d.n >= 1 && d.n <= kMaxN;
+}
+
+size_t ternary_ws_bytes(const ndft_desc &d, int sm) {
+    if (!ternary_supported(d)) return 0;
+    const TernLayout L = layout_for(d, sm);
+    return L.b_bytes + L.part_bytes;
+}
+
+cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
+    if (!ternary_supported(p.d)) return cudaErrorNotSupported;
+    const int N = p.d.n;
+    const int nth = nth_for(N);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p.ang, (size_t)(nth + R_LO) * sizeof(float2))) != cudaSuccess) return e;
+    p.table_bytes += (size_t)(nth + R_LO) * sizeof(float2);
+    k_angles<<<(nth + R_LO + 255) / 256, 256, 0, s>>>(N, nth, p.ang);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const TernLayout L = layout_for(p.d, p.sm_count);
+    p.b_bytes = L.b_bytes;
+    p.part_bytes = L.part_bytes;
+    p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));  // CUtensorMap wants 64-byte alignment
+    if (!p.tmap_host) return cudaErrorMemoryAllocation;
+    return make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host));
+}
+
+static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, void *out, cudaStream_t s,
+                              int *launches) {
+    const int N = p.d.n, nb = p.d.nbins;
+    const TernLayout L = layout_for(p.d, p.sm_count);
+    cudaError_t e = launch_pack(nullptr, nullptr, 0, pp, (int64_t)L.kblocks * ncols, p.d.flags, caf, p.ws, p.sm_count, s);
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    Problem P{};
+    P.N = N;
+    P.p0 = p.d.p0;
+    P.nbins = nb;
+    P.ncols = ncols;
+    P.kblocks = L.kblocks;
+    P.mtiles = (2 * nb + TM - 1) / TM;
+    P.ntiles = (ncols + TN - 1) / TN;
+    P.nsplit = choose_split((int64_t)P.mtiles * P.ntiles, L.kblocks, p.sm_count, p.tune_split);
+    P.b_row0 = 0;
+    P.ld = 2LL * nb;
+    P.split_stride = (int64_t)ncols * 2 * nb;
+    P.ang = p.ang;
+    P.nth = nth_for(N);
+    float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + L.b_bytes);
+    P.out = P.nsplit == 1 ? static_cast<float *>(out) : part;
+    const int64_t nunits = (int64_t)P.mtiles * P.ntiles * P.nsplit;
+    if ((e = launch_gemm(p, P, nullptr, nullptr, nunits, s)) != cudaSuccess) return e;
+    *launches += 1;
+    if (P.nsplit > 1) {
+        *launches += 1;
+        return launch_reduce_splits(part, P.nsplit, (int64_t)ncols * 2 * nb, static_cast<float *>(out), s);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_ternary_ndft(Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s, int *launches) {
+    PackProb pp{};
+    pp.a = static_cast<const float2 *>(x);
+    pp.N = p.d.n;
+    pp.ncols = (int)batch;
+    pp.kblocks = (p.d.n + 7) / 8;
+    pp.ldx = p.d.n;
+    return run_single(p, pp, false, (int)batch, X, s, launches);
+}
+
+cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags, void *A,
+                               cudaStream_t s, int *launches) {
+    PackProb pp{};
+    pp.a = static_cast<const float2 *>(s_surv);
+    pp.r = static_cast<const float2 *>(s_ref);
+    pp.N = p.d.n;
+    pp.lag0 = lag0;
+    pp.ncols = nlags;
+    pp.kblocks = (p.d.n + 7) / 8;
+    return run_single(p, pp, true, nlags, A, s, launches);
+}
+
 }  // namespace ndft

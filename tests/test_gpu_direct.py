@@ -45,21 +45,6 @@ def test_tables_match_oracle(api, N):
     assert np.array_equal(q.twiddles(1).cpu().numpy(), oracle.twiddle_table_q14(N))
 
 
-def test_ternary_quarter_table(api):
-    """bf16 hi/lo quarter table: hi + lo within 2^-16 of cos, exact axis values."""
-    N = 1024
-    p = api.Plan(N, max_lags=1, form="ternary", prec="bf16x2")
-    t = p.twiddles(2).cpu().numpy().view(np.uint32)
-    hi = (t & 0xFFFF).astype(np.uint32) << 16
-    lo = (t >> 16).astype(np.uint32) << 16
-    v = hi.view(np.float32).astype(np.float64) + lo.view(np.float32).astype(np.float64)
-    j = np.arange(N // 4 + 1)
-    want = np.cos(np.pi / 2 * (4 * j) / N)
-    want[-1] = 0.0
-    assert np.max(np.abs(v - want)) < 2.0 ** -16
-    assert v[0] == 1.0 and v[-1] == 0.0
-
-
 # --------------------------------------------------------------------------------
 # NDFT, Eq. 8
 # --------------------------------------------------------------------------------

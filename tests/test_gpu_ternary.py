@@ -1,0 +1,116 @@
+"""GPU parity of the tensor-core (ternary GEMM) form against the CPU oracle.
+
+The form computes X = S v + F sigma(v) with bf16 hi+lo operands and fp32
+accumulation; the bar is the fp32 one, 1e-5 of max |X| (against the oracle
+with the lag product formed in fp32, the element-wise stage both forms share)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0532_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_0532_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
+
+
+def test_ternary_small_ndft(api):
+    rng = np.random.default_rng(40)
+    x = scenes.cn(rng, (300, 64)).astype(np.complex64)
+    p = api.Plan(64, max_batch=300, form="ternary", prec="bf16x2")
+    got = p.ndft(dev(x)).cpu().numpy()
+    p.query_error()
+    ref = oracle.ndft(x.astype(np.complex128))
+    assert relerr(got, ref) < TOL
+
+
+def test_ternary_angle_table(api):
+    N = 65536
+    p = api.Plan(N, max_lags=1, form="ternary", prec="bf16x2")
+    t = p.twiddles(2).cpu().numpy()
+    nth = (N - 1) // 256 + 1
+    a = np.concatenate([np.pi / 2 * (256 * np.arange(nth)) / N, np.pi / 2 * np.arange(256) / N])
+    assert np.max(np.abs(t.real - np.cos(a))) < 1e-7 and np.max(np.abs(t.imag - np.sin(a))) < 1e-7
+    assert t[0] == 1 and t[nth] == 1
+
+
+@pytest.mark.parametrize("N,batch,p0,nbins", [(100, 130, -7, 77), (1024, 600, 0, 0), (9, 5, 2, 5), (1, 4, 0, 1)])
+def test_ternary_ndft_ragged(api, N, batch, p0, nbins):
+    rng = np.random.default_rng(41 + N)
+    x = scenes.cn(rng, (batch, N)).astype(np.complex64)
+    x[:, ::7] = 0
+    nb = nbins or N
+    ref = oracle.ndft(x.astype(np.complex128), p0=p0, nbins=nb)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="ternary", prec="bf16x2")
+    got = p.ndft(dev(x)).cpu().numpy()
+    p.query_error()
+    assert relerr(got, ref) < TOL
+
+
+def test_ternary_tone_batch_peak(api):
+    x = scenes.tone_batch()
+    ref = oracle.ndft(x.astype(np.complex128))
+    p = api.Plan(64, max_batch=4096, form="ternary", prec="bf16x2")
+    X = p.ndft(dev(x))
+    got = X.cpu().numpy()
+    per = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    assert per.max() < TOL
+    idx, _ = api.argmax(X)
+    assert int(idx[0]) == 7
+
+
+def test_ternary_caf(api):
+    sc = scenes.radar_scene(N=4133, nlags=100, nbins=96, seed=31)
+    ref = oracle.caf(sc.s_surv, sc.s_ref, -3, 100, sc.p0, 96, z32=True)
+    p = api.Plan(sc.N, p0=sc.p0, nbins=96, max_lags=128, form="ternary", prec="bf16x2")
+    got = p.caf(dev(sc.s_surv), dev(sc.s_ref), -3, 100).cpu().numpy()
+    p.query_error()
+    assert relerr(got, ref) < TOL
+
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_ternary_caf_flags(api, flags):
+    sc = scenes.radar_scene(N=700, nlags=40, nbins=33, seed=32)
+    ref = oracle.caf(sc.s_surv, sc.s_ref, 650, 40, -16, 33, flags=flags, z32=True)
+    p = api.Plan(sc.N, p0=-16, nbins=33, max_lags=40, flags=flags, form="ternary", prec="bf16x2")
+    got = p.caf(dev(sc.s_surv), dev(sc.s_ref), 650, 40).cpu().numpy()
+    assert relerr(got, ref) < TOL
+
+
+def test_ternary_caf_split_k_sampled(api):
+    """A long sample axis (split into many K ranges) on sampled cells."""
+    sc = scenes.radar_scene(N=16384, nlags=300, nbins=256, seed=42)
+    p = api.Plan(sc.N, p0=sc.p0, nbins=256, max_lags=300, form="ternary", prec="bf16x2")
+    A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 300)
+    got = A.cpu().numpy()
+    p.query_error()
+    rng = np.random.default_rng(43)
+    lags = np.concatenate([[0, 37, 120, 299], rng.integers(0, 300, 60)])
+    bins = np.concatenate([[0, 5, -12, 127], rng.integers(-128, 128, 60)])
+    ref = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
+    peak = abs(oracle.caf_cells(sc.s_surv, sc.s_ref, [0], [0], z32=True)[0])
+    err = np.max(np.abs(got[lags, bins - sc.p0] - ref))
+    assert err / peak < TOL
+    # the direct form agrees too
+    pd = api.Plan(sc.N, p0=sc.p0, nbins=256, max_lags=300)
+    Ad = pd.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 300).cpu().numpy()
+    assert np.max(np.abs(Ad - got)) / peak < 2 * TOL
