@@ -180,9 +180,11 @@ ndft_status ndft_plan_bytes(ndft_plan_t plan, int64_t *bytes);
 ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
 
 /* Tile / split choice for the plan's kernels: key 0 = split count along the
- * sample axis (0 = automatic), key 1 = ternary-GEMM columns per tile (128 or
- * 256; 0 = automatic).  Used by the autotuner; affects speed, not results
- * beyond fp32 summation order. */
+ * sample axis (0 = automatic), key 1 = ternary-GEMM rows per tile (256: one
+ * tensor-memory accumulator pair, the default; 128: two accumulators used in
+ * turn), key 2 = ternary-GEMM K blocks (8 samples each) per
+ * tensor-memory accumulation chain before it is folded into the fp32 result
+ * (0 = 64).  Used by the autotuner; affects speed and fp32 rounding only. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
 
 /* Device timing of the plan's main contraction kernel (the tensor-core GEMM,
@@ -199,6 +201,10 @@ const char *ndft_status_string(ndft_status s);
 
 /* Library version as an integer (major * 10000 + minor * 100 + patch). */
 int32_t ndft_version(void);
+
+/* Text of the last CUDA error behind an NDFT_E_CUDA / NDFT_E_NOMEM status
+ * returned on the calling host thread ("no error" if none); static storage. */
+const char *ndft_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ F_NO_CONJ_REF, F_CIRCULAR_LAG = 0x1, 0x2
 EXPORTS = ("ndft_plan", "ndft_plan_batched", "ndft_plan_destroy", "ndft_exec", "nfft_exec", "caf_exec",
            "caf_exec_batched", "caf_backward", "ndft_argmax", "ndft_query_error", "ndft_get_twiddles",
            "ndft_plan_bytes", "ndft_last_launches", "ndft_set_tuning", "ndft_timer_start", "ndft_timer_read",
-           "ndft_status_string", "ndft_version")
+           "ndft_status_string", "ndft_version", "ndft_last_cuda_error")
 
 
 class NdftDesc(ctypes.Structure):
@@ -38,7 +38,10 @@ class NdftCpi(ctypes.Structure):
 class NdftError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        extra = ""
+        if status in (E_CUDA, E_NOMEM) and _lib is not None:
+            extra = f": {_lib.ndft_last_cuda_error().decode()}"
+        super().__init__(f"{what}: {status_string(status)} (status {status}){extra}")
 
 
 _lib = None
@@ -73,6 +76,7 @@ def load() -> ctypes.CDLL:
         "ndft_timer_read": (i32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]),
         "ndft_status_string": (ctypes.c_char_p, [i32]),
         "ndft_version": (i32, []),
+        "ndft_last_cuda_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

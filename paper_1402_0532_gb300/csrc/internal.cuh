@@ -55,6 +55,7 @@ struct Plan {
     // tuning
     int tune_split = 0;
     int tune_cols = 0;
+    int tune_chunk = 0;          // ternary form: K blocks per TMEM accumulation chain
     int last_launches = 0;
     // optional timing of the main contraction kernel (event pairs, see ndft_timer_start)
     mutable cudaEvent_t *tev = nullptr;

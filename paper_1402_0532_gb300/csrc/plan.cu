@@ -18,8 +18,11 @@ namespace {
 
 bool aligned16(const void *ptr) { return ptr && ((uintptr_t)ptr & 15u) == 0; }
 
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
 ndft_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return NDFT_OK;
+    g_last_cuda = e;
     if (e == cudaErrorMemoryAllocation) return NDFT_E_NOMEM;
     return NDFT_E_CUDA;
 }
@@ -91,6 +94,8 @@ const char *ndft_status_string(ndft_status s) {
 }
 
 int32_t ndft_version(void) { return 100; }
+
+const char *ndft_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
 
 ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream) {
     if (!out || !d) return NDFT_E_INVALID;
@@ -300,6 +305,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
     } else if (key == 1) {
         if (value != 0 && value != 128 && value != 256) return NDFT_E_INVALID;
         plan->p.tune_cols = value;
+    } else if (key == 2) {
+        if (value > 1 << 20) return NDFT_E_INVALID;
+        plan->p.tune_chunk = value;
     } else {
         return NDFT_E_INVALID;
     }

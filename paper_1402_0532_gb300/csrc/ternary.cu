@@ -37,11 +37,8 @@ namespace ndft {
 
 namespace {
 
-constexpr int TM = 256;            // A rows per tile: 128 bins x (re, im)
 constexpr int TN = 256;            // columns per tile
 constexpr int KB = 64;             // bf16 K per stage = 8 samples x 8 entries
-constexpr int STAGES = 3;
-constexpr int A_BYTES = TM * 128;  // 32 KiB
 constexpr int B_BYTES = TN * 128;  // 32 KiB
 constexpr int R_LO = 256;          // angle split r = r_hi * 256 + r_lo
 constexpr int kMaxN = 1 << 18;
@@ -50,13 +47,9 @@ constexpr int kGenWarps = 8;
 constexpr int kEpiWarp0 = 2 + kGenWarps;  // warps 10..13 -> TMEM lane quarters 2, 3, 0, 1
 constexpr int kThreads = (2 + kGenWarps + 4) * 32;
 constexpr int kMaxSplit = 32;
+constexpr int kChunk = 64;  // K blocks per TMEM accumulation chain (512 samples)
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
-constexpr size_t kSmemA = 0;
-constexpr size_t kSmemB = kSmemA + (size_t)STAGES * A_BYTES;
-constexpr size_t kSmemTab = kSmemB + (size_t)STAGES * B_BYTES;
-constexpr size_t kSmemBar = kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2);
-constexpr size_t kSmemTotal = kSmemBar + 128 + 1024;  // barriers, flags, alignment slack
 
 // One problem: the single transform of a plan, or one CPI of a batched plan.
 struct Problem {
@@ -163,6 +156,10 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
+__device__ __forceinline__ void red_add_f32(float *addr, float v) {
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(addr), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory"); }
 
 // ---- unit decoding -------------------------------------------------------------
@@ -231,31 +228,54 @@ __device__ __forceinline__ void gen_pair(uint32_t a_stage, int pl, int t, uint32
     sts128(base_im, si, sr, wi, wr);
 }
 
+// MH row halves of 128 rows per tile.  MH = 2: 256 x 256 tile, one TMEM
+// accumulator pair (all 512 columns), the MMA waits while a finished chain is
+// folded out.  MH = 1: 128 x 256 tile, two 256-column accumulators used in
+// turn, so the fold of one chain overlaps the MMAs of the next.
+template <int MH>
+struct Tile {
+    static constexpr int kRows = 128 * MH;
+    static constexpr int kABytes = kRows * 128;
+    static constexpr int kStages = MH == 1 ? 4 : 3;
+    static constexpr int kBufs = MH == 1 ? 2 : 1;
+    static constexpr size_t kSmemA = 0;
+    static constexpr size_t kSmemB = kSmemA + (size_t)kStages * kABytes;
+    static constexpr size_t kSmemTab = kSmemB + (size_t)kStages * B_BYTES;
+    static constexpr size_t kSmemBar = kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2);
+    static constexpr size_t kSmemTotal = kSmemBar + 160 + 1024;  // barriers, flags, alignment slack
+};
+
+template <int MH>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, Problem single, const Problem *__restrict__ probs,
-                   const Unit *__restrict__ units, int64_t nunits, int32_t *err) {
+                   const Unit *__restrict__ units, int64_t nunits, int chunk, int32_t *err) {
+    using T = Tile<MH>;
+    constexpr int STG = T::kStages;
+    constexpr int NB = T::kBufs;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    float2 *s_thi = reinterpret_cast<float2 *>(smem + kSmemTab);
+    float2 *s_thi = reinterpret_cast<float2 *>(smem + T::kSmemTab);
     float2 *s_tlo = s_thi + kMaxThi;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSmemBar);
-    uint64_t *empty = full + STAGES;
-    uint64_t *tmem_full = empty + STAGES;
-    uint64_t *tmem_empty = tmem_full + 1;
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tmem_empty + 1);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + T::kSmemBar);
+    uint64_t *empty = full + STG;
+    uint64_t *tmem_full = empty + STG;    // [NB]
+    uint64_t *tmem_empty = tmem_full + NB;  // [NB]
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tmem_empty + NB);
     volatile int32_t *s_abort = reinterpret_cast<volatile int32_t *>(s_tmem + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t a_base = smem_u32(smem + kSmemA), b_base = smem_u32(smem + kSmemB);
+    const uint32_t a_base = smem_u32(smem + T::kSmemA), b_base = smem_u32(smem + T::kSmemB);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < STG; ++s) {
             mbar_init(&full[s], 1 + kGenWarps);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(tmem_full, 1);
-        mbar_init(tmem_empty, 4);
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&tmem_full[b], 1);
+            mbar_init(&tmem_empty[b], 4);
+        }
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive_tx(&full[stage], B_BYTES);
                     const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN;
                     tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
-                    if (++stage == STAGES) {
+                    if (++stage == STG) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -295,37 +315,45 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0, tphase = 0;
+            uint32_t phase = 0, chain = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 const Work w = decode(u, single, probs, units);
-                if (!(ok = mbar_wait(tmem_empty, tphase ^ 1u, s_abort, err))) break;
-                tc_fence_after();
-                for (int kb = w.kb0; kb < w.kb1; ++kb) {
-                    if (!(ok = mbar_wait(&full[stage], phase, s_abort, err))) break;
+                // one accumulation chain per chunk of `chunk` K blocks; the epilogue
+                // folds each chain into the destination in fp32 (round to nearest)
+                for (int c0 = w.kb0; c0 < w.kb1 && ok; c0 += chunk, ++chain) {
+                    const int c1 = min(c0 + chunk, w.kb1);
+                    const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
+                    if (!(ok = mbar_wait(&tmem_empty[buf], tpar ^ 1u, s_abort, err))) break;
                     tc_fence_after();
-                    const uint32_t a_st = a_base + stage * A_BYTES, b_st = b_base + stage * B_BYTES;
+                    const uint32_t d0 = tmem + buf * (uint32_t)TN;
+                    for (int kb = c0; kb < c1; ++kb) {
+                        if (!(ok = mbar_wait(&full[stage], phase, s_abort, err))) break;
+                        tc_fence_after();
+                        const uint32_t a_st = a_base + stage * T::kABytes, b_st = b_base + stage * B_BYTES;
 #pragma unroll
-                    for (int k = 0; k < KB / 16; ++k) {
-                        const uint64_t bd = umma_desc(b_st + k * 32);
-                        const uint32_t acc = (kb > w.kb0 || k > 0) ? 1u : 0u;
-                        umma(tmem, umma_desc(a_st + k * 32), bd, acc);
-                        umma(tmem + TN, umma_desc(a_st + 128 * 128 + k * 32), bd, acc);
+                        for (int k = 0; k < KB / 16; ++k) {
+                            const uint64_t bd = umma_desc(b_st + k * 32);
+                            const uint32_t acc = (kb > c0 || k > 0) ? 1u : 0u;
+#pragma unroll
+                            for (int h = 0; h < MH; ++h)
+                                umma(d0 + h * TN, umma_desc(a_st + h * 128 * 128 + k * 32), bd, acc);
+                        }
+                        umma_commit(&empty[stage]);
+                        if (++stage == STG) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    umma_commit(&empty[stage]);
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
+                    if (!ok) break;
+                    umma_commit(&tmem_full[buf]);
                 }
-                if (!ok) break;
-                umma_commit(tmem_full);
-                tphase ^= 1u;
             }
         }
         __syncwarp();
     } else if (warp < kEpiWarp0) {
         // ---------------- A producers ----------------
+        constexpr int PPT = 2 * MH;      // (bin, sample) pairs per thread per K block
         const int g = threadIdx.x - 64;  // 0..255
         const int t = g & 7, pg = g >> 3;
         int stage = 0;
@@ -342,10 +370,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             gen_bar();
             if (!ok) continue;
             const uint32_t N = (uint32_t)w.P.N;
-            uint32_t uu[4], dd[4];
+            uint32_t uu[PPT], dd[PPT];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int k = w.mt * (TM / 2) + pg + 32 * j;  // bin index
+            for (int j = 0; j < PPT; ++j) {
+                const int k = w.mt * (T::kRows / 2) + pg + 32 * j;  // bin index
                 int64_t pm = ((int64_t)w.P.p0 + k) % (int64_t)N;
                 if (pm < 0) pm += N;
                 const int64_t i0 = (int64_t)w.kb0 * 8 + t;
@@ -354,9 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             for (int kb = w.kb0; kb < w.kb1; ++kb) {
                 if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
-                const uint32_t a_st = a_base + stage * A_BYTES;
+                const uint32_t a_st = a_base + stage * T::kABytes;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < PPT; ++j) {
                     gen_pair(a_st, pg + 32 * j, t, uu[j], N, s_thi, s_tlo);
                     uu[j] += dd[j];
                     if (uu[j] >= 4u * N) uu[j] -= 4u * N;
@@ -364,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[stage]);
-                if (++stage == STAGES) {
+                if (++stage == STG) {
                     stage = 0;
                     phase ^= 1u;
                 }
@@ -373,32 +401,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
-        uint32_t tphase = 0;
-        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        uint32_t chain = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             const Work w = decode(u, single, probs, units);
-            if (!mbar_wait(tmem_full, tphase, s_abort, err)) break;
-            tc_fence_after();
             const int64_t limit_m = 2LL * w.P.nbins;
+            for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
+                const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
+                if (!(ok = mbar_wait(&tmem_full[buf], tpar, s_abort, err))) break;
+                tc_fence_after();
+                // the first chain of a unit stores; later chains are added in L2 with
+                // fire-and-forget reductions (round to nearest).  Each address is
+                // written by one thread only, in chain order, so the sum is
+                // deterministic.
+                const bool first = (c0 == w.kb0);
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int64_t m = (int64_t)w.mt * TM + 128 * h + 32 * quarter + lane;
+                for (int h = 0; h < MH; ++h) {
+                    const int64_t m = (int64_t)w.mt * T::kRows + 128 * h + 32 * quarter + lane;
 #pragma unroll 1
-                for (int c0 = 0; c0 < TN; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(h * TN + c0), r);
-                    tmem_wait_ld();
-                    const int64_t col0 = (int64_t)w.nt * TN + c0;
-                    if (m < limit_m) {
+                    for (int cc = 0; cc < TN; cc += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf + h) * TN + cc), r);
+                        tmem_wait_ld();
+                        const int64_t col0 = (int64_t)w.nt * TN + cc;
+                        if (m < limit_m) {
+                            float *dst = w.out + col0 * w.P.ld + m;
+                            const int64_t left = w.P.ncols - col0;
+                            const int nj = left < 32 ? (int)left : 32;
+                            if (first) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (col0 + j < w.P.ncols) w.out[(col0 + j) * w.P.ld + m] = __uint_as_float(r[j]);
+                                for (int j = 0; j < 32; ++j)
+                                    if (j < nj) dst[j * w.P.ld] = __uint_as_float(r[j]);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 32; ++j)
+                                    if (j < nj) red_add_f32(dst + j * w.P.ld, __uint_as_float(r[j]));
+                            }
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tmem_empty[buf]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tmem_empty);
-            tphase ^= 1u;
         }
     }
 
@@ -520,10 +565,11 @@ int nth_for(int N) { return (N - 1) / R_LO + 1; }
 int max_cols(const ndft_desc &d) { return (int)std::max<int64_t>(d.max_lags, d.max_batch); }
 
 // Splits along the sample axis: none when the tiles alone fill two waves;
-// otherwise between 2 and 4 waves of units, preferring a whole number of
-// waves.  split * tiles <= 4 * sm bounds the partials buffer.
-int choose_split(int64_t tiles, int kblocks, int sm, int tune) {
-    const int cap = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (4LL * sm) / tiles));
+// otherwise the split count in [2 waves, capacity] with the best wave
+// quantisation (smallest on ties).  `cap_units` bounds split * tiles by the
+// partials buffer.
+int choose_split(int64_t tiles, int kblocks, int sm, int tune, int64_t cap_units) {
+    const int cap = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, cap_units / tiles));
     int s;
     if (tune > 0) {
         s = std::min(tune, cap);
@@ -532,11 +578,15 @@ int choose_split(int64_t tiles, int kblocks, int sm, int tune) {
     } else {
         const int lo = (int)std::min<int64_t>((2LL * sm + tiles - 1) / tiles, cap);
         s = lo;
-        for (int c = lo; c <= cap; ++c)
-            if ((tiles * c) % sm == 0) {
+        double best = 0.0;
+        for (int c = lo; c <= cap; ++c) {
+            const int64_t units = tiles * c;
+            const double eff = (double)units / (double)(((units + sm - 1) / sm) * sm);
+            if (eff > best + 1e-9) {
+                best = eff;
                 s = c;
-                break;
             }
+        }
     }
     return std::max(1, std::min(s, std::max(1, kblocks / 4)));
 }
@@ -551,17 +601,24 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
+template <int MH>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+    constexpr size_t smem = Tile<MH>::kSmemTotal;
+    cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm<MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
+    const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
     timer_begin(p, s);
-    k_ternary_gemm<<<grid, kThreads, kSmemTotal, s>>>(*map, single, probs, units, nunits, p.err);
+    k_ternary_gemm<MH><<<grid, kThreads, smem, s>>>(*map, single, probs, units, nunits, chunk, p.err);
     timer_end(p, s);
     return cudaGetLastError();
 }
+
+// Rows per tile: 256 (one accumulator pair; fewer B re-reads) unless tuned to
+// 128 (two accumulators used in turn).
+int tile_halves(const Plan &p) { return p.tune_cols == 128 ? 1 : 2; }
 
 struct TernLayout {
     int kblocks;
@@ -576,7 +633,7 @@ TernLayout layout_for(const ndft_desc &d, int sm) {
     const int cols = max_cols(d);
     L.b_rows = (int64_t)L.kblocks * cols;
     L.b_bytes = (size_t)L.b_rows * 128;
-    L.part_bytes = (size_t)4 * sm * TM * TN * sizeof(float);  // split * tiles <= 4 sm
+    L.part_bytes = (size_t)4 * sm * 256 * TN * sizeof(float);  // 4 waves of 256 x 256 partial tiles
     return L;
 }
 
@@ -622,9 +679,12 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     P.nbins = nb;
     P.ncols = ncols;
     P.kblocks = L.kblocks;
-    P.mtiles = (2 * nb + TM - 1) / TM;
+    const int MH = tile_halves(p);
+    const int rows = 128 * MH;
+    P.mtiles = (2 * nb + rows - 1) / rows;
     P.ntiles = (ncols + TN - 1) / TN;
-    P.nsplit = choose_split((int64_t)P.mtiles * P.ntiles, L.kblocks, p.sm_count, p.tune_split);
+    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * TN * sizeof(float)));
+    P.nsplit = choose_split((int64_t)P.mtiles * P.ntiles, L.kblocks, p.sm_count, p.tune_split, cap_units);
     P.b_row0 = 0;
     P.ld = 2LL * nb;
     P.split_stride = (int64_t)ncols * 2 * nb;
@@ -633,7 +693,8 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + L.b_bytes);
     P.out = P.nsplit == 1 ? static_cast<float *>(out) : part;
     const int64_t nunits = (int64_t)P.mtiles * P.ntiles * P.nsplit;
-    if ((e = launch_gemm(p, P, nullptr, nullptr, nunits, s)) != cudaSuccess) return e;
+    e = MH == 2 ? launch_gemm<2>(p, P, nullptr, nullptr, nunits, s) : launch_gemm<1>(p, P, nullptr, nullptr, nunits, s);
+    if (e != cudaSuccess) return e;
     *launches += 1;
     if (P.nsplit > 1) {
         *launches += 1;
