@@ -151,6 +151,22 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
 ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                          int32_t nlags, const void *dA, void *ds, cudaStream_t stream);
 
+/* Allocation-free variant of caf_exec for the direct fp32 form (the paper has
+ * no counterpart: this serves callers that cannot allocate device memory at
+ * the point of use, such as a real-time loop that forbids cudaMalloc after
+ * start-up or code running during another thread's global-mode graph capture).
+ * Same result as caf_exec on a direct fp32 plan with the same n, p0, nbins,
+ * flags (up to fp32 summation order), with no plan: the twiddle table and the
+ * split-K partials live in a 32 MiB static device array that every GPU loading
+ * the library keeps until exit.  Limits: 1 <= n <= 2^20, 1 <= nbins <= n,
+ * 1 <= nlags <= 2^20; beyond them NDFT_E_INVALID and nothing is launched.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race and must be serialised.
+ * s_surv, s_ref: [n] complex64; A: [nlags][nbins] complex64; device pointers. */
+ndft_status caf_exec_noalloc(int32_t n, int32_t p0, int32_t nbins, const void *s_surv, const void *s_ref,
+                             int32_t lag0, int32_t nlags, uint32_t flags, void *A, cudaStream_t stream);
+
 /* ---- epilogue helpers -------------------------------------------------------- */
 
 /* Per row of X ([rows][cols] complex64): the index of the largest |X|^2

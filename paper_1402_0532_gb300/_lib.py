@@ -20,7 +20,7 @@ F_NO_CONJ_REF, F_CIRCULAR_LAG = 0x1, 0x2
 EXPORTS = ("ndft_plan", "ndft_plan_batched", "ndft_plan_destroy", "ndft_exec", "nfft_exec", "caf_exec",
            "caf_exec_batched", "caf_backward", "ndft_argmax", "ndft_query_error", "ndft_get_twiddles",
            "ndft_plan_bytes", "ndft_last_launches", "ndft_set_tuning", "ndft_timer_start", "ndft_timer_read",
-           "ndft_status_string", "ndft_version", "ndft_last_cuda_error")
+           "ndft_status_string", "ndft_version", "ndft_last_cuda_error", "caf_exec_noalloc")
 
 
 class NdftDesc(ctypes.Structure):
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "ndft_status_string": (ctypes.c_char_p, [i32]),
         "ndft_version": (i32, []),
         "ndft_last_cuda_error": (ctypes.c_char_p, []),
+        "caf_exec_noalloc": (i32, [i32, i32, i32, P, P, i32, i32, u32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
