@@ -321,7 +321,6 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
     if (!out || !cpis || ncpi < 1 || ncpi > (1 << 20) || (flags & ~kKnownFlags)) return NDFT_E_INVALID;
     *out = nullptr;
     if (!valid_pair(form, prec)) return NDFT_E_UNSUPPORTED;
-    if (form != NDFT_FORM_DIRECT) return NDFT_E_UNSUPPORTED;
     for (int c = 0; c < ncpi; ++c) {
         const ndft_cpi &q = cpis[c];
         if (q.n < 1 || q.n > kMaxN || q.nlags < 1 || q.nlags > (1 << 20) || q.nbins < 1 || q.nbins > q.n ||
@@ -330,6 +329,13 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
         // 16-byte alignment of each CPI's rows: offsets in elements of 8 bytes (complex64) or 4 (Q1.14)
         const int esz = prec == NDFT_PREC_Q14 ? 4 : 8;
         if ((q.off_surv * esz) % 16 || (q.off_ref * esz) % 16) return NDFT_E_INVALID;
+        if (form == NDFT_FORM_TERNARY_GEMM) {
+            ndft_desc one{};
+            one.n = q.n;
+            one.form = form;
+            one.prec = prec;
+            if (!ternary_supported(one)) return NDFT_E_UNSUPPORTED;
+        }
     }
     auto *h = new (std::nothrow) ndft_plan_s();
     if (!h) return NDFT_E_NOMEM;
@@ -343,6 +349,16 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
     p.sm_count = sm_count_now(&p.device);
     cudaError_t e = cudaSuccess;
     std::vector<int32_t> work;
+    if (form == NDFT_FORM_TERNARY_GEMM) {
+        if ((e = alloc(&p.err, 1)) != cudaSuccess || (e = cudaMemsetAsync(p.err, 0, sizeof(int32_t), stream)) != cudaSuccess ||
+            (e = ternary_batched_init(p, cpis, ncpi, stream)) != cudaSuccess) {
+            free_plan(p);
+            delete h;
+            return e == cudaErrorNotSupported ? NDFT_E_UNSUPPORTED : from_cuda(e);
+        }
+        *out = h;
+        return NDFT_OK;
+    }
     p.cpis_host = new (std::nothrow) CpiDev[ncpi];
     if (!p.cpis_host) {
         delete h;
@@ -418,6 +434,8 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
     if (!aligned16(surv_base) || !aligned16(ref_base) || !aligned16(out_base)) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
+    if (p.d.form == NDFT_FORM_TERNARY_GEMM)
+        return from_cuda(launch_ternary_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));
     return from_cuda(launch_direct_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));
 }
 

@@ -31,6 +31,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 namespace ndft {
@@ -56,7 +58,7 @@ struct Problem {
     int32_t N, p0, nbins, ncols;
     int32_t kblocks, nsplit, mtiles, ntiles;
     int64_t b_row0;        // first 128-byte row of this problem's packed B
-    float *out;            // output (nsplit == 1) or split-K partials, fp32 view
+    int64_t out_off;       // floats from the launch's output base to this problem's output / partials
     int64_t ld;            // floats per column of out (= 2 * nbins)
     int64_t split_stride;  // floats between split partials
     const float2 *ang;     // two-level table: [nth] (r_hi) then [256] (r_lo)
@@ -166,7 +168,7 @@ __device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 struct Work {
     Problem P;
     int mt, nt, kb0, kb1;
-    float *out;
+    int64_t out_off;  // floats from the launch's output base
 };
 
 __device__ __forceinline__ Work decode(int64_t u, const Problem &single, const Problem *probs, const Unit *units) {
@@ -178,7 +180,7 @@ __device__ __forceinline__ Work decode(int64_t u, const Problem &single, const P
         w.nt = un.nt;
         w.kb0 = (int)((int64_t)un.split * w.P.kblocks / w.P.nsplit);
         w.kb1 = (int)((int64_t)(un.split + 1) * w.P.kblocks / w.P.nsplit);
-        w.out = w.P.out + (int64_t)un.split * w.P.split_stride;
+        w.out_off = w.P.out_off + (int64_t)un.split * w.P.split_stride;
     } else {
         w.P = single;
         const int64_t tiles = (int64_t)single.mtiles * single.ntiles;
@@ -188,7 +190,7 @@ __device__ __forceinline__ Work decode(int64_t u, const Problem &single, const P
         w.nt = (int)(t / single.mtiles);
         w.kb0 = (int)((int64_t)split * single.kblocks / single.nsplit);
         w.kb1 = (int)((int64_t)(split + 1) * single.kblocks / single.nsplit);
-        w.out = single.out + (int64_t)split * single.split_stride;
+        w.out_off = single.out_off + (int64_t)split * single.split_stride;
     }
     return w;
 }
@@ -248,7 +250,8 @@ struct Tile {
 template <int MH>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, Problem single, const Problem *__restrict__ probs,
-                   const Unit *__restrict__ units, int64_t nunits, int chunk, int32_t *err) {
+                   const Unit *__restrict__ units, int64_t nunits, int chunk, float *__restrict__ out_base,
+                   int32_t *err) {
     using T = Tile<MH>;
     constexpr int STG = T::kStages;
     constexpr int NB = T::kBufs;
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_wait_ld();
                         const int64_t col0 = (int64_t)w.nt * TN + cc;
                         if (m < limit_m) {
-                            float *dst = w.out + col0 * w.P.ld + m;
+                            float *dst = out_base + w.out_off + col0 * w.P.ld + m;
                             const int64_t left = w.P.ncols - col0;
                             const int nj = left < 32 ? (int)left : 32;
                             if (first) {
@@ -474,14 +477,15 @@ __device__ __forceinline__ uint4 pack_entry(float2 v) {
 }
 
 struct PackProb {
-    const float2 *a;  // x (NDFT) or s_surv (CAF)
-    const float2 *r;  // s_ref (CAF) or null
+    int64_t a_off;    // elements from the launch's first input base: x (NDFT) or s_surv (CAF)
+    int64_t r_off;    // elements from the launch's second input base: s_ref (CAF)
     int32_t N, lag0, ncols, kblocks;
     int64_t ldx;      // row stride of x
     int64_t row0;     // first packed row
 };
 
-__device__ __forceinline__ float2 lag_product(const PackProb &P, int64_t col, int64_t i, uint32_t flags) {
+__device__ __forceinline__ float2 lag_product(const PackProb &P, const float2 *__restrict__ a,
+                                              const float2 *__restrict__ r, int64_t col, int64_t i, uint32_t flags) {
     int64_t j = i - (P.lag0 + col);
     float2 ref = make_float2(0.f, 0.f);
     if (flags & NDFT_F_CIRCULAR_LAG) {
@@ -489,16 +493,17 @@ __device__ __forceinline__ float2 lag_product(const PackProb &P, int64_t col, in
         if (j < 0) j += P.N;
     }
     if (j >= 0 && j < P.N) {
-        ref = P.r[j];
+        ref = r[j];
         if (!(flags & NDFT_F_NO_CONJ_REF)) ref.y = -ref.y;
     }
-    return cox_f32(P.a[i], ref);
+    return cox_f32(a[i], ref);
 }
 
 // Packs nprob problems; thread e handles entry t = e & 7 of row e >> 3 of the
 // problem that row falls in (prefix[] holds each problem's first flat row).
 __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__restrict__ prefix, int nprob,
-                       PackProb single, int64_t total_rows, uint32_t flags, bool caf, uint4 *__restrict__ B) {
+                       PackProb single, int64_t total_rows, uint32_t flags, bool caf, const float2 *__restrict__ a_base,
+                       const float2 *__restrict__ r_base, uint4 *__restrict__ B) {
     const int64_t total = total_rows * 8;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int t = (int)(e & 7);
@@ -519,7 +524,8 @@ __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__rest
         const int64_t col = local - kb * P.ncols;
         const int64_t i = kb * 8 + t;
         float2 v = make_float2(0.f, 0.f);
-        if (i < P.N) v = caf ? lag_product(P, col, i, flags) : P.a[col * P.ldx + i];
+        const float2 *a = a_base + P.a_off;
+        if (i < P.N) v = caf ? lag_product(P, a, r_base + P.r_off, col, i, flags) : a[col * P.ldx + i];
         B[(P.row0 + local) * 8 + t] = pack_entry(v);
     }
 }
@@ -592,18 +598,20 @@ int choose_split(int64_t tiles, int kblocks, int sm, int tune, int64_t cap_units
 }
 
 cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob, const PackProb &single,
-                        int64_t rows, uint32_t flags, bool caf, void *B, int sm, cudaStream_t s) {
+                        int64_t rows, uint32_t flags, bool caf, const void *a_base, const void *r_base, void *B, int sm,
+                        cudaStream_t s) {
     const int threads = 256;
     const int64_t want = (rows * 8 + threads - 1) / threads;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)sm * 32);
     k_pack<<<std::max(blocks, 1), threads, 0, s>>>(probs, prefix, nprob, single, rows, flags, caf,
-                                                   static_cast<uint4 *>(B));
+                                                   static_cast<const float2 *>(a_base),
+                                                   static_cast<const float2 *>(r_base), static_cast<uint4 *>(B));
     return cudaGetLastError();
 }
 
 template <int MH>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
-                        int64_t nunits, cudaStream_t s) {
+                        int64_t nunits, float *out_base, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
     cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm<MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -611,7 +619,7 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
     const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
     timer_begin(p, s);
-    k_ternary_gemm<MH><<<grid, kThreads, smem, s>>>(*map, single, probs, units, nunits, chunk, p.err);
+    k_ternary_gemm<MH><<<grid, kThreads, smem, s>>>(*map, single, probs, units, nunits, chunk, out_base, p.err);
     timer_end(p, s);
     return cudaGetLastError();
 }
@@ -635,6 +643,24 @@ TernLayout layout_for(const ndft_desc &d, int sm) {
     L.b_bytes = (size_t)L.b_rows * 128;
     L.part_bytes = (size_t)4 * sm * 256 * TN * sizeof(float);  // 4 waves of 256 x 256 partial tiles
     return L;
+}
+
+// Device-side description of a batched plan (one allocation, laid out by
+// ternary_batched_init): Problem[ncpi], PackProb[ncpi], int64 prefix[ncpi + 1],
+// Unit[nunits].
+struct BatchedLayout {
+    size_t probs, packs, prefix, units, total;
+};
+
+BatchedLayout batched_layout(int ncpi, int64_t nunits) {
+    BatchedLayout b;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    b.probs = 0;
+    b.packs = al(b.probs + (size_t)ncpi * sizeof(Problem));
+    b.prefix = al(b.packs + (size_t)ncpi * sizeof(PackProb));
+    b.units = al(b.prefix + (size_t)(ncpi + 1) * sizeof(int64_t));
+    b.total = al(b.units + (size_t)nunits * sizeof(Unit));
+    return b;
 }
 
 }  // namespace
@@ -666,11 +692,12 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
     return make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host));
 }
 
-static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, void *out, cudaStream_t s,
-                              int *launches) {
+static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, const void *a_base,
+                              const void *r_base, void *out, cudaStream_t s, int *launches) {
     const int N = p.d.n, nb = p.d.nbins;
     const TernLayout L = layout_for(p.d, p.sm_count);
-    cudaError_t e = launch_pack(nullptr, nullptr, 0, pp, (int64_t)L.kblocks * ncols, p.d.flags, caf, p.ws, p.sm_count, s);
+    cudaError_t e = launch_pack(nullptr, nullptr, 0, pp, (int64_t)L.kblocks * ncols, p.d.flags, caf, a_base, r_base,
+                                p.ws, p.sm_count, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
     Problem P{};
@@ -690,10 +717,12 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     P.split_stride = (int64_t)ncols * 2 * nb;
     P.ang = p.ang;
     P.nth = nth_for(N);
+    P.out_off = 0;
     float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + L.b_bytes);
-    P.out = P.nsplit == 1 ? static_cast<float *>(out) : part;
+    float *out_base = P.nsplit == 1 ? static_cast<float *>(out) : part;
     const int64_t nunits = (int64_t)P.mtiles * P.ntiles * P.nsplit;
-    e = MH == 2 ? launch_gemm<2>(p, P, nullptr, nullptr, nunits, s) : launch_gemm<1>(p, P, nullptr, nullptr, nunits, s);
+    e = MH == 2 ? launch_gemm<2>(p, P, nullptr, nullptr, nunits, out_base, s)
+                : launch_gemm<1>(p, P, nullptr, nullptr, nunits, out_base, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
     if (P.nsplit > 1) {
@@ -705,24 +734,117 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
 
 cudaError_t launch_ternary_ndft(Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s, int *launches) {
     PackProb pp{};
-    pp.a = static_cast<const float2 *>(x);
     pp.N = p.d.n;
     pp.ncols = (int)batch;
     pp.kblocks = (p.d.n + 7) / 8;
     pp.ldx = p.d.n;
-    return run_single(p, pp, false, (int)batch, X, s, launches);
+    return run_single(p, pp, false, (int)batch, x, nullptr, X, s, launches);
 }
 
 cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags, void *A,
                                cudaStream_t s, int *launches) {
     PackProb pp{};
-    pp.a = static_cast<const float2 *>(s_surv);
-    pp.r = static_cast<const float2 *>(s_ref);
     pp.N = p.d.n;
     pp.lag0 = lag0;
     pp.ncols = nlags;
     pp.kblocks = (p.d.n + 7) / 8;
-    return run_single(p, pp, true, nlags, A, s, launches);
+    return run_single(p, pp, true, nlags, s_surv, s_ref, A, s, launches);
+}
+
+// Batched CPIs: per-CPI angle tables, packed-B regions and a work list of
+// (cpi, m-tile, n-tile) units, longest CPI first, built once here.  No split
+// of the sample axis: the CPIs supply thousands of units.
+cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaStream_t s) {
+    std::vector<Problem> probs(ncpi);
+    std::vector<PackProb> packs(ncpi);
+    std::vector<int64_t> prefix(ncpi + 1, 0);
+    int64_t ang_total = 0, rows_total = 0;
+    for (int c = 0; c < ncpi; ++c) {
+        const ndft_cpi &q = cpis[c];
+        if (q.n > kMaxN) return cudaErrorNotSupported;
+        Problem &P = probs[c];
+        P.N = q.n;
+        P.p0 = q.p0;
+        P.nbins = q.nbins;
+        P.ncols = q.nlags;
+        P.kblocks = (q.n + 7) / 8;
+        P.nsplit = 1;
+        P.mtiles = (2 * q.nbins + 255) / 256;
+        P.ntiles = (q.nlags + TN - 1) / TN;
+        P.b_row0 = rows_total;
+        P.out_off = 2 * q.off_out;
+        P.ld = 2LL * q.nbins;
+        P.split_stride = 0;
+        P.nth = nth_for(q.n);
+        PackProb &K = packs[c];
+        K.a_off = q.off_surv;
+        K.r_off = q.off_ref;
+        K.N = q.n;
+        K.lag0 = q.lag0;
+        K.ncols = q.nlags;
+        K.kblocks = P.kblocks;
+        K.row0 = rows_total;
+        prefix[c] = rows_total;
+        rows_total += (int64_t)P.kblocks * q.nlags;
+        probs[c].ang = reinterpret_cast<const float2 *>(ang_total);  // offset, rebased below
+        ang_total += P.nth + R_LO;
+    }
+    prefix[ncpi] = rows_total;
+    if (rows_total >= (1LL << 31)) return cudaErrorNotSupported;  // TMA row coordinate is 32-bit
+    std::vector<int> order(ncpi);
+    for (int c = 0; c < ncpi; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cpis[a].n > cpis[b].n; });
+    std::vector<Unit> units;
+    for (int c : order)
+        for (int nt = 0; nt < probs[c].ntiles; ++nt)
+            for (int mt = 0; mt < probs[c].mtiles; ++mt) units.push_back(Unit{c, mt, nt, 0});
+    cudaError_t e;
+    float2 *ang = nullptr;
+    if ((e = cudaMalloc(&ang, (size_t)ang_total * sizeof(float2))) != cudaSuccess) return e;
+    p.ang = ang;
+    p.table_bytes += (size_t)ang_total * sizeof(float2);
+    for (int c = 0; c < ncpi; ++c) {
+        const int64_t off = reinterpret_cast<int64_t>(probs[c].ang);
+        probs[c].ang = ang + off;
+        k_angles<<<(probs[c].nth + R_LO + 255) / 256, 256, 0, s>>>(probs[c].N, probs[c].nth, ang + off);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const BatchedLayout BL = batched_layout(ncpi, (int64_t)units.size());
+    if ((e = cudaMalloc(&p.work_dev, BL.total)) != cudaSuccess) return e;
+    unsigned char *wd = reinterpret_cast<unsigned char *>(p.work_dev);
+    std::vector<unsigned char> host(BL.total, 0);
+    std::memcpy(host.data() + BL.probs, probs.data(), probs.size() * sizeof(Problem));
+    std::memcpy(host.data() + BL.packs, packs.data(), packs.size() * sizeof(PackProb));
+    std::memcpy(host.data() + BL.prefix, prefix.data(), prefix.size() * sizeof(int64_t));
+    std::memcpy(host.data() + BL.units, units.data(), units.size() * sizeof(Unit));
+    if ((e = cudaMemcpyAsync(wd, host.data(), BL.total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // `host` must outlive the copy
+    p.nwork = (int64_t)units.size();
+    p.b_bytes = (size_t)std::max<int64_t>(rows_total, 1) * 128;
+    p.ws_bytes = p.b_bytes;
+    if ((e = cudaMalloc(&p.ws, p.ws_bytes)) != cudaSuccess) return e;
+    p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));
+    if (!p.tmap_host) return cudaErrorMemoryAllocation;
+    return make_tmap(p.ws, std::max<int64_t>(rows_total, 1), static_cast<CUtensorMap *>(p.tmap_host));
+}
+
+cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
+                                   int *launches) {
+    const BatchedLayout BL = batched_layout(p.ncpi, p.nwork);
+    unsigned char *wd = reinterpret_cast<unsigned char *>(p.work_dev);
+    const Problem *probs = reinterpret_cast<const Problem *>(wd + BL.probs);
+    const PackProb *packs = reinterpret_cast<const PackProb *>(wd + BL.packs);
+    const int64_t *prefix = reinterpret_cast<const int64_t *>(wd + BL.prefix);
+    const Unit *units = reinterpret_cast<const Unit *>(wd + BL.units);
+    const int64_t rows = (int64_t)(p.b_bytes / 128);
+    cudaError_t e = launch_pack(packs, prefix, p.ncpi, PackProb{}, rows, p.d.flags, true, surv, ref, p.ws,
+                                p.sm_count, s);
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    if ((e = launch_gemm<2>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out), s)) != cudaSuccess)
+        return e;
+    *launches += 1;
+    return cudaSuccess;
 }
 
 }  // namespace ndft

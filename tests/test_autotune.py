@@ -1,0 +1,72 @@
+"""Autotuner: selection and cache logic on the CPU with a fake plan and timer,
+and one real tuning pass on the GPU that must keep the accuracy bar."""
+import numpy as np
+import pytest
+
+from paper_1402_0532_gb300 import autotune as at
+
+
+class FakePlan:
+    def __init__(self):
+        self.knobs = {}
+
+    def set_tuning(self, k, v):
+        self.knobs[k] = v
+
+
+def test_select_fastest_and_cache(tmp_path):
+    path = str(tmp_path / "cache.json")
+    space = {0: [0, 4, 8], 2: [64, 32]}
+    cost = {(0, 64): 3.0, (0, 32): 2.5, (4, 64): 1.0, (4, 32): 1.2, (8, 64): 1.0005, (8, 32): 4.0}
+    plan = FakePlan()
+    calls = []
+
+    def timer(run, reps):
+        calls.append(dict(plan.knobs))
+        return cost[(plan.knobs[0], plan.knobs[2])]
+
+    best = at.tune(plan, lambda: None, "k", space, "GPU", timer=timer, path=path)
+    assert best == {0: 4, 2: 64}
+    assert plan.knobs == {0: 4, 2: 64}
+    assert len(calls) == 6
+    # cached: no timing on the second call, same setting applied
+    plan2 = FakePlan()
+    best2 = at.tune(plan2, lambda: None, "k", space, "GPU", timer=lambda r, n: pytest.fail("timed"), path=path)
+    assert best2 == best and plan2.knobs == best
+    # another device is a different key: timed again
+    plan3 = FakePlan()
+    timed = []
+
+    def timer3(run, reps):
+        timed.append(1)
+        return cost[(plan3.knobs[0], plan3.knobs[2])]
+
+    best3 = at.tune(plan3, lambda: None, "k", space, "OTHER", timer=timer3, path=path)
+    assert best3 == best and len(timed) == 6
+
+
+def test_candidates_cover_the_product():
+    c = at.candidates({1: [256, 128], 2: [64, 32]})
+    assert len(c) == 4 and {1: 128, 2: 32} in c
+
+
+@pytest.mark.gpu
+def test_tune_real_caf_keeps_accuracy(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1402_0532_gb300 import api, scenes
+    sc = scenes.radar_scene(N=8192, nlags=512, nbins=256, seed=70)
+    ss, sr = torch.from_numpy(sc.s_surv).cuda(), torch.from_numpy(sc.s_ref).cuda()
+    plan = api.Plan(sc.N, p0=sc.p0, nbins=256, max_lags=512, form="ternary", prec="bf16x2")
+    best = at.tune_caf(plan, ss, sr, 0, 512, path=str(tmp_path / "c.json"), reps=2)
+    assert best[at.ROWS] in (256, 128) and best[at.CHUNK] in (64, 32)
+    A = plan.caf(ss, sr, 0, 512).cpu().numpy()
+    plan.query_error()
+    lags = np.array([0, 37, 120, 301, 511, 3])
+    bins = np.array([0, 5, -12, 40, 127, -128])
+    ref = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
+    assert np.max(np.abs(A[lags, bins - sc.p0] - ref)) / np.max(np.abs(A)) < 1e-5

@@ -1,0 +1,126 @@
+"""Batched CPIs: many uneven coherent processing intervals in one persistent
+launch sequence, captured in a CUDA graph.  Parity against the oracle per CPI,
+graph replay against eager execution, and the full 256-CPI workload
+(N_c ~ U{1024..32768}, L_c ~ U{64..1024}, 1024 bins) on sampled cells."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0532_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_0532_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def pack(scs, q14=False):
+    surv, ref, cpis, oo, so = [], [], [], 0, 0
+    for sc in scs:
+        a = scenes.quantize_q14(sc.s_surv, 0.25) if q14 else sc.s_surv
+        b = scenes.quantize_q14(sc.s_ref, 0.25) if q14 else sc.s_ref
+        pad = (-sc.N) % 4
+        cpis.append(dict(off_surv=so, off_ref=so, off_out=oo, n=sc.N, lag0=sc.lag0, nlags=sc.nlags, p0=sc.p0,
+                         nbins=sc.nbins))
+        z = np.zeros((pad, 2), np.int16) if q14 else np.zeros(pad, np.complex64)
+        surv += [a, z]
+        ref += [b, z]
+        so += sc.N + pad
+        oo += sc.nlags * sc.nbins
+    return np.concatenate(surv), np.concatenate(ref), cpis, oo
+
+
+def small_scenes():
+    rng = np.random.default_rng(36)
+    return [scenes.radar_scene(N=int(n), nlags=int(l), nbins=int(b), rng=rng)
+            for n, l, b in ((1000, 70, 64), (1536, 5, 96), (777, 130, 33), (2048, 300, 128), (1111, 1, 7))]
+
+
+def test_batched_ternary_small(api):
+    scs = small_scenes()
+    surv, ref, cpis, total = pack(scs)
+    bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    out = torch.zeros(total, dtype=torch.complex64, device="cuda")
+    bp(dev(surv), dev(ref), out)
+    bp.query_error()
+    got = out.cpu().numpy()
+    for sc, c in zip(scs, cpis):
+        g = got[c["off_out"]: c["off_out"] + sc.nlags * sc.nbins].reshape(sc.nlags, sc.nbins)
+        want = oracle.caf(sc.s_surv, sc.s_ref, sc.lag0, sc.nlags, sc.p0, sc.nbins, z32=True)
+        assert np.max(np.abs(g - want)) / np.max(np.abs(want)) < TOL
+
+
+@pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2"), ("direct", "q14")])
+def test_batched_graph_replay_equals_eager(api, form, prec):
+    q14 = prec == "q14"
+    surv, ref, cpis, total = pack(small_scenes(), q14=q14)
+    bp = api.BatchedPlan(cpis, form=form, prec=prec)
+    shape = (total, 2) if q14 else (total,)
+    dt = torch.int32 if q14 else torch.complex64
+    ds, dr = dev(surv), dev(ref)
+    eager = torch.zeros(shape, dtype=dt, device="cuda")
+    bp(ds, dr, eager)
+    torch.cuda.synchronize()
+    out = torch.zeros(shape, dtype=dt, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bp(ds, dr, out)  # warm the kernels' attributes outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bp(ds, dr, out)
+    out.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    bp.query_error()
+    assert torch.equal(out, eager)
+
+
+@pytest.fixture(scope="module")
+def cpi256():
+    return scenes.cpi_batch()
+
+
+@pytest.mark.parametrize("form,prec", [("ternary", "bf16x2"), ("direct", "fp32"), ("direct", "q14")])
+def test_full_256_cpi_batch_sampled(api, cpi256, form, prec):
+    scs = cpi256
+    assert len(scs) == 256
+    q14 = prec == "q14"
+    surv, ref, cpis, total = pack(scs, q14=q14)
+    bp = api.BatchedPlan(cpis, form=form, prec=prec)
+    shape = (total, 2) if q14 else (total,)
+    out = torch.zeros(shape, dtype=torch.int32 if q14 else torch.complex64, device="cuda")
+    bp(dev(surv), dev(ref), out)
+    bp.query_error()
+    got = out.cpu().numpy()
+    rng = np.random.default_rng(60)
+    for c in list(rng.choice(256, 12, replace=False)) + [int(np.argmax([s.N for s in scs]))]:
+        sc, cp = scs[c], cpis[c]
+        lags = np.concatenate([[0, min(37, sc.nlags - 1)], rng.integers(0, sc.nlags, 14)])
+        bins = np.concatenate([[0, 5], rng.integers(sc.p0, sc.p0 + sc.nbins, 14)])
+        idx = cp["off_out"] + lags * sc.nbins + (bins - sc.p0)
+        if q14:
+            qs, qr = scenes.quantize_q14(sc.s_surv, 0.25), scenes.quantize_q14(sc.s_ref, 0.25)
+            for l, b, i in zip(lags, bins, idx):
+                want, _ = oracle.caf_q14(qs, qr, int(l), 1, int(b), 1)
+                assert np.array_equal(got[i], want[0, 0])
+        else:
+            want = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
+            peak = abs(oracle.caf_cells(sc.s_surv, sc.s_ref, [0], [0], z32=True)[0])
+            assert np.max(np.abs(got[idx] - want)) / peak < TOL, c
