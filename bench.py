@@ -51,7 +51,100 @@ def parse():
     ap.add_argument("--direct-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="surface", choices=["surface", "small"],
+                    help="surface: N=65536 (the benchmark); small: N=16384, same lags/bins (profiling case)")
+    ap.add_argument("--profile", action="store_true",
+                    help="time the tensor-core steps only (no direct form, e2e, error or CPU legs)")
+    ap.add_argument("--no-others", action="store_true", help="skip the secondary workloads")
     return ap.parse_args()
+
+
+def _time_ms(fn, reps: int, flush=None) -> float:
+    """Mean device time of fn() over reps calls (CUDA events; L2 flushed before each when given)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def other_workloads(api, scenes, dev, hbm_peak_gbs):
+    """The secondary workloads, timed outside the headline region: the NFFT of 65536
+    vectors of 1024 points, the N=64 tone batch (both forms), the 256-CPI batch
+    (tensor-core form, one persistent launch sequence) and the N=16384
+    forward + backward through the autograd function."""
+    import numpy as np
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    # NFFT, Sec. 3
+    x = torch.from_numpy(scenes.cn_batch()).to(dev)
+    pf = api.Plan(1024, max_batch=x.shape[0], device=dev)
+    y = torch.empty_like(x)
+    ms = _time_ms(lambda: pf.nfft(x, out=y), 10, flush)
+    moved = 2 * x.numel() * 8
+    out["nfft_1024_x65536"] = {"ms": ms, "vectors_per_s": x.shape[0] / (ms / 1e3),
+                               "hbm_gbs": moved / (ms / 1e3) / 1e9, "hbm_frac": moved / (ms / 1e3) / 1e9 / hbm_peak_gbs,
+                               "butterflies_per_s": x.shape[0] * 512 * 10 / (ms / 1e3)}
+    del x, y
+    # NDFT of the N=64 tone batch
+    xt = torch.from_numpy(scenes.tone_batch()).to(dev)
+    for form, prec in (("direct", "fp32"), ("ternary", "bf16x2")):
+        p = api.Plan(64, max_batch=4096, form=form, prec=prec, device=dev)
+        X = torch.empty_like(xt)
+        ms = _time_ms(lambda: p.ndft(xt, out=X), 20, flush)
+        out[f"ndft_64_x4096_{form}"] = {"ms": ms, "vectors_per_s": 4096 / (ms / 1e3)}
+    # 256 CPIs, tensor-core form
+    scs = scenes.cpi_batch()
+    surv, ref, cpis, oo, so = [], [], [], 0, 0
+    for sc in scs:
+        pad = (-sc.N) % 4
+        cpis.append(dict(off_surv=so, off_ref=so, off_out=oo, n=sc.N, lag0=0, nlags=sc.nlags, p0=sc.p0,
+                         nbins=sc.nbins))
+        surv += [sc.s_surv, np.zeros(pad, np.complex64)]
+        ref += [sc.s_ref, np.zeros(pad, np.complex64)]
+        so += sc.N + pad
+        oo += sc.nlags * sc.nbins
+    ds = torch.from_numpy(np.concatenate(surv)).to(dev)
+    dr = torch.from_numpy(np.concatenate(ref)).to(dev)
+    bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    A = torch.empty(oo, dtype=torch.complex64, device=dev)
+    ms = _time_ms(lambda: bp(ds, dr, A), 3)
+    units = sum(c["nlags"] * c["nbins"] * c["n"] for c in cpis)
+    out["caf_256_cpis_ternary"] = {"ms": ms, "cells_per_s": oo / (ms / 1e3), "otimes_per_s": units / (ms / 1e3),
+                                   "cells": oo}
+    bp.close()
+    del ds, dr, A
+    torch.cuda.empty_cache()
+    # forward + backward, N = 16384, 512 x 512
+    sc = scenes.radar_scene(N=16384, seed=4, nlags=512, nbins=512)
+    mask = torch.from_numpy(scenes.differentiation_mask(sc)).to(dev)
+    sr = torch.from_numpy(sc.s_ref).to(dev)
+    plan = api.Plan(sc.N, p0=sc.p0, nbins=512, max_lags=512, form="ternary", prec="bf16x2", device=dev)
+
+    def fb():
+        s = torch.from_numpy(sc.s_surv).to(dev).requires_grad_(True)
+        api.caf_autograd(s, sr, plan, 0, 512).abs()[mask].sum().backward()
+    ms = _time_ms(fb, 5)
+    out["caf_16384_fwd_bwd"] = {"ms": ms, "cells": 512 * 512}
+    return out
+
+
+def set_workload(name: str):
+    global N, WORKLOAD
+    if name == "small":
+        N = 16384
+        WORKLOAD = ("passive-radar nonlinear CAF (Eq. 12a), N=16384, 1024 lags x 1024 Doppler bins, fp32 scene "
+                    "(profiling case)")
 
 
 def dist_env():
@@ -161,7 +254,7 @@ def run_reference(args, rank, world):
     import oracle
     from paper_1402_0532_gb300 import scenes
     oracle.build()
-    scene = scenes.radar_scene()
+    scene = scenes.radar_scene(N=N)
     rate_guess = 2000.0  # cells/s, sizes the per-step sample so the run stays within minutes
     per_step = int(max(16, min(NBINS, 90.0 * rate_guess / max(1, args.steps + args.warmup))))
     rng = np.random.default_rng(7)
@@ -191,6 +284,7 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    set_workload(args.workload)
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -210,7 +304,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    scene = scenes.radar_scene()
+    scene = scenes.radar_scene(N=N)
     ss = torch.from_numpy(scene.s_surv).to(dev)
     sr = torch.from_numpy(scene.s_ref).to(dev)
     plan = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="ternary", prec="bf16x2", device=dev)
@@ -269,6 +363,18 @@ def main():
                 "issued_frac": issued_flops / gemm_avg_s / 1e12 / bf16_peak,
                 "kernel_ms": gemm_avg_s * 1000.0}
 
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": K,
+                              "warmup": max(3, args.warmup), "ms_per_step": t_total / K, "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                              "config": {"workload": WORKLOAD, "N": N, "nlags": NLAGS, "nbins": NBINS,
+                                         "mode": "profile (tensor-core steps only)"},
+                              "roofline": roofline, "gpu_launches": launches_per_step * K}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+
     # the plain direct form, same surface
     pd = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="direct", prec="fp32", device=dev)
     Ad = torch.empty_like(A)
@@ -285,6 +391,8 @@ def main():
         dms.append(e0.elapsed_time(e1))
     direct = {"value": cells / (statistics.mean(dms) / 1000.0), "unit": "cells/s",
               "ms_per_step": statistics.mean(dms)}
+
+    others = other_workloads(api, scenes, dev, hbm_peak) if not args.no_others else None
 
     # end to end through the public API: pinned host inputs in, surface out
     hss = torch.from_numpy(scene.s_surv).pin_memory()
@@ -329,7 +437,7 @@ def main():
                            "parallelism": f"{world} independent surface(s), one per GPU"},
                 "roofline": roofline, "direct": direct, "speedup_vs_direct": value / world / direct["value"],
                 "max_err_vs_fp64": err, "e2e": e2e, "gpu_launches": launches_per_step * K,
-                "clocks": clocks, "cpu_baseline": base}
+                "clocks": clocks, "cpu_baseline": base, "other_workloads": others}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -196,11 +196,14 @@ ndft_status ndft_plan_bytes(ndft_plan_t plan, int64_t *bytes);
 ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
 
 /* Tile / split choice for the plan's kernels: key 0 = split count along the
- * sample axis (0 = automatic), key 1 = ternary-GEMM rows per tile (256: one
- * tensor-memory accumulator pair, the default; 128: two accumulators used in
- * turn), key 2 = ternary-GEMM K blocks (8 samples each) per
- * tensor-memory accumulation chain before it is folded into the fp32 result
- * (0 = 64).  Used by the autotuner; affects speed and fp32 rounding only. */
+ * sample axis (0 = automatic); key 1 = ternary-GEMM tile (256: 256 rows in one
+ * CTA with one tensor-memory accumulator pair, the default; 128: 128 rows with
+ * two accumulators used in turn; 129: the 128-row tile in 2-CTA clusters that
+ * share each operand tile by TMA multicast); key 2 = ternary-GEMM K blocks
+ * (8 samples each) per tensor-memory accumulation chain before it is folded
+ * into the fp32 result (0 = 64); key 3 = ternary-GEMM fold path (0: bulk
+ * tensor stores/adds, 1: per-element adds).  Used by the autotuner; affects
+ * speed and fp32 rounding only. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
 
 /* Device timing of the plan's main contraction kernel (the tensor-core GEMM,

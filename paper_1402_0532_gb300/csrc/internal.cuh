@@ -56,6 +56,7 @@ struct Plan {
     int tune_split = 0;
     int tune_cols = 0;
     int tune_chunk = 0;          // ternary form: K blocks per TMEM accumulation chain
+    int tune_drain = 0;          // ternary form: 0 bulk tensor stores/adds, 1 per-element adds
     int last_launches = 0;
     // optional timing of the main contraction kernel (event pairs, see ndft_timer_start)
     mutable cudaEvent_t *tev = nullptr;
@@ -63,6 +64,7 @@ struct Plan {
     mutable int tcount = 0;
     // ternary GEMM: TMA descriptor storage (host copy + device copy)
     void *tmap_host = nullptr;
+    void *tmap_host2 = nullptr;  // same buffer, 128-row box (2-CTA cluster variant)
     void *tmap_dev = nullptr;
     size_t b_bytes = 0;          // packed-B region of the workspace
     size_t part_bytes = 0;       // split-K partials region of the workspace

@@ -50,6 +50,7 @@ void free_plan(Plan &p) {
     cudaFree(p.counter);
     cudaFree(p.tmap_dev);
     std::free(p.tmap_host);
+    std::free(p.tmap_host2);
     delete[] p.cpis_host;
     if (p.tev) {
         for (int i = 0; i < 2 * p.tcap; ++i) cudaEventDestroy(p.tev[i]);
@@ -303,11 +304,14 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
         if (value > 4096) return NDFT_E_INVALID;
         plan->p.tune_split = value;
     } else if (key == 1) {
-        if (value != 0 && value != 128 && value != 256) return NDFT_E_INVALID;
+        if (value != 0 && value != 128 && value != 129 && value != 256) return NDFT_E_INVALID;
         plan->p.tune_cols = value;
     } else if (key == 2) {
         if (value > 1 << 20) return NDFT_E_INVALID;
         plan->p.tune_chunk = value;
+    } else if (key == 3) {
+        if (value > 1) return NDFT_E_INVALID;
+        plan->p.tune_drain = value;
     } else {
         return NDFT_E_INVALID;
     }

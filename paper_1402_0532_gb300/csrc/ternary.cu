@@ -139,6 +139,33 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
+// 2-CTA cluster helpers: this CTA's rank, a cluster-wide barrier, a TMA load
+// whose data and mbarrier signal go to the same offsets in every CTA of
+// `mask`, and an MMA commit that arrives on the barrier in every CTA of `mask`.
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_b_mc(uint32_t dst, const CUtensorMap *map, int32_t row, uint64_t *bar,
+                                              uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -163,23 +190,60 @@ __device__ __forceinline__ void red_add_f32(float *addr, float v) {
 }
 
 __device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+
+// Bulk tensor copies of a staged [32 columns][128 rows] fp32 block to the
+// output map at {row, column, split}: plain store, or element-wise add in L2.
+__device__ __forceinline__ void tma_store_out(const CUtensorMap *map, uint32_t src, int m, int col, int split) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(m), "r"(col), "r"(split), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_reduce_out(const CUtensorMap *map, uint32_t src, int m, int col, int split) {
+    asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(m), "r"(col), "r"(split), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // ---- unit decoding -------------------------------------------------------------
 struct Work {
     Problem P;
     int mt, nt, kb0, kb1;
+    int split;
     int64_t out_off;  // floats from the launch's output base
 };
 
-__device__ __forceinline__ Work decode(int64_t u, const Problem &single, const Problem *probs, const Unit *units) {
+// Unit u of the launch.  With a 2-CTA cluster (cl = 2) a unit is a pair of
+// neighbouring m-tiles sharing one B tile; CTA `rank` of the pair takes
+// m-tile 2 mp + rank (single problems only).
+__device__ __forceinline__ Work decode(int64_t u, const Problem &single, const Problem *probs, const Unit *units,
+                                       int rank, int cl) {
     Work w;
-    if (units) {
+    if (cl == 2) {
+        w.P = single;
+        const int mp = (single.mtiles + 1) / 2;
+        const int64_t tiles = (int64_t)mp * single.ntiles;
+        const int split = (int)(u / tiles);
+        const int64_t t = u - (int64_t)split * tiles;
+        w.mt = 2 * (int)(t % mp) + rank;
+        w.nt = (int)(t / mp);
+        w.kb0 = (int)((int64_t)split * single.kblocks / single.nsplit);
+        w.kb1 = (int)((int64_t)(split + 1) * single.kblocks / single.nsplit);
+        w.split = split;
+        w.out_off = single.out_off + (int64_t)split * single.split_stride;
+    } else if (units) {
         const Unit un = units[u];
         w.P = probs[un.prob];
         w.mt = un.mt;
         w.nt = un.nt;
         w.kb0 = (int)((int64_t)un.split * w.P.kblocks / w.P.nsplit);
         w.kb1 = (int)((int64_t)(un.split + 1) * w.P.kblocks / w.P.nsplit);
+        w.split = un.split;
         w.out_off = w.P.out_off + (int64_t)un.split * w.P.split_stride;
     } else {
         w.P = single;
@@ -190,6 +254,7 @@ __device__ __forceinline__ Work decode(int64_t u, const Problem &single, const P
         w.nt = (int)(t / single.mtiles);
         w.kb0 = (int)((int64_t)split * single.kblocks / single.nsplit);
         w.kb1 = (int)((int64_t)(split + 1) * single.kblocks / single.nsplit);
+        w.split = split;
         w.out_off = single.out_off + (int64_t)split * single.split_stride;
     }
     return w;
@@ -243,16 +308,23 @@ struct Tile {
     static constexpr size_t kSmemA = 0;
     static constexpr size_t kSmemB = kSmemA + (size_t)kStages * kABytes;
     static constexpr size_t kSmemTab = kSmemB + (size_t)kStages * B_BYTES;
-    static constexpr size_t kSmemBar = kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2);
+    static constexpr size_t kSmemStage = (kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2) + 127) / 128 * 128;
+    static constexpr size_t kSmemBar = kSmemStage + 32 * 128 * sizeof(float);  // [32 cols][128 rows] fp32
     static constexpr size_t kSmemTotal = kSmemBar + 160 + 1024;  // barriers, flags, alignment slack
 };
 
-template <int MH>
+// CL = 2 (with MH = 1): a 2-CTA cluster on neighbouring m-tiles; each CTA
+// loads half of the shared 256-column B tile and multicasts it to both, and
+// each stage is refilled only after both CTAs' MMAs released it.  `tmap` then
+// has a 128-row box.
+template <int MH, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, Problem single, const Problem *__restrict__ probs,
-                   const Unit *__restrict__ units, int64_t nunits, int chunk, float *__restrict__ out_base,
-                   int32_t *err) {
+    k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
+                   Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
+                   int chunk, float *__restrict__ out_base, int32_t *err) {
+    static_assert(CL == 1 || (CL == 2 && MH == 1), "the cluster variant uses 128-row tiles");
     using T = Tile<MH>;
+    const int rank = CL == 2 ? (int)cluster_rank() : 0;
     constexpr int STG = T::kStages;
     constexpr int NB = T::kBufs;
     extern __shared__ unsigned char smem_raw[];
@@ -273,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STG; ++s) {
             mbar_init(&full[s], 1 + kGenWarps);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CL);  // one MMA commit per CTA of the cluster
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(&tmem_full[b], 1);
@@ -291,6 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (CL == 2) cluster_sync();  // the peer's barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
@@ -300,13 +373,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const Work w = decode(u, single, probs, units);
+            for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
+                const Work w = decode(u, single, probs, units, rank, CL);
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     mbar_arrive_tx(&full[stage], B_BYTES);
                     const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN;
-                    tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
+                    if (CL == 2)
+                        tma_load_b_mc(b_base + stage * B_BYTES + rank * (B_BYTES / 2), &tmap,
+                                      (int32_t)(row + rank * (TN / 2)), &full[stage], (uint16_t)0x3);
+                    else
+                        tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
                     if (++stage == STG) {
                         stage = 0;
                         phase ^= 1u;
@@ -320,8 +397,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0, chain = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const Work w = decode(u, single, probs, units);
+            for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
+                const Work w = decode(u, single, probs, units, rank, CL);
                 // one accumulation chain per chunk of `chunk` K blocks; the epilogue
                 // folds each chain into the destination in fp32 (round to nearest)
                 for (int c0 = w.kb0; c0 < w.kb1 && ok; c0 += chunk, ++chain) {
@@ -342,7 +419,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             for (int h = 0; h < MH; ++h)
                                 umma(d0 + h * TN, umma_desc(a_st + h * 128 * 128 + k * 32), bd, acc);
                         }
-                        umma_commit(&empty[stage]);
+                        if (CL == 2) umma_commit_mc(&empty[stage], (uint16_t)0x3);
+                        else umma_commit(&empty[stage]);
                         if (++stage == STG) {
                             stage = 0;
                             phase ^= 1u;
@@ -362,8 +440,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-            const Work w = decode(u, single, probs, units);
+        for (int64_t u = blockIdx.x / CL; u < nunits; u += gridDim.x / CL) {
+            const Work w = decode(u, single, probs, units, rank, CL);
             gen_bar();  // every producer is done with the previous table
             for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
                 const float2 v = w.P.ang[e];
@@ -406,8 +484,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quarter = warp & 3;
         uint32_t chain = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-            const Work w = decode(u, single, probs, units);
+        for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
+            const Work w = decode(u, single, probs, units, rank, CL);
             const int64_t limit_m = 2LL * w.P.nbins;
             for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
                 const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
@@ -418,6 +496,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // written by one thread only, in chain order, so the sum is
                 // deterministic.
                 const bool first = (c0 == w.kb0);
+                if (out_tma) {
+                    // Stage each 32-column group as [32 cols][128 rows] in shared memory and
+                    // hand it to one bulk tensor store (first chain) or add (later chains).
+                    // The previous chain's bulk operations are complete before this chain's
+                    // start, so the additions land in chain order.
+                    const int et = threadIdx.x - 32 * kEpiWarp0;
+                    const uint32_t stg = smem_u32(smem + T::kSmemStage);
+                    float *stg_f = reinterpret_cast<float *>(smem + T::kSmemStage);
+#pragma unroll 1
+                    for (int h = 0; h < MH; ++h) {
+#pragma unroll 1
+                        for (int cc = 0; cc < TN; cc += 32) {
+                            uint32_t r[32];
+                            tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf + h) * TN + cc), r);
+                            tmem_wait_ld();
+                            if (et == 0) {
+                                if (h == 0 && cc == 0) bulk_wait_all();
+                                else bulk_wait_read();
+                            }
+                            epi_bar();
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) stg_f[j * 128 + 32 * quarter + lane] = __uint_as_float(r[j]);
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            epi_bar();
+                            if (et == 0) {
+                                const int mrow = w.mt * T::kRows + 128 * h;
+                                const int col = w.nt * TN + cc;
+                                if (first) tma_store_out(&omap, stg, mrow, col, w.split);
+                                else tma_reduce_out(&omap, stg, mrow, col, w.split);
+                                bulk_commit();
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+                    continue;
+                }
 #pragma unroll 1
                 for (int h = 0; h < MH; ++h) {
                     const int64_t m = (int64_t)w.mt * T::kRows + 128 * h + 32 * quarter + lane;
@@ -448,6 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(&tmem_empty[buf]);
             }
         }
+        if (out_tma && threadIdx.x == 32 * kEpiWarp0) bulk_wait_all();  // bulk writes done before exit
     }
 
     __syncthreads();
@@ -457,6 +574,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         while (clock64() - t0 < 200000) {
         }
     }
+    // neither CTA of a pair leaves while the other may still multicast into its
+    // shared memory or arrive on its barriers
+    if (CL == 2) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
@@ -520,13 +640,36 @@ __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__rest
             P = probs[lo];
             local = frow - prefix[lo];
         }
-        const int64_t kb = local / P.ncols;
-        const int64_t col = local - kb * P.ncols;
-        const int64_t i = kb * 8 + t;
+        // rows of one problem number < 2^31 (checked at plan time): 32-bit division
+        const uint32_t kb = (uint32_t)local / (uint32_t)P.ncols;
+        const uint32_t col = (uint32_t)local - kb * (uint32_t)P.ncols;
+        const int64_t i = (int64_t)kb * 8 + t;
         float2 v = make_float2(0.f, 0.f);
         const float2 *a = a_base + P.a_off;
         if (i < P.N) v = caf ? lag_product(P, a, r_base + P.r_off, col, i, flags) : a[col * P.ldx + i];
         B[(P.row0 + local) * 8 + t] = pack_entry(v);
+    }
+}
+
+// One problem: block (x, y) packs columns [32 x, 32 x + 32) of K blocks
+// [8 y, 8 y + 8), one 16-byte entry per thread and K block, no division.
+constexpr int kPackKb = 8;
+__global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags, bool caf,
+                                                     const float2 *__restrict__ a_base,
+                                                     const float2 *__restrict__ r_base, uint4 *__restrict__ B) {
+    const int t = threadIdx.x & 7;
+    const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
+    if (col >= P.ncols) return;
+    const float2 *a = a_base + P.a_off;
+    const float2 *r = r_base + P.r_off;
+    const int kb0 = blockIdx.y * kPackKb;
+    const int kb1 = min(kb0 + kPackKb, P.kblocks);
+#pragma unroll 2
+    for (int kb = kb0; kb < kb1; ++kb) {
+        const int64_t i = (int64_t)kb * 8 + t;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < P.N) v = caf ? lag_product(P, a, r, col, i, flags) : a[(int64_t)col * P.ldx + i];
+        B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
     }
 }
 
@@ -553,15 +696,32 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-cudaError_t make_tmap(void *base, int64_t rows, CUtensorMap *map) {
+cudaError_t make_tmap(void *base, int64_t rows, CUtensorMap *map, int box_rows = TN) {
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     cuuint64_t dims[2] = {64, (cuuint64_t)rows};
     cuuint64_t strides[1] = {128};
-    cuuint32_t box[2] = {64, (cuuint32_t)TN};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Output (or split partials) as a 3-D fp32 tensor {2 nbins rows, ncols, nsplit},
+// box 128 rows x 32 columns x 1 split, no swizzle: the epilogue's bulk
+// stores / adds.  Needs 2 nbins * 4 bytes to be a multiple of 16 (nbins even).
+cudaError_t make_out_map(void *base, int nbins, int ncols, int nsplit, CUtensorMap *map) {
+    auto enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t rows = 2ull * nbins;
+    cuuint64_t dims[3] = {rows, (cuuint64_t)ncols, (cuuint64_t)nsplit};
+    cuuint64_t strides[2] = {rows * 4, rows * 4 * (cuuint64_t)ncols};
+    cuuint32_t box[3] = {128, 32, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -601,6 +761,12 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
                         int64_t rows, uint32_t flags, bool caf, const void *a_base, const void *r_base, void *B, int sm,
                         cudaStream_t s) {
     const int threads = 256;
+    if (!probs && (single.kblocks + kPackKb - 1) / kPackKb <= 65535) {
+        const dim3 grid((single.ncols + 31) / 32, (single.kblocks + kPackKb - 1) / kPackKb);
+        k_pack_single<<<grid, threads, 0, s>>>(single, flags, caf, static_cast<const float2 *>(a_base),
+                                               static_cast<const float2 *>(r_base), static_cast<uint4 *>(B));
+        return cudaGetLastError();
+    }
     const int64_t want = (rows * 8 + threads - 1) / threads;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)sm * 32);
     k_pack<<<std::max(blocks, 1), threads, 0, s>>>(probs, prefix, nprob, single, rows, flags, caf,
@@ -609,24 +775,48 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH>
+template <int MH, int CL>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
-                        int64_t nunits, float *out_base, cudaStream_t s) {
+                        int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
-    cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm<MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = k_ternary_gemm<MH, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
-    const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
+    const CUtensorMap *map = static_cast<const CUtensorMap *>(CL == 2 ? p.tmap_host2 : p.tmap_host);
     const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    const CUtensorMap &om = omap ? *omap : none;
+    const int out_tma = omap ? 1 : 0;
     timer_begin(p, s);
-    k_ternary_gemm<MH><<<grid, kThreads, smem, s>>>(*map, single, probs, units, nunits, chunk, out_base, p.err);
+    if (CL == 1) {
+        const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
+        kern<<<grid, kThreads, smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, out_base, p.err);
+        e = cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(nunits, p.sm_count / 2)));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, *map, om, out_tma, single, probs, units, nunits, chunk, out_base, p.err);
+    }
     timer_end(p, s);
-    return cudaGetLastError();
+    return e;
 }
 
-// Rows per tile: 256 (one accumulator pair; fewer B re-reads) unless tuned to
-// 128 (two accumulators used in turn).
-int tile_halves(const Plan &p) { return p.tune_cols == 128 ? 1 : 2; }
+// Tile shape: 256 rows in one CTA (one accumulator pair, the default), or
+// 128 rows per CTA in 2-CTA clusters sharing B by multicast (two
+// accumulators used in turn), or 128 rows without the cluster.
+int tile_halves(const Plan &p) { return (p.tune_cols == 128 || p.tune_cols == 129) ? 1 : 2; }
+int tile_cluster(const Plan &p) { return p.tune_cols == 129 ? 2 : 1; }
 
 struct TernLayout {
     int kblocks;
@@ -689,7 +879,12 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
     p.part_bytes = L.part_bytes;
     p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));  // CUtensorMap wants 64-byte alignment
     if (!p.tmap_host) return cudaErrorMemoryAllocation;
-    return make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host));
+    if ((e = make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
+        cudaSuccess)
+        return e;
+    p.tmap_host2 = std::aligned_alloc(64, sizeof(CUtensorMap));  // 128-row box for the 2-CTA variant
+    if (!p.tmap_host2) return cudaErrorMemoryAllocation;
+    return make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host2), TN / 2);
 }
 
 static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, const void *a_base,
@@ -706,12 +901,15 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     P.nbins = nb;
     P.ncols = ncols;
     P.kblocks = L.kblocks;
-    const int MH = tile_halves(p);
+    const int MH = tile_halves(p), CL = tile_cluster(p);
     const int rows = 128 * MH;
     P.mtiles = (2 * nb + rows - 1) / rows;
     P.ntiles = (ncols + TN - 1) / TN;
-    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * TN * sizeof(float)));
-    P.nsplit = choose_split((int64_t)P.mtiles * P.ntiles, L.kblocks, p.sm_count, p.tune_split, cap_units);
+    // scheduled units per split and the slots that run them (a 2-CTA pair per unit in the cluster variant)
+    const int64_t tiles = (CL == 2 ? (P.mtiles + 1) / 2 : P.mtiles) * (int64_t)P.ntiles;
+    const int slots = CL == 2 ? p.sm_count / 2 : p.sm_count;
+    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * CL * TN * sizeof(float)));
+    P.nsplit = choose_split(tiles, L.kblocks, slots, p.tune_split, cap_units);
     P.b_row0 = 0;
     P.ld = 2LL * nb;
     P.split_stride = (int64_t)ncols * 2 * nb;
@@ -720,9 +918,15 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     P.out_off = 0;
     float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + L.b_bytes);
     float *out_base = P.nsplit == 1 ? static_cast<float *>(out) : part;
-    const int64_t nunits = (int64_t)P.mtiles * P.ntiles * P.nsplit;
-    e = MH == 2 ? launch_gemm<2>(p, P, nullptr, nullptr, nunits, out_base, s)
-                : launch_gemm<1>(p, P, nullptr, nullptr, nunits, out_base, s);
+    const int64_t nunits = tiles * P.nsplit;
+    // bulk tensor stores / adds for the epilogue when the rows are 16-byte multiples
+    alignas(64) CUtensorMap omap;
+    const bool tma_out = (nb % 2 == 0) && p.tune_drain == 0 &&
+                         make_out_map(out_base, nb, ncols, P.nsplit, &omap) == cudaSuccess;
+    const CUtensorMap *om = tma_out ? &omap : nullptr;
+    if (MH == 2) e = launch_gemm<2, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
+    else if (CL == 2) e = launch_gemm<1, 2>(p, P, nullptr, nullptr, nunits, out_base, om, s);
+    else e = launch_gemm<1, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
     if (P.nsplit > 1) {
@@ -841,7 +1045,8 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
                                 p.sm_count, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
-    if ((e = launch_gemm<2>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out), s)) != cudaSuccess)
+    if ((e = launch_gemm<2, 1>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out), nullptr, s)) !=
+        cudaSuccess)
         return e;
     *launches += 1;
     return cudaSuccess;
