@@ -114,3 +114,30 @@ def test_ternary_caf_split_k_sampled(api):
     pd = api.Plan(sc.N, p0=sc.p0, nbins=256, max_lags=300)
     Ad = pd.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 300).cpu().numpy()
     assert np.max(np.abs(Ad - got)) / peak < 2 * TOL
+
+
+@pytest.mark.parametrize("tile", [256, 128, 129])
+@pytest.mark.parametrize("chunk", [64, 16])
+def test_ternary_tile_variants(api, tile, chunk):
+    """Every tile shape (256 rows; 128 rows with two accumulators; 128 rows in
+    2-CTA clusters sharing B by multicast) and chain length gives the same
+    surface within the bar, on a ragged problem with split sample axis."""
+    sc = scenes.radar_scene(N=9000, nlags=300, nbins=200, seed=45)
+    lags = np.array([0, 37, 120, 299, 5, 250])
+    bins = np.array([0, 5, -12, 99, -100, 40])
+    ref = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
+    p = api.Plan(sc.N, p0=sc.p0, nbins=200, max_lags=300, form="ternary", prec="bf16x2")
+    p.set_tuning(1, tile)
+    p.set_tuning(2, chunk)
+    A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 300).cpu().numpy()
+    p.query_error()
+    assert np.isfinite(A).all()
+    peak = np.max(np.abs(A))
+    assert np.max(np.abs(A[lags, bins - sc.p0] - ref)) / peak < TOL
+    x = scenes.cn(np.random.default_rng(46), (300, 100)).astype(np.complex64)
+    q = api.Plan(100, p0=-7, nbins=77, max_batch=300, form="ternary", prec="bf16x2")
+    q.set_tuning(1, tile)
+    q.set_tuning(2, chunk)
+    got = q.ndft(dev(x)).cpu().numpy()
+    want = oracle.ndft(x.astype(np.complex128), p0=-7, nbins=77)
+    assert relerr(got, want) < TOL
