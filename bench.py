@@ -56,7 +56,41 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="time the tensor-core steps only (no direct form, e2e, error or CPU legs)")
     ap.add_argument("--no-others", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft"],
+                    help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
+
+
+def profile_other(args, api, scenes, dev):
+    """--profile with the direct form (the CAF surface of the workload) or the NFFT
+    (65536 vectors of 1024 points): K timed steps, one JSON line."""
+    import torch
+    if args.profile_form == "direct":
+        scene = scenes.radar_scene(N=N)
+        ss = torch.from_numpy(scene.s_surv).to(dev)
+        sr = torch.from_numpy(scene.s_ref).to(dev)
+        plan = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="direct", prec="fp32", device=dev)
+        out = torch.empty(NLAGS, NBINS, dtype=torch.complex64, device=dev)
+        step = lambda: plan.caf(ss, sr, 0, NLAGS, out=out)  # noqa: E731
+        units = NLAGS * NBINS
+        what = f"direct-form CAF, N={N}, {NLAGS} lags x {NBINS} bins"
+    else:
+        x = torch.from_numpy(scenes.cn_batch()).to(dev)
+        plan = api.Plan(1024, max_batch=x.shape[0], device=dev)
+        out = torch.empty_like(x)
+        step = lambda: plan.nfft(x, out=out)  # noqa: E731
+        units = x.shape[0]
+        what = "NFFT, 65536 vectors of 1024 points"
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.timer_start(args.steps)
+    for _ in range(args.steps):
+        step()
+    ms, n = plan.timer_read()
+    plan.query_error()
+    print(json.dumps({"mode": "profile", "form": args.profile_form, "workload": what, "steps": args.steps,
+                      "kernel_ms": ms / max(n, 1), "units_per_s": units / (ms / max(n, 1) / 1e3)}), flush=True)
 
 
 def _time_ms(fn, reps: int, flush=None) -> float:
@@ -303,6 +337,12 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.profile and args.profile_form != "ternary":
+        if rank == 0:
+            profile_other(args, api, scenes, dev)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     scene = scenes.radar_scene(N=N)
     ss = torch.from_numpy(scene.s_surv).to(dev)

@@ -97,20 +97,27 @@ def test_ndft_q14_bit_exact(api, N, batch, p0, nbins):
 # --------------------------------------------------------------------------------
 # NFFT, Sec. 3
 # --------------------------------------------------------------------------------
-@pytest.mark.parametrize("N,batch", [(2, 300), (4, 301), (8, 300), (64, 100), (1024, 40), (16384, 3), (32768, 2)])
+@pytest.mark.parametrize("N,batch", [(2, 300), (4, 301), (8, 300), (16, 77), (32, 65), (64, 100), (128, 33),
+                                     (256, 17), (512, 9), (1024, 40), (2048, 5), (4096, 3), (8192, 3),
+                                     (16384, 3), (32768, 2), (64, 40000)])
 def test_nfft_bit_exact(api, N, batch):
+    """Bit for bit (zero signs included) against the oracle's fp32 recursion,
+    for every register-kernel size, ragged batches, and a batch large enough
+    that each persistent block loops over several vector groups."""
     rng = np.random.default_rng(N)
     x = scenes.cn(rng, (batch, N)).astype(np.complex64)
     x[0] = scenes.exact_tone(N, 1 if N > 1 else 0).astype(np.complex64)
     x[1, ::3] = 0
+    x[2, ::5] = np.complex64(complex(-0.0, -0.0))
+    x[2, 1::5] = np.complex64(complex(0.0, -0.0))
     want = oracle.nfft_f32(x)
     p = api.Plan(N, max_batch=batch)
     got = p.nfft(dev(x)).cpu().numpy()
-    assert np.array_equal(got.view(np.uint32), want.view(np.uint32)) or np.array_equal(got, want)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
     # in place
     t = dev(x)
     p.nfft(t, out=t)
-    assert np.array_equal(t.cpu().numpy(), want)
+    assert np.array_equal(t.cpu().numpy().view(np.uint32), want.view(np.uint32))
     # and within fp32 rounding of the fp64 recursion on well-conditioned rows
     if N <= 1024:
         ref = oracle.nfft(x.astype(np.complex128))
