@@ -159,6 +159,19 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs):
     bp.close()
     del ds, dr, A
     torch.cuda.empty_cache()
+    # Eq. 12a through the NFFT (Sec. 3), the surface of the headline workload:
+    # 65536-sample lag products, 1024 lags, the 1024 centred bins
+    sc = scenes.radar_scene(N=65536)
+    ss = torch.from_numpy(sc.s_surv).to(dev)
+    sr = torch.from_numpy(sc.s_ref).to(dev)
+    pn = api.Plan(65536, p0=-512, nbins=1024, max_lags=1024, form="nfft", prec="fp32", device=dev)
+    An = torch.empty(1024, 1024, dtype=torch.complex64, device=dev)
+    ms = _time_ms(lambda: pn.caf(ss, sr, 0, 1024, out=An), 10, flush)
+    bfl = 1024 * 32768 * 16  # butterflies per surface: nlags x N/2 x log2 N
+    out["caf_nfft_65536_1024lags_1024bins"] = {"ms": ms, "cells_per_s": 1024 * 1024 / (ms / 1e3),
+                                               "butterflies_per_s": bfl / (ms / 1e3),
+                                               "launches": pn.last_launches()}
+    del pn, An, ss, sr
     # forward + backward, N = 16384, 512 x 512
     sc = scenes.radar_scene(N=16384, seed=4, nlags=512, nbins=512)
     mask = torch.from_numpy(scenes.differentiation_mask(sc)).to(dev)

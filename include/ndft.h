@@ -49,7 +49,10 @@ typedef enum {
 
 typedef enum {
     NDFT_FORM_DIRECT = 0,       /* (x) evaluated term by term on the CUDA cores */
-    NDFT_FORM_TERNARY_GEMM = 1  /* a (x) b = sgn(b) a + sgn(a) b as two dense contractions on tcgen05 */
+    NDFT_FORM_TERNARY_GEMM = 1, /* a (x) b = sgn(b) a + sgn(a) b as two dense contractions on tcgen05 */
+    NDFT_FORM_NFFT = 2          /* the Sec. 3 NFFT in place of the NDFT (N a power of two <= 65536,
+                                   FP32): ndft_exec gives the NFFT's bins p0 .. p0 + nbins - 1 and
+                                   caf_exec Eq. 12a with the NFFT over each lag product */
 } ndft_form;
 
 typedef enum {
@@ -68,7 +71,7 @@ typedef enum {
 /* Plan descriptor.  Output bins are k = p0 .. p0 + nbins - 1 (signed, taken
  * modulo N); nbins = 0 means N bins starting at p0. */
 typedef struct {
-    int32_t n;          /* transform / CPI length N >= 1 (NFFT: power of two, 2..2^20) */
+    int32_t n;          /* transform / CPI length N >= 1 (NFFT: power of two, 1..2^20) */
     int32_t p0;         /* first output bin */
     int32_t nbins;      /* number of output bins, 0 -> N */
     int32_t max_lags;   /* largest nlags a caf_exec / caf_backward call will pass (0: no CAF) */
@@ -115,7 +118,8 @@ ndft_status ndft_plan_destroy(ndft_plan_t plan);
 
 /* NDFT, Eq. 8 (Sec. 2): X[b][k] = sum_n W^(((p0+k) n) mod N) (x) x[b][n].
  * x: [batch][N], X: [batch][nbins]; complex64 (FP32, BF16X2) or Q1.14.
- * 0 <= batch <= max_batch. */
+ * 0 <= batch <= max_batch.  On an NDFT_FORM_NFFT plan: X[b][k] is bin
+ * (p0 + k) mod N of the NFFT of x[b] (see nfft_exec), bit for bit. */
 ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream);
 
 /* NFFT, Sec. 3: radix-2 decimation in time with every twiddle product
@@ -130,7 +134,10 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
  *   A[a][k] = sum_i ( s_surv[i] (x) conj(s_ref[i - l]) ) (x) W^((i p) mod N),
  *   l = lag0 + a (0 <= a < nlags), p = p0 + k (0 <= k < nbins),
  * s_ref[j] = 0 outside [0, N) unless NDFT_F_CIRCULAR_LAG.
- * s_surv, s_ref: [N]; A: [nlags][nbins]; 1 <= nlags <= max_lags. */
+ * s_surv, s_ref: [N]; A: [nlags][nbins]; 1 <= nlags <= max_lags.
+ * On an NDFT_FORM_NFFT plan the sum over i is the Sec. 3 NFFT of the lag
+ * product z_l (computed in fp32 as above): A[a][k] = NFFT(z_l)[(p0 + k) mod N],
+ * reproducible bit for bit. */
 ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                      int32_t nlags, void *A, cudaStream_t stream);
 
@@ -147,7 +154,8 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
  * with c_l[i] = conj(s_ref[i-l]), S[p][i] = sigma(W^(i p)), sigma(v) =
  * sgn(v_r) + j sgn(v_i): the derivative d(a (x) b)/da = sgn(b) of Eq. 1-2
  * (valid where no operand is 0), chained through Eq. 6 and Eq. 12a.
- * ds: [N].  s_surv is not read (the derivative does not depend on it a.e.). */
+ * ds: [N].  s_surv is not read (the derivative does not depend on it a.e.).
+ * NDFT_E_UNSUPPORTED on Q1.14 and NDFT_FORM_NFFT plans. */
 ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                          int32_t nlags, const void *dA, void *ds, cudaStream_t stream);
 

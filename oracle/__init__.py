@@ -216,6 +216,19 @@ def caf(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, flags: int = 
     return A
 
 
+def caf_nfft(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, flags: int = 0,
+             f32: bool = False) -> np.ndarray:
+    """Eq. 12a with the sum over samples taken by the Sec. 3 NFFT (the form the
+    paper simulates in Sec. 5): row a is the NFFT of the lag product for lag
+    lag0 + a, read at bins p0 .. p0 + nbins - 1 (mod N).  f32: lag product and
+    NFFT in fp32, one rounding per operation; else fp64.  Shape [nlags, nbins]."""
+    N = len(s_surv)
+    lp = lagprod_f32 if f32 else lagprod
+    Z = np.stack([lp(s_surv, s_ref, lag0 + a, flags) for a in range(nlags)])
+    X = nfft_f32(Z) if f32 else nfft(Z)
+    return X[:, (p0 + np.arange(nbins)) % N]
+
+
 def caf_cells(s_surv, s_ref, lags, bins, flags: int = 0, z32: bool = False) -> np.ndarray:
     """Eq. 12a at the listed (lag, bin) cells only."""
     ss, sr = _c128(s_surv), _c128(s_ref)

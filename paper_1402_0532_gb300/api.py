@@ -13,7 +13,7 @@ import torch
 
 from . import _lib as L
 
-_FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM}
+_FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM, "nfft": L.FORM_NFFT}
 _PRECS = {"fp32": L.PREC_FP32, "bf16x2": L.PREC_BF16X2, "q14": L.PREC_Q14}
 
 
@@ -37,8 +37,10 @@ def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
 class Plan:
     """A single-transform plan: ``ndft``, ``nfft``, ``caf``, ``caf_backward``.
 
-    form: "direct" (CUDA cores) or "ternary" (tcgen05 tensor cores);
-    prec: "fp32" / "q14" (direct) or "bf16x2" (ternary).
+    form: "direct" (CUDA cores), "ternary" (tcgen05 tensor cores) or "nfft"
+    (the Sec. 3 NFFT in place of the NDFT: ``ndft`` gives NFFT bins, ``caf``
+    Eq. 12a through the NFFT; N a power of two <= 65536);
+    prec: "fp32" / "q14" (direct), "bf16x2" (ternary), "fp32" (nfft).
     Bins are p0 .. p0 + nbins - 1 (nbins = 0 -> N)."""
 
     def __init__(self, n: int, *, p0: int = 0, nbins: int = 0, max_lags: int = 0, max_batch: int = 0,

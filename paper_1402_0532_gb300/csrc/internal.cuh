@@ -39,6 +39,8 @@ struct Plan {
     float2 *tw32 = nullptr;      // [N]
     short2 *twq = nullptr;       // [N]
     float2 *ang = nullptr;       // ternary form: two-level (cos, sin) table
+    float2 *nfft_ws = nullptr;   // 8192 <= N <= 65536: intermediate of the two-kernel NFFT
+    int64_t nfft_chunk = 0;      // vectors per pass through nfft_ws
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -143,7 +145,13 @@ size_t direct_ws_bytes(const ndft_desc &d, int sm_count);
 int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune);
 
 // nfft.cu
+constexpr int64_t kNfftChunkBytes = 64ll << 20;  // intermediate per chunk: stays in the 129 MB L2
+size_t nfft_ws_bytes(const ndft_desc &d, int64_t *chunk);
 cudaError_t launch_nfft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s, int *launches);
+cudaError_t launch_nfft_bins(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
+                             int *launches);
+cudaError_t launch_nfft_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags, void *A,
+                            cudaStream_t s, int *launches);
 
 // epilogue.cu
 cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s);

@@ -334,6 +334,41 @@ def test_caf_boundary_zero_and_conjugate(oracle):
                                   oracle.caf(s, s, 0, 1, 0, 4))
 
 
+def test_caf_nfft_literal_and_structure(oracle):
+    """Eq. 12a through the Sec. 3 NFFT: each row is the literal recursion applied
+    to the literal lag product, read at bins p0 .. p0 + nbins - 1 mod N; with
+    s_ref = delta at 0 the zero-lag product is the single impulse
+    s_surv[0] (x) 1 at n = 0, whose NFFT is that value at every bin (each odd
+    half is zero, W (x) 0 = 0); lags beyond the signal give 0."""
+    rng = np.random.default_rng(22)
+    for N in (1, 2, 8, 16):
+        ss = scenes.cn(rng, (N,))
+        sr = scenes.cn(rng, (N,))
+        if N > 2:
+            ss[2] = 0
+        for lag0, nlags, p0, nb in ((0, 3, 0, N), (-2, 4, -N // 2, max(1, N // 2)), (1, 2, 3, 1)):
+            got = oracle.caf_nfft(ss, sr, lag0, nlags, p0, nb)
+            for a in range(nlags):
+                z = literal.lagprod(literal.as_pairs(ss), literal.as_pairs(sr), lag0 + a)
+                row = _c(literal.nfft(z))
+                want = row[(p0 + np.arange(nb)) % N]
+                np.testing.assert_allclose(got[a], want, rtol=0, atol=1e-12)
+    N = 64
+    ss = scenes.cn(rng, (N,))
+    delta = np.zeros(N, complex)
+    delta[0] = 1.0
+    A = oracle.caf_nfft(ss, delta, 0, 1, 0, N)
+    v = complex(np.sign(ss[0].real) * (abs(ss[0].real) + 1), np.sign(ss[0].imag) * (abs(ss[0].imag) + 1))
+    np.testing.assert_array_equal(A[0], np.full(N, v))
+    assert np.all(oracle.caf_nfft(ss, ss, N, 2, 0, 8) == 0)
+    # bin 0 meets only W^0 = 1 at every stage: with small-integer inputs every
+    # intermediate is an exact integer, so the fp32 evaluation equals the fp64 one
+    si = (rng.integers(-8, 9, 16) + 1j * rng.integers(-8, 9, 16)).astype(np.complex64)
+    sr = si[::-1].copy()
+    np.testing.assert_array_equal(oracle.caf_nfft(si, sr, -3, 6, 0, 1, f32=True),
+                                  oracle.caf_nfft(si, sr, -3, 6, 0, 1).astype(np.complex64))
+
+
 def test_caf_z32_gate(oracle):
     """Forming the lag product in fp32 changes A by no more than fp32 rounding."""
     sc = scenes.radar_scene(N=2048, nlags=8, nbins=16, seed=21)
