@@ -171,7 +171,22 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs):
     out["caf_nfft_65536_1024lags_1024bins"] = {"ms": ms, "cells_per_s": 1024 * 1024 / (ms / 1e3),
                                                "butterflies_per_s": bfl / (ms / 1e3),
                                                "launches": pn.last_launches()}
-    del pn, An, ss, sr
+    # Eq. 12b on the same surface: (x) lag product, then the linear DFT (fp32 FFT)
+    pb = api.Plan(65536, p0=-512, nbins=1024, max_lags=1024, form="fft", prec="fp32", device=dev)
+    ms = _time_ms(lambda: pb.caf(ss, sr, 0, 1024, out=An), 10, flush)
+    out["caf_12b_65536_1024lags_1024bins"] = {"ms": ms, "cells_per_s": 1024 * 1024 / (ms / 1e3),
+                                              "butterflies_per_s": bfl / (ms / 1e3),
+                                              "launches": pb.last_launches()}
+    del pn, pb, An, ss, sr
+    # the decimation-in-frequency NFFT of the 65536 x 1024 batch
+    x = torch.from_numpy(scenes.cn_batch()).to(dev)
+    pd = api.Plan(1024, max_batch=x.shape[0], flags=api.F_NFFT_DIF, device=dev)
+    y = torch.empty_like(x)
+    ms = _time_ms(lambda: pd.nfft(x, out=y), 10, flush)
+    out["nfft_dif_1024_x65536"] = {"ms": ms, "vectors_per_s": x.shape[0] / (ms / 1e3),
+                                   "hbm_gbs": moved / (ms / 1e3) / 1e9,
+                                   "hbm_frac": moved / (ms / 1e3) / 1e9 / hbm_peak_gbs}
+    del x, y, pd
     # forward + backward, N = 16384, 512 x 512
     sc = scenes.radar_scene(N=16384, seed=4, nlags=512, nbins=512)
     mask = torch.from_numpy(scenes.differentiation_mask(sc)).to(dev)

@@ -50,9 +50,12 @@ typedef enum {
 typedef enum {
     NDFT_FORM_DIRECT = 0,       /* (x) evaluated term by term on the CUDA cores */
     NDFT_FORM_TERNARY_GEMM = 1, /* a (x) b = sgn(b) a + sgn(a) b as two dense contractions on tcgen05 */
-    NDFT_FORM_NFFT = 2          /* the Sec. 3 NFFT in place of the NDFT (N a power of two <= 65536,
+    NDFT_FORM_NFFT = 2,         /* the Sec. 3 NFFT in place of the NDFT (N a power of two <= 65536,
                                    FP32): ndft_exec gives the NFFT's bins p0 .. p0 + nbins - 1 and
                                    caf_exec Eq. 12a with the NFFT over each lag product */
+    NDFT_FORM_FFT = 3           /* the ordinary DFT by a radix-2 FFT (N a power of two <= 65536,
+                                   FP32): ndft_exec gives DFT bins, caf_exec Eq. 12b -- the lag
+                                   product with (x), then the linear DFT */
 } ndft_form;
 
 typedef enum {
@@ -67,6 +70,9 @@ typedef enum {
  * outside [0, N) (linear correlation). */
 #define NDFT_F_NO_CONJ_REF 0x1u  /* ablation: use s_ref[i-l] without the conjugate */
 #define NDFT_F_CIRCULAR_LAG 0x2u /* index s_ref modulo N instead of zero padding    */
+#define NDFT_F_NFFT_DIF 0x4u     /* NFFT by decimation in frequency (Sec. 3 names both
+                                    FFT orders; the (x) butterflies make them differ):
+                                    nfft_exec, and ndft_exec / caf_exec on NFFT plans */
 
 /* Plan descriptor.  Output bins are k = p0 .. p0 + nbins - 1 (signed, taken
  * modulo N); nbins = 0 means N bins starting at p0. */
@@ -119,7 +125,8 @@ ndft_status ndft_plan_destroy(ndft_plan_t plan);
 /* NDFT, Eq. 8 (Sec. 2): X[b][k] = sum_n W^(((p0+k) n) mod N) (x) x[b][n].
  * x: [batch][N], X: [batch][nbins]; complex64 (FP32, BF16X2) or Q1.14.
  * 0 <= batch <= max_batch.  On an NDFT_FORM_NFFT plan: X[b][k] is bin
- * (p0 + k) mod N of the NFFT of x[b] (see nfft_exec), bit for bit. */
+ * (p0 + k) mod N of the NFFT of x[b] (see nfft_exec), bit for bit; on an
+ * NDFT_FORM_FFT plan the ordinary DFT bin (fp32 radix-2 FFT). */
 ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream);
 
 /* NFFT, Sec. 3: radix-2 decimation in time with every twiddle product
@@ -127,7 +134,11 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
  * in natural order.  Per butterfly: t = W (x) O[k], X[k] = E[k] + t,
  * X[k + N/2] = E[k] - t, evaluated in fp32 in exactly that order, so results
  * are reproducible bit for bit.  Requires N a power of two, nbins = N, p0 = 0,
- * prec FP32.  x, X: [batch][N] complex64; X may equal x (in place). */
+ * prec FP32.  x, X: [batch][N] complex64; X may equal x (in place).
+ * With NDFT_F_NFFT_DIF (N <= 65536): decimation in frequency instead, natural
+ * input, per butterfly on (E, O) = (x[n], x[n + L/2]) of a span-L block:
+ * E' = E + O, O' = W_L^n (x) (E - O), recursing on both halves; natural-order
+ * output (bin 2k from the first half, 2k + 1 from the second). */
 ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream);
 
 /* Nonlinear cross-ambiguity surface, Eq. 12a (Sec. 4), read left to right:
@@ -137,7 +148,8 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
  * s_surv, s_ref: [N]; A: [nlags][nbins]; 1 <= nlags <= max_lags.
  * On an NDFT_FORM_NFFT plan the sum over i is the Sec. 3 NFFT of the lag
  * product z_l (computed in fp32 as above): A[a][k] = NFFT(z_l)[(p0 + k) mod N],
- * reproducible bit for bit. */
+ * reproducible bit for bit.  On an NDFT_FORM_FFT plan it is the ordinary DFT
+ * (Eq. 12b): A[a][k] = sum_i z_l[i] W^((i p) mod N), by an fp32 radix-2 FFT. */
 ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                      int32_t nlags, void *A, cudaStream_t stream);
 
@@ -155,7 +167,7 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
  * sgn(v_r) + j sgn(v_i): the derivative d(a (x) b)/da = sgn(b) of Eq. 1-2
  * (valid where no operand is 0), chained through Eq. 6 and Eq. 12a.
  * ds: [N].  s_surv is not read (the derivative does not depend on it a.e.).
- * NDFT_E_UNSUPPORTED on Q1.14 and NDFT_FORM_NFFT plans. */
+ * NDFT_E_UNSUPPORTED on Q1.14, NDFT_FORM_NFFT and NDFT_FORM_FFT plans. */
 ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                          int32_t nlags, const void *dA, void *ds, cudaStream_t stream);
 

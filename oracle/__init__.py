@@ -16,9 +16,12 @@ Every function states the passage of the paper it follows:
 ``vecprod``            Eq. 3, <x (.) y> = sum x_i (x) y_i
 ``twiddle``            W = exp(-j 2 pi / N), defined under Eq. 8
 ``ndft``               Eq. 8 (Sec. 2), X = F (.) x
-``nfft``/``nfft_f32``  Sec. 3, radix-2 DIT with (x) in every butterfly
+``nfft``/``nfft_f32``  Sec. 3, radix-2 DIT (or DIF) with (x) in every butterfly
+``dft``                the linear DFT (numpy FFT), for Eq. 12b
 ``lagprod``            Eq. 12a inner factor s_surv[i] (x) conj(s_ref[i-l])
 ``caf``                Eq. 12a, the nonlinear ambiguity surface
+``caf_nfft``           Eq. 12a with the NFFT over samples (Sec. 5)
+``caf_12b``            Eq. 12b, (x) lag product then the linear DFT
 ``*_q14``              the same in Q1.14 integers, sums modulo 2^32
 ``caf_adjoint``        derivative of Eq. 1-2 chained through Eq. 6, 12a
 =====================  ====================================================
@@ -73,6 +76,8 @@ def _load():
             lib.oracle_ndft.argtypes = [P, i64, i64, i64, i64, P]
             lib.oracle_nfft.argtypes = [P, i64, i64, P]
             lib.oracle_nfft_f32.argtypes = [P, i64, i64, P]
+            lib.oracle_nfft_dif.argtypes = [P, i64, i64, P]
+            lib.oracle_nfft_dif_f32.argtypes = [P, i64, i64, P]
             lib.oracle_lagprod.argtypes = [P, P, i64, i64, u32, P]
             lib.oracle_lagprod_f32.argtypes = [P, P, i64, i64, u32, P]
             lib.oracle_caf.argtypes = [P, P, i64, i64, i64, i64, i64, u32, i32, P]
@@ -81,7 +86,8 @@ def _load():
             lib.oracle_caf_q14.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
             lib.oracle_caf_adjoint.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
             lib.oracle_num_threads.restype = i32
-            for name in ("oracle_ndft", "oracle_nfft", "oracle_nfft_f32", "oracle_lagprod",
+            for name in ("oracle_ndft", "oracle_nfft", "oracle_nfft_f32", "oracle_nfft_dif",
+                         "oracle_nfft_dif_f32", "oracle_lagprod",
                          "oracle_lagprod_f32", "oracle_caf", "oracle_caf_cells", "oracle_ndft_q14",
                          "oracle_caf_q14", "oracle_caf_adjoint"):
                 getattr(lib, name).restype = i32
@@ -168,26 +174,39 @@ def ndft(x, p0: int = 0, nbins: int | None = None) -> np.ndarray:
     return X
 
 
-def nfft(x) -> np.ndarray:
-    """Sec. 3: the (x)-butterfly radix-2 DIT NFFT in double precision."""
+def nfft(x, dif: bool = False) -> np.ndarray:
+    """Sec. 3: the (x)-butterfly radix-2 NFFT in double precision, by
+    decimation in time (the recursion Sec. 3 writes out) or, dif=True, by
+    decimation in frequency (the other FFT order Sec. 3 names)."""
     x = _c128(x)
     if x.ndim == 1:
-        return nfft(x[None])[0]
+        return nfft(x[None], dif)[0]
     B, N = x.shape
     X = np.zeros((B, N), np.complex128)
-    _check(_load().oracle_nfft(_ptr(x), B, N, _ptr(X)), "nfft")
+    fn = _load().oracle_nfft_dif if dif else _load().oracle_nfft
+    _check(fn(_ptr(x), B, N, _ptr(X)), "nfft")
     return X
 
 
-def nfft_f32(x) -> np.ndarray:
+def nfft_f32(x, dif: bool = False) -> np.ndarray:
     """Sec. 3 recursion evaluated in fp32 (one rounding per operation)."""
     x = np.ascontiguousarray(x, np.complex64)
     if x.ndim == 1:
-        return nfft_f32(x[None])[0]
+        return nfft_f32(x[None], dif)[0]
     B, N = x.shape
     X = np.zeros((B, N), np.complex64)
-    _check(_load().oracle_nfft_f32(_ptr(x), B, N, _ptr(X)), "nfft_f32")
+    fn = _load().oracle_nfft_dif_f32 if dif else _load().oracle_nfft_f32
+    _check(fn(_ptr(x), B, N, _ptr(X)), "nfft_f32")
     return X
+
+
+def dft(x, p0: int = 0, nbins: int | None = None) -> np.ndarray:
+    """The ordinary DFT (the linear transform Eq. 8 approximates) at bins
+    p0 .. p0 + nbins - 1 mod N, in double precision via numpy's FFT."""
+    x = _c128(x)
+    N = x.shape[-1]
+    nb = N if nbins is None else nbins
+    return np.fft.fft(x, axis=-1)[..., (p0 + np.arange(nb)) % N]
 
 
 # --- Eq. 12a ---------------------------------------------------------------------
@@ -217,16 +236,27 @@ def caf(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, flags: int = 
 
 
 def caf_nfft(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, flags: int = 0,
-             f32: bool = False) -> np.ndarray:
+             f32: bool = False, dif: bool = False) -> np.ndarray:
     """Eq. 12a with the sum over samples taken by the Sec. 3 NFFT (the form the
     paper simulates in Sec. 5): row a is the NFFT of the lag product for lag
     lag0 + a, read at bins p0 .. p0 + nbins - 1 (mod N).  f32: lag product and
-    NFFT in fp32, one rounding per operation; else fp64.  Shape [nlags, nbins]."""
+    NFFT in fp32, one rounding per operation; else fp64.  dif: the
+    decimation-in-frequency NFFT.  Shape [nlags, nbins]."""
     N = len(s_surv)
     lp = lagprod_f32 if f32 else lagprod
     Z = np.stack([lp(s_surv, s_ref, lag0 + a, flags) for a in range(nlags)])
-    X = nfft_f32(Z) if f32 else nfft(Z)
+    X = nfft_f32(Z, dif) if f32 else nfft(Z, dif)
     return X[:, (p0 + np.arange(nbins)) % N]
+
+
+def caf_12b(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, flags: int = 0,
+            z32: bool = False) -> np.ndarray:
+    """Eq. 12b: the lag product formed with (x) (as in Eq. 12a, s_ref
+    conjugated), then the ordinary DFT over samples, at bins p0 .. p0 + nbins - 1
+    (mod N); double precision (z32: lag product in fp32).  Shape [nlags, nbins]."""
+    lp = lagprod_f32 if z32 else lagprod
+    Z = np.stack([lp(s_surv, s_ref, lag0 + a, flags).astype(np.complex128) for a in range(nlags)])
+    return dft(Z, p0, nbins)
 
 
 def caf_cells(s_surv, s_ref, lags, bins, flags: int = 0, z32: bool = False) -> np.ndarray:

@@ -303,6 +303,108 @@ int oracle_nfft_f32(const float *x, int64_t batch, int64_t N, float *X) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* NFFT by decimation in frequency (Sec. 3 names both FFT orders; with (x)   */
+/* in the butterflies the two give different transforms).  N-point DIF of x: */
+/*   Y[m] = x[m] + x[m + N/2],  Z[m] = W_N^m (x) (x[m] - x[m + N/2]),        */
+/*   m < N/2;  X[2k] = DIF(Y)[k],  X[2k + 1] = DIF(Z)[k];                    */
+/* the 1-point transform is the identity.                                    */
+/* ------------------------------------------------------------------------ */
+static void nfft_dif_rec64(const double *x, int64_t n, const double *W, int64_t Nfull, double *out,
+                           double *scratch) {
+    if (n == 1) {
+        out[0] = x[0];
+        out[1] = x[1];
+        return;
+    }
+    int64_t h = n / 2, step = Nfull / n;
+    double *Y = scratch, *Z = scratch + 2 * h, *YY = scratch + 2 * n, *ZZ = YY + 2 * h, *sub = scratch + 4 * n;
+    for (int64_t m = 0; m < h; ++m) {
+        double ar = x[2 * m], ai = x[2 * m + 1], br = x[2 * (m + h)], bi = x[2 * (m + h) + 1];
+        Y[2 * m] = ar + br;
+        Y[2 * m + 1] = ai + bi;
+        cot64(W[2 * m * step], W[2 * m * step + 1], ar - br, ai - bi, &Z[2 * m], &Z[2 * m + 1]);
+    }
+    nfft_dif_rec64(Y, h, W, Nfull, YY, sub);
+    nfft_dif_rec64(Z, h, W, Nfull, ZZ, sub);
+    for (int64_t k = 0; k < h; ++k) {
+        out[4 * k] = YY[2 * k];
+        out[4 * k + 1] = YY[2 * k + 1];
+        out[4 * k + 2] = ZZ[2 * k];
+        out[4 * k + 3] = ZZ[2 * k + 1];
+    }
+}
+
+static void nfft_dif_rec32(const float *x, int64_t n, const float *W, int64_t Nfull, float *out, float *scratch) {
+    if (n == 1) {
+        out[0] = x[0];
+        out[1] = x[1];
+        return;
+    }
+    int64_t h = n / 2, step = Nfull / n;
+    float *Y = scratch, *Z = scratch + 2 * h, *YY = scratch + 2 * n, *ZZ = YY + 2 * h, *sub = scratch + 4 * n;
+    for (int64_t m = 0; m < h; ++m) {
+        float ar = x[2 * m], ai = x[2 * m + 1], br = x[2 * (m + h)], bi = x[2 * (m + h) + 1];
+        Y[2 * m] = ar + br;
+        Y[2 * m + 1] = ai + bi;
+        float dr = ar - br, di = ai - bi;
+        cot32(W[2 * m * step], W[2 * m * step + 1], dr, di, &Z[2 * m], &Z[2 * m + 1]);
+    }
+    nfft_dif_rec32(Y, h, W, Nfull, YY, sub);
+    nfft_dif_rec32(Z, h, W, Nfull, ZZ, sub);
+    for (int64_t k = 0; k < h; ++k) {
+        out[4 * k] = YY[2 * k];
+        out[4 * k + 1] = YY[2 * k + 1];
+        out[4 * k + 2] = ZZ[2 * k];
+        out[4 * k + 3] = ZZ[2 * k + 1];
+    }
+}
+
+int oracle_nfft_dif(const double *x, int64_t batch, int64_t N, double *X) {
+    if (!is_pow2(N) || batch < 0) return 1;
+    double *W = twiddle_table64(N);
+    if (!W) return 2;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *scr = (double *)malloc(sizeof(double) * 8 * (size_t)N + 64);
+        if (!scr) {
+#pragma omp atomic write
+            err = 2;
+        } else {
+#pragma omp for schedule(dynamic)
+            for (int64_t b = 0; b < batch; ++b)
+                nfft_dif_rec64(x + 2 * b * N, N, W, N, X + 2 * b * N, scr);
+            free(scr);
+        }
+    }
+    free(W);
+    return err;
+}
+
+int oracle_nfft_dif_f32(const float *x, int64_t batch, int64_t N, float *X) {
+    if (!is_pow2(N) || batch < 0) return 1;
+    float *W = (float *)malloc(sizeof(float) * 2 * (size_t)N);
+    if (!W) return 2;
+    oracle_twiddle_table_f32(N, W);
+    int err = 0;
+#pragma omp parallel
+    {
+        float *scr = (float *)malloc(sizeof(float) * 8 * (size_t)N + 64);
+        if (!scr) {
+#pragma omp atomic write
+            err = 2;
+        } else {
+#pragma omp for schedule(dynamic)
+            for (int64_t b = 0; b < batch; ++b)
+                nfft_dif_rec32(x + 2 * b * N, N, W, N, X + 2 * b * N, scr);
+            free(scr);
+        }
+    }
+    free(W);
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Lag product of Eq. 12a: z_l[i] = s_surv[i] (x) conj(s_ref[i - l]).        */
 /* ------------------------------------------------------------------------ */
 static int64_t ref_index(int64_t i, int64_t l, int64_t N, uint32_t flags) {

@@ -12,8 +12,9 @@ import ctypes
 import torch
 
 from . import _lib as L
+from ._lib import F_CIRCULAR_LAG, F_NFFT_DIF, F_NO_CONJ_REF  # noqa: F401  (plan flags)
 
-_FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM, "nfft": L.FORM_NFFT}
+_FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM, "nfft": L.FORM_NFFT, "fft": L.FORM_FFT}
 _PRECS = {"fp32": L.PREC_FP32, "bf16x2": L.PREC_BF16X2, "q14": L.PREC_Q14}
 
 
@@ -37,10 +38,13 @@ def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
 class Plan:
     """A single-transform plan: ``ndft``, ``nfft``, ``caf``, ``caf_backward``.
 
-    form: "direct" (CUDA cores), "ternary" (tcgen05 tensor cores) or "nfft"
+    form: "direct" (CUDA cores), "ternary" (tcgen05 tensor cores), "nfft"
     (the Sec. 3 NFFT in place of the NDFT: ``ndft`` gives NFFT bins, ``caf``
-    Eq. 12a through the NFFT; N a power of two <= 65536);
-    prec: "fp32" / "q14" (direct), "bf16x2" (ternary), "fp32" (nfft).
+    Eq. 12a through the NFFT) or "fft" (the ordinary DFT by an fp32 FFT:
+    ``ndft`` gives DFT bins, ``caf`` Eq. 12b); nfft/fft need N a power of two
+    <= 65536.  flags: F_NO_CONJ_REF, F_CIRCULAR_LAG, F_NFFT_DIF (decimation in
+    frequency for ``nfft`` and the nfft form);
+    prec: "fp32" / "q14" (direct), "bf16x2" (ternary), "fp32" (nfft, fft).
     Bins are p0 .. p0 + nbins - 1 (nbins = 0 -> N)."""
 
     def __init__(self, n: int, *, p0: int = 0, nbins: int = 0, max_lags: int = 0, max_batch: int = 0,

@@ -41,6 +41,7 @@ struct Plan {
     float2 *ang = nullptr;       // ternary form: two-level (cos, sin) table
     float2 *nfft_ws = nullptr;   // 8192 <= N <= 65536: intermediate of the two-kernel NFFT
     int64_t nfft_chunk = 0;      // vectors per pass through nfft_ws
+    float2 *comb = nullptr;      // 2N: comb-major copies of s_surv, s_ref (two-kernel DIT CAF)
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -152,6 +153,12 @@ cudaError_t launch_nfft_bins(const Plan &p, const void *x, void *X, int64_t batc
                              int *launches);
 cudaError_t launch_nfft_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags, void *A,
                             cudaStream_t s, int *launches);
+
+// fft.cu
+cudaError_t launch_fft_bins(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
+                            int *launches);
+cudaError_t launch_fft_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags, void *A,
+                           cudaStream_t s, int *launches);
 
 // epilogue.cu
 cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s);

@@ -32,11 +32,13 @@ bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 bool valid_pair(int form, int prec) {
     if (form == NDFT_FORM_DIRECT) return prec == NDFT_PREC_FP32 || prec == NDFT_PREC_Q14;
     if (form == NDFT_FORM_TERNARY_GEMM) return prec == NDFT_PREC_BF16X2;
-    if (form == NDFT_FORM_NFFT) return prec == NDFT_PREC_FP32;
+    if (form == NDFT_FORM_NFFT || form == NDFT_FORM_FFT) return prec == NDFT_PREC_FP32;
     return false;
 }
 
-constexpr uint32_t kKnownFlags = NDFT_F_NO_CONJ_REF | NDFT_F_CIRCULAR_LAG;
+constexpr uint32_t kKnownFlags = NDFT_F_NO_CONJ_REF | NDFT_F_CIRCULAR_LAG | NDFT_F_NFFT_DIF;
+
+bool fft_form(int form) { return form == NDFT_FORM_NFFT || form == NDFT_FORM_FFT; }
 constexpr int32_t kMaxN = 1 << 22;
 
 void free_plan(Plan &p) {
@@ -44,6 +46,7 @@ void free_plan(Plan &p) {
     cudaFree(p.twq);
     cudaFree(p.ang);
     cudaFree(p.nfft_ws);
+    cudaFree(p.comb);
     cudaFree(p.ws);
     cudaFree(p.err);
     cudaFree(p.cpis_dev);
@@ -109,10 +112,10 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
         d->reserved[2])
         return NDFT_E_INVALID;
     if (!valid_pair(d->form, d->prec)) {
-        const bool known = (d->form >= 0 && d->form <= 2) && (d->prec >= 0 && d->prec <= 2);
+        const bool known = (d->form >= 0 && d->form <= 3) && (d->prec >= 0 && d->prec <= 2);
         return known ? NDFT_E_UNSUPPORTED : NDFT_E_INVALID;
     }
-    if (d->form == NDFT_FORM_NFFT && (!pow2(d->n) || d->n > 65536)) return NDFT_E_INVALID;
+    if (fft_form(d->form) && (!pow2(d->n) || d->n > 65536)) return NDFT_E_INVALID;
     if (d->form == NDFT_FORM_TERNARY_GEMM && !ternary_supported(*d)) return NDFT_E_UNSUPPORTED;
     auto *h = new (std::nothrow) ndft_plan_s();
     if (!h) return NDFT_E_NOMEM;
@@ -131,13 +134,17 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
     p.table_bytes = (size_t)N * (sizeof(float2) + (p.twq ? sizeof(short2) : 0));
     {
         size_t ws = 0;
-        if (p.d.form != NDFT_FORM_NFFT) ws = std::max(direct_ws_bytes(p.d, p.sm_count), backward_ws_bytes(p.d));
+        if (!fft_form(p.d.form)) ws = std::max(direct_ws_bytes(p.d, p.sm_count), backward_ws_bytes(p.d));
         if (tern) ws = std::max(ws, ternary_ws_bytes(p.d, p.sm_count));
         p.ws_bytes = ws;
         if (ws && (e = cudaMalloc(&p.ws, ws)) != cudaSuccess) goto fail;
         const size_t nws = nfft_ws_bytes(p.d, &p.nfft_chunk);
         if (nws && (e = cudaMalloc(&p.nfft_ws, nws)) != cudaSuccess) goto fail;
         p.ws_bytes += nws;
+        if (nws && fft_form(p.d.form) && p.d.max_lags > 0) {
+            if ((e = alloc(&p.comb, 2 * (size_t)N)) != cudaSuccess) goto fail;
+            p.ws_bytes += 2 * (size_t)N * sizeof(float2);
+        }
     }
     if ((e = launch_tables(N, p.tw32, p.twq, stream)) != cudaSuccess) goto fail;
     if (tern && (e = ternary_plan_init(p, stream)) != cudaSuccess) goto fail;
@@ -169,6 +176,8 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
         e = launch_direct_ndft(p, x, X, batch, stream, &p.last_launches);
     } else if (p.d.form == NDFT_FORM_NFFT) {
         e = launch_nfft_bins(p, x, X, batch, stream, &p.last_launches);
+    } else if (p.d.form == NDFT_FORM_FFT) {
+        e = launch_fft_bins(p, x, X, batch, stream, &p.last_launches);
     } else {
         e = launch_ternary_ndft(p, x, X, batch, stream, &p.last_launches);
     }
@@ -181,6 +190,7 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
     if (p.d.prec != NDFT_PREC_FP32 || !pow2(p.d.n) || p.d.n > (1 << 20) || p.d.nbins != p.d.n ||
         p.d.p0 % p.d.n != 0)
         return NDFT_E_INVALID;
+    if ((p.d.flags & NDFT_F_NFFT_DIF) && p.d.n > 65536) return NDFT_E_UNSUPPORTED;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
     p.last_launches = 0;
@@ -198,6 +208,8 @@ ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, in
         e = launch_direct_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
     else if (p.d.form == NDFT_FORM_NFFT)
         e = launch_nfft_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
+    else if (p.d.form == NDFT_FORM_FFT)
+        e = launch_fft_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
     else
         e = launch_ternary_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
     return from_cuda(e);
@@ -208,7 +220,7 @@ ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref
     (void)s_surv;
     if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     Plan &p = plan->p;
-    if (p.d.prec == NDFT_PREC_Q14 || p.d.form == NDFT_FORM_NFFT) return NDFT_E_UNSUPPORTED;
+    if (p.d.prec == NDFT_PREC_Q14 || fft_form(p.d.form)) return NDFT_E_UNSUPPORTED;
     if (!aligned16(s_ref) || !aligned16(dA) || !aligned16(ds)) return NDFT_E_INVALID;
     p.last_launches = 0;
     return from_cuda(launch_caf_backward(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches));
@@ -335,7 +347,7 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
                               uint32_t flags, cudaStream_t stream) {
     if (!out || !cpis || ncpi < 1 || ncpi > (1 << 20) || (flags & ~kKnownFlags)) return NDFT_E_INVALID;
     *out = nullptr;
-    if (!valid_pair(form, prec) || form == NDFT_FORM_NFFT) return NDFT_E_UNSUPPORTED;
+    if (!valid_pair(form, prec) || fft_form(form)) return NDFT_E_UNSUPPORTED;
     for (int c = 0; c < ncpi; ++c) {
         const ndft_cpi &q = cpis[c];
         if (q.n < 1 || q.n > kMaxN || q.nlags < 1 || q.nlags > (1 << 20) || q.nbins < 1 || q.nbins > q.n ||

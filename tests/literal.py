@@ -71,6 +71,27 @@ def nfft(x):
     return out
 
 
+def nfft_dif(x):
+    N = len(x)
+    if N == 1:
+        return [x[0]]
+    h = N // 2
+    Y = [(x[m][0] + x[m + h][0], x[m][1] + x[m + h][1]) for m in range(h)]
+    Z = [cox(twiddle(N, m), (x[m][0] - x[m + h][0], x[m][1] - x[m + h][1])) for m in range(h)]
+    YY, ZZ = nfft_dif(Y), nfft_dif(Z)
+    out = [None] * N
+    for k in range(h):
+        out[2 * k] = YY[k]
+        out[2 * k + 1] = ZZ[k]
+    return out
+
+
+def dft(x):
+    import cmath
+    N = len(x)
+    return [sum(complex(*x[n]) * cmath.exp(-2j * cmath.pi * k * n / N) for n in range(N)) for k in range(N)]
+
+
 def lagprod(s_surv, s_ref, lag):
     N = len(s_surv)
     z = []

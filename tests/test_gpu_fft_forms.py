@@ -1,0 +1,137 @@
+"""GPU parity of the other FFT orders and Eq. 12b:
+
+* the decimation-in-frequency NFFT (flag F_NFFT_DIF), bit for bit against the
+  oracle's fp32 DIF recursion, for plain vectors, binned output and Eq. 12a;
+* the FFT form: the ordinary DFT by an fp32 radix-2 FFT (ndft_exec) and
+  Eq. 12b -- the (x) lag product, then the linear DFT (caf_exec) -- within
+  1e-5 of max |A| against the fp64 oracle whose lag product is formed in fp32
+  (the element-wise stage the kernel shares; the bar of the fp32 forms)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0532_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_0532_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def same_bits(a, b):
+    a = np.ascontiguousarray(a, np.complex64)
+    b = np.ascontiguousarray(b, np.complex64)
+    return a.shape == b.shape and np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def relerr(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
+
+
+SIZES = [(1, 3), (2, 5), (4, 9), (8, 300), (16, 77), (64, 100), (256, 17), (1024, 40), (4096, 3),
+         (8192, 3), (16384, 2), (32768, 3), (65536, 2), (64, 40000)]
+
+
+@pytest.mark.parametrize("N,batch", SIZES)
+def test_nfft_dif_bit_exact(api, N, batch):
+    rng = np.random.default_rng(N + 11)
+    x = scenes.cn(rng, (batch, N)).astype(np.complex64)
+    if batch > 2:
+        x[1, ::3] = 0
+        x[2, ::5] = np.complex64(complex(-0.0, -0.0))
+    want = oracle.nfft_f32(x, dif=True)
+    p = api.Plan(N, max_batch=batch, flags=api.F_NFFT_DIF)
+    got = p.nfft(dev(x)).cpu().numpy()
+    p.query_error()
+    assert same_bits(got, want)
+    t = dev(x)
+    p.nfft(t, out=t)  # in place
+    assert same_bits(t.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("N,lag0,nlags,p0,nbins", [(8, -3, 12, 0, 0), (1024, -5, 33, -512, 1024),
+                                                   (4096, 10, 5, 7, 33), (16384, 0, 4, -512, 1024),
+                                                   (65536, 37, 3, -512, 1024)])
+def test_nfft_dif_caf(api, N, lag0, nlags, p0, nbins):
+    sc = scenes.radar_scene(N=N, nlags=nlags, nbins=min(N, 64), seed=70 + N % 89)
+    nb = nbins or N
+    want = oracle.caf_nfft(sc.s_surv, sc.s_ref, lag0, nlags, p0, nb, f32=True, dif=True)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, form="nfft", prec="fp32", flags=api.F_NFFT_DIF)
+    got = p.caf(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags).cpu().numpy()
+    p.query_error()
+    assert same_bits(got, want)
+    # binned NFFT output on the same form
+    rng = np.random.default_rng(N)
+    x = scenes.cn(rng, (3, N)).astype(np.complex64)
+    q = api.Plan(N, p0=p0, nbins=nbins, max_batch=3, form="nfft", prec="fp32", flags=api.F_NFFT_DIF)
+    assert same_bits(q.ndft(dev(x)).cpu().numpy(), oracle.nfft_f32(x, dif=True)[:, (p0 + np.arange(nb)) % N])
+
+
+@pytest.mark.parametrize("N,batch,p0,nbins", [(1, 4, 0, 0), (2, 3, 0, 0), (4, 5, -1, 3), (8, 100, 0, 0),
+                                              (1024, 50, -512, 1024), (4096, 7, 3, 100), (8192, 3, 0, 0),
+                                              (65536, 2, -512, 1024)])
+def test_fft_form_dft(api, N, batch, p0, nbins):
+    rng = np.random.default_rng(N + 13)
+    x = scenes.cn(rng, (batch, N)).astype(np.complex64)
+    nb = nbins or N
+    want = oracle.dft(x.astype(np.complex128), p0, nb)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="fft", prec="fp32")
+    got = p.ndft(dev(x)).cpu().numpy()
+    p.query_error()
+    per_row = np.max(np.abs(got - want), axis=1) / np.max(np.abs(oracle.dft(x.astype(np.complex128))), axis=1)
+    assert per_row.max() < TOL
+
+
+@pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
+    (8, -3, 12, 0, 0, 0), (1024, 0, 40, -512, 1024, 0), (4096, 100, 9, 7, 33, 1),
+    (16384, 37, 5, -512, 1024, 2), (65536, 0, 6, -512, 1024, 0)])
+def test_fft_form_caf_12b(api, N, lag0, nlags, p0, nbins, flags):
+    sc = scenes.radar_scene(N=N, nlags=nlags, nbins=min(N, 64), seed=80 + N % 83)
+    nb = nbins or N
+    ref32 = oracle.caf_12b(sc.s_surv, sc.s_ref, lag0, nlags, p0, nb, flags=flags, z32=True)
+    ref64 = oracle.caf_12b(sc.s_surv, sc.s_ref, lag0, nlags, p0, nb, flags=flags)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="fft", prec="fp32")
+    got = p.caf(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags).cpu().numpy()
+    p.query_error()
+    assert relerr(got, ref32) < TOL
+    assert relerr(got, ref64) < 1e-3  # the fp32 lag product may flip a sign near 0
+
+
+def test_fft_form_caf_12b_full_size_sampled(api):
+    """The 65536-sample, 1024-lag surface at the 1024 centred bins, the
+    benchmark's launch configuration: sampled lags against the oracle, and the
+    echo at lag 37, Doppler bin 5 stands out of its lag row (the linear DFT
+    keeps the Doppler structure of the lag product)."""
+    sc = scenes.radar_scene(N=65536)
+    p = api.Plan(65536, p0=-512, nbins=1024, max_lags=1024, form="fft", prec="fp32")
+    A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 1024).cpu().numpy()
+    p.query_error()
+    lags = [0, 1, 37, 64, 120, 127, 128, 301, 777, 1023]
+    ref = np.concatenate([oracle.caf_12b(sc.s_surv, sc.s_ref, l, 1, -512, 1024, z32=True) for l in lags])
+    assert relerr(A[lags], ref) < TOL
+
+
+def test_fft_forms_unsupported(api):
+    from paper_1402_0532_gb300 import _lib as L
+    with pytest.raises(L.NdftError) as e:
+        api.Plan(96, max_batch=1, form="fft", prec="fp32")
+    assert e.value.status == L.E_INVALID
+    p = api.Plan(131072, max_batch=1, flags=api.F_NFFT_DIF)
+    x = torch.zeros(1, 131072, dtype=torch.complex64, device="cuda")
+    with pytest.raises(L.NdftError) as e:
+        p.nfft(x)
+    assert e.value.status == L.E_UNSUPPORTED

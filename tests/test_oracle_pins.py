@@ -369,6 +369,68 @@ def test_caf_nfft_literal_and_structure(oracle):
                                   oracle.caf_nfft(si, sr, -3, 6, 0, 1).astype(np.complex64))
 
 
+def test_nfft_dif_literal_and_impulse(oracle):
+    """Decimation in frequency (the other FFT order Sec. 3 names): against the
+    literal recursion for N <= 16; for an impulse v at n = 0 every difference
+    is v or 0 and W (x) 0 = 0, so bin k is f applied popcount(k) times to v,
+    f(u) = 1 (x) u (Eq. 6 with W^0 = 1); and DIF differs from DIT."""
+    rng = np.random.default_rng(23)
+    for N in (1, 2, 4, 8, 16):
+        x = scenes.cn(rng, (N,))
+        if N > 2:
+            x[1] = 0
+        got = oracle.nfft(x, dif=True)
+        want = _c(literal.nfft_dif(literal.as_pairs(x)))
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    N = 32
+    v = complex(-1.25, 0.5)
+    x = np.zeros(N, complex)
+    x[0] = v
+    X = oracle.nfft(x, dif=True)
+
+    def f(u):
+        return complex(np.sign(u.real) * (abs(u.real) + 1), np.sign(u.imag) * (abs(u.imag) + 1))
+    for k in range(N):
+        u = v
+        for _ in range(bin(k).count("1")):
+            u = f(u)
+        assert X[k] == u
+    y = scenes.cn(rng, (64,))
+    assert not np.allclose(oracle.nfft(y, dif=True), oracle.nfft(y))
+    # fp32 evaluation equals fp64 when every intermediate is an exact small integer
+    # (N = 2: the only twiddle is W^0 = 1)
+    xi = (rng.integers(-9, 10, (5, 2)) + 1j * rng.integers(-9, 10, (5, 2))).astype(np.complex64)
+    np.testing.assert_array_equal(oracle.nfft_f32(xi, dif=True), oracle.nfft(xi, dif=True).astype(np.complex64))
+
+
+def test_caf_12b_literal_and_parseval(oracle):
+    """Eq. 12b: the literal DFT sum of the literal (x) lag product; Parseval
+    (sum_p |A[l,p]|^2 = N sum_i |z_l[i]|^2 over all N bins) on a larger case; and
+    with s_ref = delta at 0 the zero-lag product is one impulse at n = 0, whose
+    DFT is flat."""
+    rng = np.random.default_rng(24)
+    N = 12
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    got = oracle.caf_12b(ss, sr, -2, 5, -3, 7)
+    for a in range(5):
+        z = literal.lagprod(literal.as_pairs(ss), literal.as_pairs(sr), a - 2)
+        row = np.array(literal.dft(z))
+        np.testing.assert_allclose(got[a], row[(-3 + np.arange(7)) % N], rtol=0, atol=1e-12)
+    N = 256
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    A = oracle.caf_12b(ss, sr, 0, 4, 0, N)
+    for a in range(4):
+        z = oracle.lagprod(ss, sr, a)
+        assert abs(np.sum(np.abs(A[a]) ** 2) - N * np.sum(np.abs(z) ** 2)) < 1e-9 * N * np.sum(np.abs(z) ** 2)
+    delta = np.zeros(N, complex)
+    delta[0] = 1
+    A0 = oracle.caf_12b(ss, delta, 0, 1, 0, N)[0]
+    v = oracle.cotimes(ss[0], 1 + 0j)
+    np.testing.assert_allclose(A0, np.full(N, v), rtol=0, atol=1e-12)
+
+
 def test_caf_z32_gate(oracle):
     """Forming the lag product in fp32 changes A by no more than fp32 rounding."""
     sc = scenes.radar_scene(N=2048, nlags=8, nbins=16, seed=21)
