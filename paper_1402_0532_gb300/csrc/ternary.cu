@@ -179,6 +179,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -190,7 +197,6 @@ __device__ __forceinline__ void red_add_f32(float *addr, float v) {
 }
 
 __device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory"); }
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
 // Bulk tensor copies of a staged [32 columns][128 rows] fp32 block to the
 // output map at {row, column, split}: plain store, or element-wise add in L2.
@@ -207,7 +213,7 @@ __device__ __forceinline__ void tma_reduce_out(const CUtensorMap *map, uint32_t 
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // ---- unit decoding -------------------------------------------------------------
@@ -263,8 +269,11 @@ __device__ __forceinline__ Work decode(int64_t u, const Problem &single, const P
 // ---- A generation: one (bin, sample) pair -> rows 2 pl and 2 pl + 1 ------------
 // u = 4 m, m = (p i) mod N; theta = 2 pi m / N = q pi/2 + a with q = floor(u / N),
 // a = (pi/2) r / N, r = u - q N.  cos a, sin a from the two-level table.
-__device__ __forceinline__ void gen_pair(uint32_t a_stage, int pl, int t, uint32_t u, uint32_t N,
-                                         const float2 *__restrict__ thi, const float2 *__restrict__ tlo) {
+// The 8 K entries of the Re row go to re[], those of the Im row to im[]; the
+// caller stores them after all of its pairs are computed, so the table loads of
+// every pair are in flight together.
+__device__ __forceinline__ void gen_pair(uint32_t u, uint32_t N, const float2 *__restrict__ thi,
+                                         const float2 *__restrict__ tlo, uint4 &re, uint4 &im) {
     const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
     const uint32_t r = u - q * N;
     const float2 h = thi[r >> 8];
@@ -288,11 +297,18 @@ __device__ __forceinline__ void gen_pair(uint32_t a_stage, int pl, int t, uint32
     // ternary sign pattern, exact: 0 where the magnitude is exactly 0
     const uint32_t sr = (mr == 0.f) ? 0u : (0x3F803F80u ^ neg_r);  // [S_r, S_r]
     const uint32_t si = (mi == 0.f) ? 0u : (0x3F803F80u ^ neg_i);  // [S_i, S_i]
+    re = make_uint4(sr, si ^ 0x80008000u, wr, wi ^ 0x80008000u);
+    im = make_uint4(si, sr, wi, wr);
+}
+
+// Rows 2 pl (Re) and 2 pl + 1 (Im), 16-byte chunk t of the 128-byte row, in the
+// 128-byte-swizzled K-major layout the MMA descriptors expect.
+__device__ __forceinline__ void store_pair(uint32_t a_stage, int pl, int t, const uint4 &re, const uint4 &im) {
     const uint32_t row_re = 2u * pl, row_im = row_re + 1u;
     const uint32_t base_re = a_stage + row_re * 128u + (((uint32_t)t ^ (row_re & 7u)) << 4);
     const uint32_t base_im = a_stage + row_im * 128u + (((uint32_t)t ^ (row_im & 7u)) << 4);
-    sts128(base_re, sr, si ^ 0x80008000u, wr, wi ^ 0x80008000u);
-    sts128(base_im, si, sr, wi, wr);
+    sts128(base_re, re.x, re.y, re.z, re.w);
+    sts128(base_im, im.x, im.y, im.z, im.w);
 }
 
 // MH row halves of 128 rows per tile.  MH = 2: 256 x 256 tile, one TMEM
@@ -309,7 +325,7 @@ struct Tile {
     static constexpr size_t kSmemB = kSmemA + (size_t)kStages * kABytes;
     static constexpr size_t kSmemTab = kSmemB + (size_t)kStages * B_BYTES;
     static constexpr size_t kSmemStage = (kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2) + 127) / 128 * 128;
-    static constexpr size_t kSmemBar = kSmemStage + 32 * 128 * sizeof(float);  // [32 cols][128 rows] fp32
+    static constexpr size_t kSmemBar = kSmemStage + 4 * 4096;  // per epilogue warp 2 x [16 cols][32 rows] fp32
     static constexpr size_t kSmemTotal = kSmemBar + 160 + 1024;  // barriers, flags, alignment slack
 };
 
@@ -464,12 +480,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kb = w.kb0; kb < w.kb1; ++kb) {
                 if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                 const uint32_t a_st = a_base + stage * T::kABytes;
+                uint4 vre[PPT], vim[PPT];
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    gen_pair(a_st, pg + 32 * j, t, uu[j], N, s_thi, s_tlo);
+                    gen_pair(uu[j], N, s_thi, s_tlo, vre[j], vim[j]);
                     uu[j] += dd[j];
                     if (uu[j] >= 4u * N) uu[j] -= 4u * N;
                 }
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) store_pair(a_st, pg + 32 * j, t, vre[j], vim[j]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[stage]);
@@ -497,41 +516,62 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // deterministic.
                 const bool first = (c0 == w.kb0);
                 if (out_tma) {
-                    // Stage each 32-column group as [32 cols][128 rows] in shared memory and
-                    // hand it to one bulk tensor store (first chain) or add (later chains).
-                    // The previous chain's bulk operations are complete before this chain's
-                    // start, so the additions land in chain order.
-                    const int et = threadIdx.x - 32 * kEpiWarp0;
-                    const uint32_t stg = smem_u32(smem + T::kSmemStage);
-                    float *stg_f = reinterpret_cast<float *>(smem + T::kSmemStage);
-#pragma unroll 1
-                    for (int h = 0; h < MH; ++h) {
-#pragma unroll 1
-                        for (int cc = 0; cc < TN; cc += 32) {
-                            uint32_t r[32];
-                            tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf + h) * TN + cc), r);
-                            tmem_wait_ld();
-                            if (et == 0) {
-                                if (h == 0 && cc == 0) bulk_wait_all();
-                                else bulk_wait_read();
-                            }
-                            epi_bar();
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) stg_f[j * 128 + 32 * quarter + lane] = __uint_as_float(r[j]);
-                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            epi_bar();
-                            if (et == 0) {
-                                const int mrow = w.mt * T::kRows + 128 * h;
-                                const int col = w.nt * TN + cc;
-                                if (first) tma_store_out(&omap, stg, mrow, col, w.split);
-                                else tma_reduce_out(&omap, stg, mrow, col, w.split);
-                                bulk_commit();
-                            }
+                    // Each epilogue warp drains its own 32 TMEM lanes (rows) on its own:
+                    // 16-column groups go TMEM -> registers -> one of two 2 KB staging
+                    // buffers [16 cols][32 rows] -> one bulk tensor store (first chain)
+                    // or add (later chains) issued by lane 0.  The next group's TMEM
+                    // load is in flight while the current one is staged, and a buffer
+                    // is refilled once the bulk copy issued two groups earlier has read
+                    // it.  Lane 0 waits for all of its previous chain's copies before
+                    // the first copy of a chain, so the additions to each row land in
+                    // chain order (deterministic sums).  TMEM is released as soon as
+                    // the warp's last load has completed.
+                    const uint32_t wst = smem_u32(smem + T::kSmemStage) + (uint32_t)quarter * 4096u;
+                    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+                    const int mrow0 = w.mt * T::kRows + 32 * quarter;
+                    constexpr int GPH = TN / 16;       // 16-column groups per row half
+                    constexpr int NG = MH * GPH;       // groups per chain (even)
+                    auto tcol = [&](int g) { return (uint32_t)((buf + g / GPH) * TN + (g % GPH) * 16); };
+                    auto drain = [&](const uint32_t (&r)[16], int g) {
+                        const uint32_t sb = wst + (uint32_t)(g & 1) * 2048u;
+                        if (lane == 0) {
+                            if (g == 0) bulk_wait_all();
+                            else bulk_wait_read1();
                         }
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(sb + (uint32_t)(j * 32 + lane) * 4u), "r"(r[j])
+                                         : "memory");
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) {
+                            const int mrow = mrow0 + 128 * (g / GPH);
+                            const int col = w.nt * TN + (g % GPH) * 16;
+                            if (first) tma_store_out(&omap, sb, mrow, col, w.split);
+                            else tma_reduce_out(&omap, sb, mrow, col, w.split);
+                            bulk_commit();
+                        }
+                    };
+                    uint32_t ra[16], rb[16];
+                    tmem_ld16(trow + tcol(0), ra);
+                    tmem_wait_ld();
+#pragma unroll 1
+                    for (int g = 0; g < NG; g += 2) {
+                        tmem_ld16(trow + tcol(g + 1), rb);
+                        drain(ra, g);
+                        tmem_wait_ld();
+                        const bool more = g + 2 < NG;
+                        if (more) {
+                            tmem_ld16(trow + tcol(g + 2), ra);
+                        } else {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+                        }
+                        drain(rb, g + 1);
+                        if (more) tmem_wait_ld();
                     }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tmem_empty[buf]);
                     continue;
                 }
 #pragma unroll 1
@@ -564,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(&tmem_empty[buf]);
             }
         }
-        if (out_tma && threadIdx.x == 32 * kEpiWarp0) bulk_wait_all();  // bulk writes done before exit
+        if (out_tma && lane == 0) bulk_wait_all();  // this warp's bulk copies done before exit
     }
 
     __syncthreads();
@@ -710,15 +750,15 @@ cudaError_t make_tmap(void *base, int64_t rows, CUtensorMap *map, int box_rows =
 }
 
 // Output (or split partials) as a 3-D fp32 tensor {2 nbins rows, ncols, nsplit},
-// box 128 rows x 32 columns x 1 split, no swizzle: the epilogue's bulk
-// stores / adds.  Needs 2 nbins * 4 bytes to be a multiple of 16 (nbins even).
+// box 32 rows x 16 columns x 1 split, no swizzle: the epilogue warps' bulk
+// stores / adds (one warp's 32 TMEM lanes, a 16-column group).  Needs 2 nbins * 4 bytes to be a multiple of 16 (nbins even).
 cudaError_t make_out_map(void *base, int nbins, int ncols, int nsplit, CUtensorMap *map) {
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t rows = 2ull * nbins;
     cuuint64_t dims[3] = {rows, (cuuint64_t)ncols, (cuuint64_t)nsplit};
     cuuint64_t strides[2] = {rows * 4, rows * 4 * (cuuint64_t)ncols};
-    cuuint32_t box[3] = {128, 32, 1};
+    cuuint32_t box[3] = {32, 16, 1};  // one epilogue warp's 32 rows x 16 columns
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
