@@ -276,14 +276,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def gemm_traffic():
+def gemm_traffic(per_step: int):
     """dram bytes per launch of the contraction kernel from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+    or None when the kernel source or the launches per step changed since the capture."""
     try:
         txt = open(GEMM_PROFILE).read()
         m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
         h = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", txt)
-        if not m or not h:
+        n = re.search(r"launches_per_step:\s*([0-9]+)", txt)
+        if not m or not h or not n or int(n.group(1)) != per_step:
             return None
         cur = hashlib.sha1(open(GEMM_SOURCE, "rb").read()).hexdigest()
         return float(m.group(1)) if cur == h.group(1) else None
@@ -398,7 +399,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    plan.timer_start(K)
+    plan.timer_start(8 * K)  # every contraction launch of every step (up to 4 phases each)
     for k in range(K):
         flush.fill_(k & 0xFF)
         ev[k][0].record()
@@ -420,16 +421,20 @@ def main():
 
     # the dominant kernel against its roofline
     bf16_peak, hbm_peak, peak_src = peaks()
-    gemm_avg_s = gemm_ms / max(gemm_n, 1) / 1000.0
+    # the contraction runs as `per_step` launches (K phases, each a whole number of
+    # waves); flops per launch / mean launch time = flops per step / time per step
+    per_step = max(gemm_n // K, 1)
+    gemm_step_s = gemm_ms / K / 1000.0
     alg_flops = 16.0 * NBINS * N * NLAGS          # 16 real flop per (bin, sample, lag)
     issued_flops = 2.0 * (2 * NBINS) * (8 * N) * NLAGS  # the bf16 hi+lo contraction as issued
-    achieved = alg_flops / gemm_avg_s / 1e12
+    achieved = alg_flops / gemm_step_s / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": achieved / bf16_peak, "traffic": gemm_traffic(), "kernel": "k_ternary_gemm",
+                "frac": achieved / bf16_peak, "traffic": gemm_traffic(per_step), "kernel": "k_ternary_gemm",
                 "peak_source": f"{peak_src} bf16 dense (burst)",
-                "issued_tflops": issued_flops / gemm_avg_s / 1e12,
-                "issued_frac": issued_flops / gemm_avg_s / 1e12 / bf16_peak,
-                "kernel_ms": gemm_avg_s * 1000.0}
+                "issued_tflops": issued_flops / gemm_step_s / 1e12,
+                "issued_frac": issued_flops / gemm_step_s / 1e12 / bf16_peak,
+                "kernel_ms_per_step": gemm_step_s * 1000.0, "launches_per_step": per_step,
+                "kernel_ms_per_launch": gemm_ms / max(gemm_n, 1)}
 
     if args.profile:
         if rank == 0:
