@@ -207,10 +207,12 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
             uint4 ws[4], vs[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
+                // bins ty*4 + i: two distinct per warp (broadcast); columns tx + 16 i:
+                // consecutive across the warp's 16 distinct tx, conflict-free
                 wm[i] = tM[kk * Smem::kMagStride + ty * 4 + i];
                 ws[i] = tS[kk * Smem::kSgnStride + ty * 4 + i];
-                vm[i] = vM[kk * Smem::kMagStride + tx * 4 + i];
-                vs[i] = vS[kk * Smem::kSgnStride + tx * 4 + i];
+                vm[i] = vM[kk * Smem::kMagStride + tx + 16 * i];
+                vs[i] = vS[kk * Smem::kSgnStride + tx + 16 * i];
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -222,7 +224,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int col = col0 + tx * 4 + j;
+        const int col = col0 + tx + 16 * j;
         if (col >= ncols) continue;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
