@@ -71,6 +71,10 @@ struct Plan {
     void *tmap_dev = nullptr;
     size_t b_bytes = 0;          // packed-B region of the workspace
     size_t part_bytes = 0;       // split-K partials region of the workspace
+    // batched ternary plans: the output viewed as one [rows][2 nbins] fp32 tensor
+    // for the bulk-copy fold-out (0 rows: CPIs differ in nbins or are not row-aligned)
+    int32_t bt_nbins = 0;
+    int64_t bt_rows = 0;
 };
 
 // ---- the operator on device ------------------------------------------------------

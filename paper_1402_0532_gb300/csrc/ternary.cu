@@ -63,7 +63,7 @@ struct Problem {
     int64_t split_stride;  // floats between split partials
     const float2 *ang;     // two-level table: [nth] (r_hi) then [256] (r_lo)
     int32_t nth;
-    int32_t pad;
+    int32_t crow0;         // batched: first column of this problem in the output tensor map
 };
 
 struct Unit {
@@ -333,7 +333,7 @@ struct Tile {
 // loads half of the shared 256-column B tile and multicasts it to both, and
 // each stage is refilled only after both CTAs' MMAs released it.  `tmap` then
 // has a 128-row box.
-template <int MH, int CL>
+template <int MH, int CL, bool BT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
@@ -532,11 +532,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                     constexpr int GPH = TN / 16;       // 16-column groups per row half
                     constexpr int NG = MH * GPH;       // groups per chain (even)
                     auto tcol = [&](int g) { return (uint32_t)((buf + g / GPH) * TN + (g % GPH) * 16); };
+                    // bulk copy c of the chain uses buffer c & 1 (without partial groups
+                    // every group is one copy, so c = g)
+                    int ncopy = 0;
                     auto drain = [&](const uint32_t (&r)[16], int g) {
-                        const uint32_t sb = wst + (uint32_t)(g & 1) * 2048u;
+                        const int cidx = BT ? ncopy : g;
+                        const uint32_t sb = wst + (uint32_t)(cidx & 1) * 2048u;
+                        const int colg = w.nt * TN + (g % GPH) * 16;  // the group's first column
+                        if (BT && w.P.ncols - colg < 16) {
+                            if (lane == 0 && g == 0) bulk_wait_all();
+                            // batched: the map spans all problems, so a group that runs past
+                            // this problem's last column is written element by element
+                            const int valid = w.P.ncols - colg;
+                            const int64_t m = mrow0 + 128 * (g / GPH) + lane;
+                            if (valid > 0 && m < limit_m) {
+                                float *dst = out_base + w.out_off + (int64_t)colg * w.P.ld + m;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    if (j >= valid) break;
+                                    if (first) dst[j * w.P.ld] = __uint_as_float(r[j]);
+                                    else red_add_f32(dst + j * w.P.ld, __uint_as_float(r[j]));
+                                }
+                            }
+                            return;
+                        }
                         if (lane == 0) {
-                            if (g == 0) bulk_wait_all();
-                            else bulk_wait_read1();
+                            if (g == 0) bulk_wait_all();  // the previous chain's copies are complete
+                            else if (cidx > 0) bulk_wait_read1();  // copy cidx - 2 has read this buffer
                         }
                         __syncwarp();
 #pragma unroll
@@ -547,11 +569,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                         if (lane == 0) {
                             const int mrow = mrow0 + 128 * (g / GPH);
-                            const int col = w.nt * TN + (g % GPH) * 16;
+                            const int col = (BT ? w.P.crow0 : 0) + colg;
                             if (first) tma_store_out(&omap, sb, mrow, col, w.split);
                             else tma_reduce_out(&omap, sb, mrow, col, w.split);
                             bulk_commit();
                         }
+                        if (BT) ++ncopy;
                     };
                     uint32_t ra[16], rb[16];
                     tmem_ld16(trow + tcol(0), ra);
@@ -815,11 +838,11 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH, int CL>
+template <int MH, int CL, bool BT = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
-    auto kern = k_ternary_gemm<MH, CL>;
+    auto kern = k_ternary_gemm<MH, CL, BT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(CL == 2 ? p.tmap_host2 : p.tmap_host);
@@ -1035,6 +1058,22 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
     }
     prefix[ncpi] = rows_total;
     if (rows_total >= (1LL << 31)) return cudaErrorNotSupported;  // TMA row coordinate is 32-bit
+    // one output tensor map for all CPIs when they share an even nbins and every
+    // surface starts on a row of 2 nbins floats
+    {
+        bool uniform = cpis[0].nbins % 2 == 0;
+        int64_t rows = 0;
+        for (int c = 0; c < ncpi && uniform; ++c) {
+            const ndft_cpi &q = cpis[c];
+            uniform = q.nbins == cpis[0].nbins && q.off_out % q.nbins == 0;
+            rows = std::max<int64_t>(rows, q.off_out / q.nbins + q.nlags);
+        }
+        if (uniform && rows < (1LL << 31)) {
+            p.bt_nbins = cpis[0].nbins;
+            p.bt_rows = rows;
+            for (int c = 0; c < ncpi; ++c) probs[c].crow0 = (int32_t)(cpis[c].off_out / cpis[c].nbins);
+        }
+    }
     std::vector<int> order(ncpi);
     for (int c = 0; c < ncpi; ++c) order[c] = c;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cpis[a].n > cpis[b].n; });
@@ -1085,8 +1124,11 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
                                 p.sm_count, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
-    if ((e = launch_gemm<2, 1>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out), nullptr, s)) !=
-        cudaSuccess)
+    alignas(64) CUtensorMap omap;
+    const bool tma_out = p.bt_rows > 0 && p.tune_drain == 0 && ((uintptr_t)out & 15u) == 0 &&
+                         make_out_map(out, p.bt_nbins, (int)p.bt_rows, 1, &omap) == cudaSuccess;
+    if ((e = launch_gemm<2, 1, true>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out),
+                               tma_out ? &omap : nullptr, s)) != cudaSuccess)
         return e;
     *launches += 1;
     return cudaSuccess;

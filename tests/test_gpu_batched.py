@@ -64,6 +64,30 @@ def test_batched_ternary_small(api):
         assert np.max(np.abs(g - want)) / np.max(np.abs(want)) < TOL
 
 
+def test_batched_ternary_uniform_bins(api):
+    """CPIs that share an even nbins use one output tensor map for the bulk-copy
+    fold-out; lag counts that are not multiples of 16 end in column groups that
+    are written element by element (so no CPI's copy runs into the next
+    surface).  Long CPIs make several accumulation chains per unit."""
+    rng = np.random.default_rng(37)
+    scs = [scenes.radar_scene(N=int(n), nlags=int(l), nbins=40, rng=rng)
+           for n, l in ((9000, 5), (1536, 17), (12000, 33), (2048, 300), (700, 1), (16384, 16))]
+    surv, ref, cpis, total = pack(scs)
+    bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    out = torch.zeros(total, dtype=torch.complex64, device="cuda")
+    guard = torch.full((total + 64,), complex(7.0, -7.0), dtype=torch.complex64, device="cuda")
+    bp(dev(surv), dev(ref), guard[:total])
+    bp(dev(surv), dev(ref), out)
+    bp.query_error()
+    got = out.cpu().numpy()
+    assert np.all(guard[total:].cpu().numpy() == complex(7.0, -7.0))  # nothing past the last surface
+    assert np.array_equal(guard[:total].cpu().numpy(), got)  # the stale contents do not leak in
+    for sc, c in zip(scs, cpis):
+        g = got[c["off_out"]: c["off_out"] + sc.nlags * sc.nbins].reshape(sc.nlags, sc.nbins)
+        want = oracle.caf(sc.s_surv, sc.s_ref, sc.lag0, sc.nlags, sc.p0, sc.nbins, z32=True)
+        assert np.max(np.abs(g - want)) / np.max(np.abs(want)) < TOL
+
+
 @pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2"), ("direct", "q14")])
 def test_batched_graph_replay_equals_eager(api, form, prec):
     q14 = prec == "q14"
