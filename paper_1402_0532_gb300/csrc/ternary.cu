@@ -736,6 +736,48 @@ __global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags,
     }
 }
 
+// Many problems: tiles of 8 K blocks x 32 columns (the k_pack_single block)
+// numbered problem by problem; tile_prefix[c] is problem c's first tile.  Each
+// block of a persistent grid packs one contiguous range of tiles: it finds the
+// problem of its first tile by a binary search over tile_prefix and then steps
+// through the problems in order.
+__global__ void __launch_bounds__(256) k_pack_tiles(const PackProb *__restrict__ probs,
+                                                    const int64_t *__restrict__ tile_prefix, int nprob,
+                                                    uint32_t flags, const float2 *__restrict__ a_base,
+                                                    const float2 *__restrict__ r_base, uint4 *__restrict__ B) {
+    const int64_t total = tile_prefix[nprob];
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = t0 + per < total ? t0 + per : total;
+    const int t = threadIdx.x & 7;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_prefix[mid] <= t0) lo = mid;
+        else hi = mid - 1;
+    }
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        while (tile >= tile_prefix[lo + 1]) ++lo;
+        const PackProb &P = probs[lo];
+        const int ct = (P.ncols + 31) / 32;
+        const int local = (int)(tile - tile_prefix[lo]);
+        const int kbt = local / ct;
+        const int col = (local - kbt * ct) * 32 + (threadIdx.x >> 3);
+        if (col >= P.ncols) continue;
+        const float2 *a = a_base + P.a_off;
+        const float2 *r = r_base + P.r_off;
+        const int kb0 = kbt * kPackKb;
+        const int kb1 = min(kb0 + kPackKb, P.kblocks);
+#pragma unroll 2
+        for (int kb = kb0; kb < kb1; ++kb) {
+            const int64_t i = (int64_t)kb * 8 + t;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < P.N) v = lag_product(P, a, r, col, i, flags);
+            B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
+        }
+    }
+}
+
 // Two-level angle table: entry j < nth is (cos, sin)((pi/2) 256 j / N), entry
 // nth + j (j < 256) is (cos, sin)((pi/2) j / N); fp64, rounded to fp32.
 __global__ void k_angles(int N, int nth, float2 *__restrict__ ang) {
@@ -899,10 +941,11 @@ TernLayout layout_for(const ndft_desc &d, int sm) {
 }
 
 // Device-side description of a batched plan (one allocation, laid out by
-// ternary_batched_init): Problem[ncpi], PackProb[ncpi], int64 prefix[ncpi + 1],
+// ternary_batched_init): Problem[ncpi], PackProb[ncpi], int64 prefix[ncpi + 1]
+// (first packed row), int64 tile prefix[ncpi + 1] (first pack tile),
 // Unit[nunits].
 struct BatchedLayout {
-    size_t probs, packs, prefix, units, total;
+    size_t probs, packs, prefix, tprefix, units, total;
 };
 
 BatchedLayout batched_layout(int ncpi, int64_t nunits) {
@@ -911,7 +954,8 @@ BatchedLayout batched_layout(int ncpi, int64_t nunits) {
     b.probs = 0;
     b.packs = al(b.probs + (size_t)ncpi * sizeof(Problem));
     b.prefix = al(b.packs + (size_t)ncpi * sizeof(PackProb));
-    b.units = al(b.prefix + (size_t)(ncpi + 1) * sizeof(int64_t));
+    b.tprefix = al(b.prefix + (size_t)(ncpi + 1) * sizeof(int64_t));
+    b.units = al(b.tprefix + (size_t)(ncpi + 1) * sizeof(int64_t));
     b.total = al(b.units + (size_t)nunits * sizeof(Unit));
     return b;
 }
@@ -1024,7 +1068,7 @@ cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, i
 cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaStream_t s) {
     std::vector<Problem> probs(ncpi);
     std::vector<PackProb> packs(ncpi);
-    std::vector<int64_t> prefix(ncpi + 1, 0);
+    std::vector<int64_t> prefix(ncpi + 1, 0), tprefix(ncpi + 1, 0);
     int64_t ang_total = 0, rows_total = 0;
     for (int c = 0; c < ncpi; ++c) {
         const ndft_cpi &q = cpis[c];
@@ -1053,6 +1097,7 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
         K.row0 = rows_total;
         prefix[c] = rows_total;
         rows_total += (int64_t)P.kblocks * q.nlags;
+        tprefix[c + 1] = tprefix[c] + (int64_t)((P.kblocks + kPackKb - 1) / kPackKb) * ((q.nlags + 31) / 32);
         probs[c].ang = reinterpret_cast<const float2 *>(ang_total);  // offset, rebased below
         ang_total += P.nth + R_LO;
     }
@@ -1099,6 +1144,7 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
     std::memcpy(host.data() + BL.probs, probs.data(), probs.size() * sizeof(Problem));
     std::memcpy(host.data() + BL.packs, packs.data(), packs.size() * sizeof(PackProb));
     std::memcpy(host.data() + BL.prefix, prefix.data(), prefix.size() * sizeof(int64_t));
+    std::memcpy(host.data() + BL.tprefix, tprefix.data(), tprefix.size() * sizeof(int64_t));
     std::memcpy(host.data() + BL.units, units.data(), units.size() * sizeof(Unit));
     if ((e = cudaMemcpyAsync(wd, host.data(), BL.total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // `host` must outlive the copy
@@ -1117,11 +1163,11 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
     unsigned char *wd = reinterpret_cast<unsigned char *>(p.work_dev);
     const Problem *probs = reinterpret_cast<const Problem *>(wd + BL.probs);
     const PackProb *packs = reinterpret_cast<const PackProb *>(wd + BL.packs);
-    const int64_t *prefix = reinterpret_cast<const int64_t *>(wd + BL.prefix);
+    const int64_t *tprefix = reinterpret_cast<const int64_t *>(wd + BL.tprefix);
     const Unit *units = reinterpret_cast<const Unit *>(wd + BL.units);
-    const int64_t rows = (int64_t)(p.b_bytes / 128);
-    cudaError_t e = launch_pack(packs, prefix, p.ncpi, PackProb{}, rows, p.d.flags, true, surv, ref, p.ws,
-                                p.sm_count, s);
+    k_pack_tiles<<<p.sm_count * 8, 256, 0, s>>>(packs, tprefix, p.ncpi, p.d.flags, static_cast<const float2 *>(surv),
+                                                static_cast<const float2 *>(ref), static_cast<uint4 *>(p.ws));
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *launches += 1;
     alignas(64) CUtensorMap omap;
