@@ -1,0 +1,88 @@
+"""Parity at the full sizes of the benchmark's workloads, in the launch
+configurations the benchmark times:
+
+* the NFFT of 65536 vectors of N = 1024 (every vector, bit for bit against
+  the oracle's fp32 recursion) and the NDFT of the same batch in both forms
+  (sampled vectors against the fp64 oracle, within 1e-5 of each vector's
+  max |X|, and their peaks wherever the oracle's top two are separated);
+* the CAF surface of 65536 samples, 1024 lags x 1024 bins in both forms on
+  sampled cells against the fp64 oracle (lag product in fp32, the stage both
+  forms share), within 1e-5 of max |A|.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0532_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_0532_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return scenes.cn_batch()
+
+
+def test_nfft_full_batch_bit_exact(api, batch):
+    p = api.Plan(1024, max_batch=batch.shape[0])
+    got = p.nfft(torch.from_numpy(batch).cuda()).cpu().numpy()
+    p.query_error()
+    want = oracle.nfft_f32(batch)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2")])
+def test_ndft_full_batch_sampled(api, batch, form, prec):
+    p = api.Plan(1024, max_batch=batch.shape[0], form=form, prec=prec)
+    X = p.ndft(torch.from_numpy(batch).cuda())
+    idx, _ = api.argmax(X)
+    got = X.cpu().numpy()
+    idx = idx.cpu().numpy()
+    p.query_error()
+    rng = np.random.default_rng(50)
+    rows = np.unique(np.concatenate([np.arange(16), rng.integers(0, batch.shape[0], 112), [batch.shape[0] - 1]]))
+    ref = oracle.ndft(batch[rows].astype(np.complex128))
+    amax = np.max(np.abs(ref), axis=1)
+    err = np.max(np.abs(got[rows] - ref), axis=1) / amax
+    assert err.max() < TOL
+    # peaks: equal wherever the oracle's top two magnitudes are separated by more than the bar
+    mag = np.sort(np.abs(ref), axis=1)
+    clear = (mag[:, -1] - mag[:, -2]) > 2 * TOL * amax
+    assert clear.sum() > len(rows) // 2
+    assert np.array_equal(idx[rows][clear], np.argmax(np.abs(ref), axis=1)[clear])
+
+
+@pytest.fixture(scope="module")
+def surface():
+    return scenes.radar_scene(N=65536)
+
+
+@pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2")])
+def test_caf_full_surface_sampled(api, surface, form, prec):
+    sc = surface
+    p = api.Plan(sc.N, p0=-512, nbins=1024, max_lags=1024, form=form, prec=prec)
+    A = p.caf(torch.from_numpy(sc.s_surv).cuda(), torch.from_numpy(sc.s_ref).cuda(), 0, 1024)
+    idx, _ = api.argmax(A.reshape(1, -1))
+    got = A.cpu().numpy()
+    p.query_error()
+    rng = np.random.default_rng(51)
+    lags = np.concatenate([[0, 0, 37, 120, 301, 1023, 500], rng.integers(0, 1024, 57)])
+    bins = np.concatenate([[0, 1, 5, -12, 40, -512, 511], rng.integers(-512, 512, 57)])
+    ref = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
+    amax = np.max(np.abs(got))
+    assert np.max(np.abs(got[lags, bins + 512] - ref)) / amax < TOL
+    # the surface's peak is the direct path (lag 0, bin 0)
+    assert int(idx[0]) == 0 * 1024 + 512
