@@ -209,6 +209,17 @@ def set_workload(name: str):
                     "(profiling case)")
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's `value` (the slowest rank's time); `value`
+    itself on a single process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -411,11 +422,7 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     gemm_ms, gemm_n = plan.timer_read()
-    t_total = sum(step_ms)
-    if dist:
-        t = torch.tensor([t_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(sum(step_ms), dist, dev)
     plan.query_error()
     value = world * cells * K / (t_total / 1000.0)
 
@@ -476,7 +483,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         plan.caf_from_host(hss, hsr, 0, NLAGS, hA, staging)
-    e2e_dt = time.perf_counter() - t0
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e = {"value": world * cells * args.e2e_steps / e2e_dt, "unit": "cells/s",
            "h2d_bytes_per_step": hss.numel() * 8 + hsr.numel() * 8, "d2h_bytes_per_step": hA.numel() * 8}
 
