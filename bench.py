@@ -137,26 +137,49 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs):
         X = torch.empty_like(xt)
         ms = _time_ms(lambda: p.ndft(xt, out=X), 20, flush)
         out[f"ndft_64_x4096_{form}"] = {"ms": ms, "vectors_per_s": 4096 / (ms / 1e3)}
-    # 256 CPIs, tensor-core form
+    # 256 CPIs: the tensor-core form as one captured CUDA graph (pack + one
+    # persistent contraction), the plain form in fp32 and Q1.14 (eager, one run)
     scs = scenes.cpi_batch()
-    surv, ref, cpis, oo, so = [], [], [], 0, 0
+    surv, ref, qsurv, qref, cpis, oo, so = [], [], [], [], [], 0, 0
     for sc in scs:
         pad = (-sc.N) % 4
         cpis.append(dict(off_surv=so, off_ref=so, off_out=oo, n=sc.N, lag0=0, nlags=sc.nlags, p0=sc.p0,
                          nbins=sc.nbins))
         surv += [sc.s_surv, np.zeros(pad, np.complex64)]
         ref += [sc.s_ref, np.zeros(pad, np.complex64)]
+        qsurv += [scenes.quantize_q14(sc.s_surv, 0.25), np.zeros((pad, 2), np.int16)]
+        qref += [scenes.quantize_q14(sc.s_ref, 0.25), np.zeros((pad, 2), np.int16)]
         so += sc.N + pad
         oo += sc.nlags * sc.nbins
+    units = sum(c["nlags"] * c["nbins"] * c["n"] for c in cpis)
     ds = torch.from_numpy(np.concatenate(surv)).to(dev)
     dr = torch.from_numpy(np.concatenate(ref)).to(dev)
     bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
     A = torch.empty(oo, dtype=torch.complex64, device=dev)
-    ms = _time_ms(lambda: bp(ds, dr, A), 3)
-    units = sum(c["nlags"] * c["nbins"] * c["n"] for c in cpis)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        bp(ds, dr, A)  # kernel attributes set outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bp(ds, dr, A)
+    ms = _time_ms(graph.replay, 3)
     out["caf_256_cpis_ternary"] = {"ms": ms, "cells_per_s": oo / (ms / 1e3), "otimes_per_s": units / (ms / 1e3),
-                                   "cells": oo}
+                                   "cells": oo, "launch": "CUDA graph replay", "launches": bp.last_launches()}
+    del graph
     bp.close()
+    for prec in ("fp32", "q14"):
+        q = prec == "q14"
+        bq = api.BatchedPlan(cpis, form="direct", prec=prec)
+        xs = torch.from_numpy(np.concatenate(qsurv if q else surv)).to(dev)
+        xr = torch.from_numpy(np.concatenate(qref if q else ref)).to(dev)
+        Aq = torch.empty((oo, 2) if q else (oo,), dtype=torch.int32 if q else torch.complex64, device=dev)
+        ms = _time_ms(lambda: bq(xs, xr, Aq), 1)
+        out[f"caf_256_cpis_direct_{prec}"] = {"ms": ms, "cells_per_s": oo / (ms / 1e3),
+                                              "otimes_per_s": units / (ms / 1e3)}
+        bq.close()
+        del xs, xr, Aq
     del ds, dr, A
     torch.cuda.empty_cache()
     # Eq. 12a through the NFFT (Sec. 3), the surface of the headline workload:
