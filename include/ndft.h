@@ -223,7 +223,11 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * (8 samples each) per tensor-memory accumulation chain before it is folded
  * into the fp32 result (0 = 64); key 3 = ternary-GEMM fold path (0: bulk
  * tensor stores/adds, 1: per-element adds).  Used by the autotuner; affects
- * speed and fp32 rounding only. */
+ * speed and fp32 rounding only.  Key 4 (test only) = 1: the ternary GEMM's
+ * operand loader issues no loads, so every bounded wait of the kernel runs out
+ * (about 2 s): the kernel abandons its work, releases its tensor memory and
+ * returns, the output is left unspecified and ndft_query_error reports
+ * NDFT_E_TIMEOUT; the plan stays usable once the key is set back to 0. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
 
 /* Device timing of the plan's main contraction kernel (the tensor-core GEMM,

@@ -60,6 +60,7 @@ struct Plan {
     int tune_cols = 0;
     int tune_chunk = 0;          // ternary form: K blocks per TMEM accumulation chain
     int tune_drain = 0;          // ternary form: 0 bulk tensor stores/adds, 1 per-element adds
+    int test_starve = 0;         // ternary form, tests only: issue no operand loads (waits run out)
     int last_launches = 0;
     // optional timing of the main contraction kernel (event pairs, see ndft_timer_start)
     mutable cudaEvent_t *tev = nullptr;

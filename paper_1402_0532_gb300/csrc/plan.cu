@@ -153,6 +153,7 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
 fail:
     free_plan(p);
     delete h;
+    cudaGetLastError();  // a failed allocation is also the runtime's last error: do not leak it into later calls
     return from_cuda(e);
 }
 
@@ -335,6 +336,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
     } else if (key == 3) {
         if (value > 1) return NDFT_E_INVALID;
         plan->p.tune_drain = value;
+    } else if (key == 4) {
+        if (value > 1) return NDFT_E_INVALID;
+        plan->p.test_starve = value;
     } else {
         return NDFT_E_INVALID;
     }
@@ -452,6 +456,7 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
 fail:
     free_plan(p);
     delete h;
+    cudaGetLastError();  // a failed allocation is also the runtime's last error: do not leak it into later calls
     return from_cuda(e);
 }
 

@@ -337,7 +337,7 @@ template <int MH, int CL, bool BT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
-                   int chunk, float *__restrict__ out_base, int32_t *err) {
+                   int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
     static_assert(CL == 1 || (CL == 2 && MH == 1), "the cluster variant uses 128-row tiles");
     using T = Tile<MH>;
     const int rank = CL == 2 ? (int)cluster_rank() : 0;
@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const Work w = decode(u, single, probs, units, rank, CL);
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                    if (starve) continue;  // tests: the stage never fills, every wait runs out
                     mbar_arrive_tx(&full[stage], B_BYTES);
                     const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN;
                     if (CL == 2)
@@ -896,7 +897,8 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
     timer_begin(p, s);
     if (CL == 1) {
         const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
-        kern<<<grid, kThreads, smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, out_base, p.err);
+        kern<<<grid, kThreads, smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
+                                          out_base, p.err);
         e = cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -911,7 +913,8 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, *map, om, out_tma, single, probs, units, nunits, chunk, out_base, p.err);
+        e = cudaLaunchKernelEx(&cfg, kern, *map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
+                               out_base, p.err);
     }
     timer_end(p, s);
     return e;

@@ -141,3 +141,42 @@ def test_ternary_tile_variants(api, tile, chunk):
     got = q.ndft(dev(x)).cpu().numpy()
     want = oracle.ndft(x.astype(np.complex128), p0=-7, nbins=77)
     assert relerr(got, want) < TOL
+
+
+def test_ternary_bounded_waits_time_out(api):
+    """Failure detection without a fault: with the test-only key that starves
+    the contraction of its operand loads, every bounded wait of the kernel runs
+    out (about 2 s), the kernel returns, and the plan's error word reports
+    NDFT_E_TIMEOUT; the context and the plan stay usable and the next normal
+    call reproduces the surface bit for bit."""
+    import time
+    from paper_1402_0532_gb300 import _lib as L
+    sc = scenes.radar_scene(N=4096, nlags=64, nbins=64, seed=49)
+    p = api.Plan(sc.N, p0=-32, nbins=64, max_lags=64, form="ternary", prec="bf16x2")
+    ss, sr = dev(sc.s_surv), dev(sc.s_ref)
+    A = p.caf(ss, sr, 0, 64).cpu().numpy()
+    p.query_error()
+    p.set_tuning(4, 1)
+    t0 = time.time()
+    p.caf(ss, sr, 0, 64)
+    with pytest.raises(L.NdftError) as e:
+        p.query_error()
+    assert e.value.status == L.E_TIMEOUT
+    assert time.time() - t0 < 60
+    p.query_error()  # the error word was cleared by the read
+    p.set_tuning(4, 0)
+    B = p.caf(ss, sr, 0, 64).cpu().numpy()
+    p.query_error()
+    assert np.array_equal(A.view(np.uint32), B.view(np.uint32))
+
+
+def test_plan_allocation_failure_is_reported(api):
+    """A plan whose workspace cannot be allocated (a 4.4 TB packed operand)
+    fails with NDFT_E_NOMEM and leaves the device usable."""
+    from paper_1402_0532_gb300 import _lib as L
+    with pytest.raises(L.NdftError) as e:
+        api.Plan(1 << 18, max_lags=1 << 20, form="ternary", prec="bf16x2")
+    assert e.value.status == L.E_NOMEM
+    x = scenes.cn(np.random.default_rng(52), (4, 64)).astype(np.complex64)
+    q = api.Plan(64, max_batch=4, form="ternary", prec="bf16x2")
+    assert relerr(q.ndft(dev(x)).cpu().numpy(), oracle.ndft(x.astype(np.complex128))) < TOL
