@@ -2,6 +2,8 @@
 // dispatch to the kernels.  Exec calls allocate nothing and never synchronise.
 #include "internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -15,6 +17,14 @@ struct ndft_plan_s {
 };
 
 namespace {
+
+// NVTX range around a C-ABI call (free unless a profiler is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 bool aligned16(const void *ptr) { return ptr && ((uintptr_t)ptr & 15u) == 0; }
 
@@ -104,6 +114,7 @@ int32_t ndft_version(void) { return 100; }
 const char *ndft_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
 
 ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream) {
+    const Range range("ndft_plan");
     if (!out || !d) return NDFT_E_INVALID;
     *out = nullptr;
     if (d->n < 1 || d->n > kMaxN || d->nbins < 0 || d->nbins > d->n || d->max_lags < 0 || d->max_batch < 0)
@@ -166,6 +177,7 @@ ndft_status ndft_plan_destroy(ndft_plan_t plan) {
 }
 
 ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream) {
+    const Range range("ndft_exec");
     if (!plan || plan->p.batched || batch < 0 || batch > plan->p.d.max_batch) return NDFT_E_INVALID;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
@@ -186,6 +198,7 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
 }
 
 ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream) {
+    const Range range("nfft_exec");
     if (!plan || plan->p.batched || batch < 0 || batch > plan->p.d.max_batch) return NDFT_E_INVALID;
     Plan &p = plan->p;
     if (p.d.prec != NDFT_PREC_FP32 || !pow2(p.d.n) || p.d.n > (1 << 20) || p.d.nbins != p.d.n ||
@@ -200,6 +213,7 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
 
 ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags, void *A,
                      cudaStream_t stream) {
+    const Range range("caf_exec");
     if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(A)) return NDFT_E_INVALID;
     Plan &p = plan->p;
@@ -218,6 +232,7 @@ ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, in
 
 ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags,
                          const void *dA, void *ds, cudaStream_t stream) {
+    const Range range("caf_backward");
     (void)s_surv;
     if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     Plan &p = plan->p;
@@ -349,6 +364,7 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
 
 ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t ncpi, int32_t form, int32_t prec,
                               uint32_t flags, cudaStream_t stream) {
+    const Range range("ndft_plan_batched");
     if (!out || !cpis || ncpi < 1 || ncpi > (1 << 20) || (flags & ~kKnownFlags)) return NDFT_E_INVALID;
     *out = nullptr;
     if (!valid_pair(form, prec) || fft_form(form)) return NDFT_E_UNSUPPORTED;
@@ -462,6 +478,7 @@ fail:
 
 ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void *ref_base, void *out_base,
                              cudaStream_t stream) {
+    const Range range("caf_exec_batched");
     if (!plan || !plan->p.batched) return NDFT_E_INVALID;
     if (!aligned16(surv_base) || !aligned16(ref_base) || !aligned16(out_base)) return NDFT_E_INVALID;
     Plan &p = plan->p;
