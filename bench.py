@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="time the tensor-core steps only (no direct form, e2e, error or CPU legs)")
     ap.add_argument("--no-others", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tile/split settings (no autotuner)")
     ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
@@ -111,13 +112,15 @@ def _time_ms(fn, reps: int, flush=None) -> float:
     return tot / reps
 
 
-def other_workloads(api, scenes, dev, hbm_peak_gbs):
+def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
     """The secondary workloads, timed outside the headline region: the NFFT of 65536
     vectors of 1024 points, the N=64 tone batch (both forms), the 256-CPI batch
     (tensor-core form, one persistent launch sequence) and the N=16384
     forward + backward through the autograd function."""
     import numpy as np
     import torch
+
+    from paper_1402_0532_gb300 import autotune
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = {}
     # NFFT, Sec. 3
@@ -156,6 +159,7 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs):
     dr = torch.from_numpy(np.concatenate(ref)).to(dev)
     bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
     A = torch.empty(oo, dtype=torch.complex64, device=dev)
+    tuned_b = autotune.tune_batched(bp, ds, dr, A) if tune else {}
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -166,7 +170,8 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs):
         bp(ds, dr, A)
     ms = _time_ms(graph.replay, 3)
     out["caf_256_cpis_ternary"] = {"ms": ms, "cells_per_s": oo / (ms / 1e3), "otimes_per_s": units / (ms / 1e3),
-                                   "cells": oo, "launch": "CUDA graph replay", "launches": bp.last_launches()}
+                                   "cells": oo, "launch": "CUDA graph replay", "launches": bp.last_launches(),
+                                   "tuning": tuned_b}
     del graph
     bp.close()
     for prec in ("fp32", "q14"):
@@ -392,7 +397,7 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_1402_0532_gb300 import api, scenes
+    from paper_1402_0532_gb300 import api, autotune, scenes
 
     dist = None
     if world > 1:
@@ -414,6 +419,7 @@ def main():
     A = torch.empty(NLAGS, NBINS, dtype=torch.complex64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     cells = NLAGS * NBINS
+    tuned = {} if args.no_tune else autotune.tune_caf(plan, ss, sr, 0, NLAGS, out=A)
 
     def step():
         plan.caf(ss, sr, 0, NLAGS, out=A)
@@ -472,7 +478,8 @@ def main():
                               "warmup": max(3, args.warmup), "ms_per_step": t_total / K, "higher_is_better": True,
                               "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
                               "config": {"workload": WORKLOAD, "N": N, "nlags": NLAGS, "nbins": NBINS,
-                                         "mode": "profile (tensor-core steps only)"},
+                                         "mode": "profile (tensor-core steps only)",
+                                         "tuning": {str(k): v for k, v in tuned.items()}},
                               "roofline": roofline, "gpu_launches": launches_per_step * K}), flush=True)
         if dist:
             dist.destroy_process_group()
@@ -481,6 +488,7 @@ def main():
     # the plain direct form, same surface
     pd = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="direct", prec="fp32", device=dev)
     Ad = torch.empty_like(A)
+    tuned_direct = {} if args.no_tune else autotune.tune_caf(pd, ss, sr, 0, NLAGS, out=Ad)
     pd.caf(ss, sr, 0, NLAGS, out=Ad)
     torch.cuda.synchronize()
     dms = []
@@ -495,7 +503,7 @@ def main():
     direct = {"value": cells / (statistics.mean(dms) / 1000.0), "unit": "cells/s",
               "ms_per_step": statistics.mean(dms)}
 
-    others = other_workloads(api, scenes, dev, hbm_peak) if not args.no_others else None
+    others = other_workloads(api, scenes, dev, hbm_peak, tune=not args.no_tune) if not args.no_others else None
 
     # end to end through the public API: pinned host inputs in, surface out
     hss = torch.from_numpy(scene.s_surv).pin_memory()
@@ -537,7 +545,9 @@ def main():
                 "config": {"workload": WORKLOAD, "N": N, "nlags": NLAGS, "nbins": NBINS, "p0": P0,
                            "form": "ternary GEMM (tcgen05, bf16 hi+lo operands, exact ternary signs, fp32 accum)",
                            "l2": "flushed between steps (256 MiB write, outside the timed events)",
-                           "parallelism": f"{world} independent surface(s), one per GPU"},
+                           "parallelism": f"{world} independent surface(s), one per GPU",
+                           "tuning": {"ternary": {str(k): v for k, v in tuned.items()},
+                                      "direct": {str(k): v for k, v in tuned_direct.items()}}},
                 "roofline": roofline, "direct": direct, "speedup_vs_direct": value / world / direct["value"],
                 "max_err_vs_fp64": err, "e2e": e2e, "gpu_launches": launches_per_step * K,
                 "clocks": clocks, "cpu_baseline": base, "other_workloads": others}

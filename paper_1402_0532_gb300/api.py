@@ -199,7 +199,11 @@ class BatchedPlan:
         for i, c in enumerate(cpis):
             arr[i] = L.NdftCpi(off_surv=c["off_surv"], off_ref=c["off_ref"], off_out=c["off_out"], n=c["n"],
                                lag0=c["lag0"], nlags=c["nlags"], p0=c["p0"], nbins=c["nbins"])
-        self.prec = prec
+        self.form, self.prec = form, prec
+        # a short digest of the CPI list, for the autotuner's cache key
+        import hashlib
+        shape = ";".join(f"{c['n']},{c['nlags']},{c['nbins']}" for c in cpis)
+        self._sig = f"{len(cpis)}cpis-" + hashlib.sha1(shape.encode()).hexdigest()[:12]
         h = ctypes.c_void_p()
         L.check(self.lib.ndft_plan_batched(ctypes.byref(h), arr, len(cpis), _FORMS[form], _PRECS[prec], int(flags),
                                            _stream(self.device)), "ndft_plan_batched")
@@ -222,6 +226,9 @@ class BatchedPlan:
 
     def set_tuning(self, key: int, value: int):
         L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
+
+    def signature(self) -> str:
+        return self._sig
 
     def query_error(self):
         L.check(self.lib.ndft_query_error(self.handle, _stream(self.device)), "ndft_query_error")

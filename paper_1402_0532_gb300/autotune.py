@@ -20,10 +20,13 @@ import threading
 
 _lock = threading.Lock()
 
-SPLIT, ROWS, CHUNK = 0, 1, 2
+SPLIT, ROWS, CHUNK, DRAIN = 0, 1, 2, 3
 
 TERNARY_SPACE = {ROWS: [256, 128], CHUNK: [64, 32], SPLIT: [0, 8, 16, 19, 24, 32]}
 DIRECT_SPACE = {SPLIT: [0, 2, 4, 6, 8, 12, 16]}
+# batched tensor-core plans: one persistent contraction over all CPIs, no split;
+# the knobs are the chain length and the fold-out path
+BATCHED_SPACE = {CHUNK: [64, 32], DRAIN: [0, 1]}
 
 
 def cache_path() -> str:
@@ -106,6 +109,14 @@ def _cuda_timer(run, reps: int) -> float:
     e.record()
     torch.cuda.synchronize()
     return s.elapsed_time(e) / 1000.0 / reps
+
+
+def tune_batched(bplan, surv, ref, out, **kw) -> dict:
+    """Tune a batched tensor-core plan on its own CPI list (one call = all CPIs)."""
+    import torch
+    key = f"batched|{bplan.form}|{bplan.prec}|{bplan.signature()}"
+    name = torch.cuda.get_device_name(surv.device)
+    return tune(bplan, lambda: bplan(surv, ref, out), key, BATCHED_SPACE, name, **kw)
 
 
 def tune_caf(plan, s_surv, s_ref, lag0: int, nlags: int, out=None, **kw) -> dict:
