@@ -280,12 +280,25 @@ cudaError_t prep_kernel(K kernel, size_t smem) {
 
 }  // namespace
 
+// Splits of the sample axis: the count in [1, 16] (and at most N / 256) whose
+// blocks fill the resident slots (2 blocks per SM) in the best-quantised
+// waves; the smallest such count when several are within 1 %.
 int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune) {
     if (tune > 0) return std::max(1, std::min(tune, std::max(1, N / KC)));
     const int64_t tiles = (int64_t)((nbins + BP - 1) / BP) * ((nlags + BC - 1) / BC);
-    int64_t s = (8LL * sm_count + tiles - 1) / tiles;
-    s = std::min<int64_t>(s, std::max(1, N / 256));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(s, 16));
+    const int64_t slots = 2LL * sm_count;
+    const int cap = std::max(1, std::min(16, N / 256));
+    int best_s = 1;
+    double best = -1.0;
+    for (int c = 1; c <= cap; ++c) {
+        const int64_t blocks = tiles * c;
+        const double eff = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
+        if (eff > best + 0.01) {
+            best = eff;
+            best_s = c;
+        }
+    }
+    return best_s;
 }
 
 size_t direct_ws_bytes(const ndft_desc &d, int sm_count) {
