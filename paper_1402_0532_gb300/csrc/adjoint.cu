@@ -35,6 +35,20 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[q][j] = make_float2(0.f, 0.f);
 
+    // Staging: thread element r is (bin k0 + kk, sample i0 + c) with kk = e >> 6,
+    // c = e & 63, e = tid + 256 r, the same sample for every k0; its twiddle
+    // index m = ((p0 + k) i) mod N advances by (KB i) mod N per bin chunk.
+    int64_t m[4], mstep[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = tid + 256 * r;
+        const int kk = e >> 6, c = e & 63;
+        const int64_t i = i0 + c;
+        int64_t pm = ((int64_t)p0 + kk) % N;
+        if (pm < 0) pm += N;
+        m[r] = (pm * i) % N;
+        mstep[r] = ((int64_t)KB * i) % N;
+    }
     for (int k0 = 0; k0 < nbins; k0 += KB) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -44,11 +58,11 @@ __global__ void __launch_bounds__(256)
             float2 sv = make_float2(0.f, 0.f);
             const int i = i0 + c, k = k0 + kk;
             if (i < N && k < nbins) {
-                int64_t pm = ((int64_t)p0 + k) % N;
-                if (pm < 0) pm += N;
-                const float2 w = __ldg(&tw[(pm * i) % N]);
+                const float2 w = __ldg(&tw[m[r]]);
                 sv = make_float2(sgnf(w.x), -sgnf(w.y));
             }
+            m[r] += mstep[r];
+            if (m[r] >= N) m[r] -= N;
             sS[kk][c] = sv;
             // upstream gradient for lag l0 + c at bin k0 + kk
             const int l = l0 + c;
@@ -59,7 +73,7 @@ __global__ void __launch_bounds__(256)
         for (int kk = 0; kk < KB; ++kk) {
             float2 s[4], d[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) s[j] = sS[kk][tx * 4 + j];
+            for (int j = 0; j < 4; ++j) s[j] = sS[kk][tx + 16 * j];  // samples tx + 16 j: no bank conflicts
 #pragma unroll
             for (int q = 0; q < 4; ++q) d[q] = sD[kk][ty * 4 + q];
 #pragma unroll
@@ -79,7 +93,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         fold[j] = make_float2(0.f, 0.f);
-        const int i = i0 + tx * 4 + j;
+        const int i = i0 + tx + 16 * j;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int l = l0 + ty * 4 + q;
@@ -97,7 +111,7 @@ __global__ void __launch_bounds__(256)
             fold[j].x += cr * acc[q][j].x + ci * acc[q][j].y;
             fold[j].y += cr * acc[q][j].y - ci * acc[q][j].x;
         }
-        red[ty][tx * 4 + j] = fold[j];
+        red[ty][tx + 16 * j] = fold[j];
     }
     __syncthreads();
     if (tid < TI) {
