@@ -187,5 +187,7 @@ cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, i
 cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaStream_t s);
 cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
                                    int *launches);
+cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nlags, const void *dA, void *ds,
+                                   cudaStream_t s, int *launches);
 
 }  // namespace ndft

@@ -239,6 +239,12 @@ ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref
     if (p.d.prec == NDFT_PREC_Q14 || fft_form(p.d.form)) return NDFT_E_UNSUPPORTED;
     if (!aligned16(s_ref) || !aligned16(dA) || !aligned16(ds)) return NDFT_E_INVALID;
     p.last_launches = 0;
+    if (p.d.form == NDFT_FORM_TERNARY_GEMM) {
+        // the transposed ternary contraction on the tensor cores (CUDA cores if it does not fit)
+        const cudaError_t e = launch_ternary_adjoint(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches);
+        if (e != cudaErrorNotSupported) return from_cuda(e);
+        p.last_launches = 0;
+    }
     return from_cuda(launch_caf_backward(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches));
 }
 

@@ -64,6 +64,10 @@ struct Problem {
     const float2 *ang;     // two-level table: [nth] (r_hi) then [256] (r_lo)
     int32_t nth;
     int32_t crow0;         // batched: first column of this problem in the output tensor map
+    // adjoint mode: s_ref and the lag window of the forward call
+    const float2 *sref;
+    int32_t lag0;
+    uint32_t flags;
 };
 
 struct Unit {
@@ -301,6 +305,23 @@ __device__ __forceinline__ void gen_pair(uint32_t u, uint32_t N, const float2 *_
     im = make_uint4(si, sr, wi, wr);
 }
 
+// ---- adjoint A generation: sample i, bins p and p + 1 -> rows 2 i and 2 i + 1 --
+// The adjoint contraction G_l[i] = sum_p conj(S[p][i]) dA[l][p] runs with rows =
+// (sample, Re/Im), columns = lags, K = bins x [dA_hi_r, dA_lo_r, dA_hi_i,
+// dA_lo_i].  Per bin the Re row holds [S_r, S_r, S_i, S_i] and the Im row
+// [-S_i, -S_i, S_r, S_r] (conj(S) dA = S_r a_r + S_i a_i + j (S_r a_i - S_i a_r)),
+// S = sigma(W^(p i)) read off u = 4 ((p i) mod N) by the integer quadrant rule
+// (exact zeros on the axes), as bf16 pairs.
+__device__ __forceinline__ void adj_signs(uint32_t u, uint32_t N, uint32_t &sr2, uint32_t &si2) {
+    const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
+    const bool axis = u == q * N;
+    constexpr uint32_t P1 = 0x3F803F80u, M1 = 0xBF80BF80u;
+    // cos: + in quadrants 0 and 3, - in 1 and 2, 0 at u = N, 3N
+    sr2 = (q == 0u) ? P1 : (q == 2u) ? M1 : axis ? 0u : (q == 1u ? M1 : P1);
+    // -sin: 0 at u = 0, 2N; - in quadrants 0 and 1, + in 2 and 3
+    si2 = (q == 1u) ? M1 : (q == 3u) ? P1 : axis ? 0u : (q == 0u ? M1 : P1);
+}
+
 // Rows 2 pl (Re) and 2 pl + 1 (Im), 16-byte chunk t of the 128-byte row, in the
 // 128-byte-swizzled K-major layout the MMA descriptors expect.
 __device__ __forceinline__ void store_pair(uint32_t a_stage, int pl, int t, const uint4 &re, const uint4 &im) {
@@ -333,12 +354,13 @@ struct Tile {
 // loads half of the shared 256-column B tile and multicasts it to both, and
 // each stage is refilled only after both CTAs' MMAs released it.  `tmap` then
 // has a 128-row box.
-template <int MH, int CL, bool BT>
+template <int MH, int CL, bool BT, bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
                    int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
     static_assert(CL == 1 || (CL == 2 && MH == 1), "the cluster variant uses 128-row tiles");
+    static_assert(!ADJ || (MH == 2 && CL == 1 && !BT), "the adjoint runs on the 256-row tile");
     using T = Tile<MH>;
     const int rank = CL == 2 ? (int)cluster_rank() : 0;
     constexpr int STG = T::kStages;
@@ -457,6 +479,47 @@ __global__ void __launch_bounds__(kThreads, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
+        if constexpr (ADJ) {
+            for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
+                const Work w = decode(u, single, probs, units, rank, CL);
+                const uint32_t N = (uint32_t)w.P.N;
+                uint32_t ua[PPT], ub[PPT], dd[PPT];
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const int64_t i = (int64_t)w.mt * (T::kRows / 2) + pg + 32 * j;  // sample
+                    int64_t pa = ((int64_t)w.P.p0 + (int64_t)w.kb0 * 16 + 2 * t) % (int64_t)N;
+                    if (pa < 0) pa += N;
+                    const int64_t pb = pa + 1 == N ? 0 : pa + 1;
+                    ua[j] = 4u * (uint32_t)((pa * (i % N)) % N);
+                    ub[j] = 4u * (uint32_t)((pb * (i % N)) % N);
+                    dd[j] = 4u * (uint32_t)((16 * (i % N)) % N);
+                }
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                    const uint32_t a_st = a_base + stage * T::kABytes;
+#pragma unroll
+                    for (int j = 0; j < PPT; ++j) {
+                        uint32_t sra, sia, srb, sib;
+                        adj_signs(ua[j], N, sra, sia);
+                        adj_signs(ub[j], N, srb, sib);
+                        const uint4 re = make_uint4(sra, sia, srb, sib);
+                        const uint4 im = make_uint4(sia ^ 0x80008000u, sra, sib ^ 0x80008000u, srb);
+                        store_pair(a_st, pg + 32 * j, t, re, im);
+                        ua[j] += dd[j];
+                        if (ua[j] >= 4u * N) ua[j] -= 4u * N;
+                        ub[j] += dd[j];
+                        if (ub[j] >= 4u * N) ub[j] -= 4u * N;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[stage]);
+                    if (++stage == STG) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        } else
         for (int64_t u = blockIdx.x / CL; u < nunits; u += gridDim.x / CL) {
             const Work w = decode(u, single, probs, units, rank, CL);
             gen_bar();  // every producer is done with the previous table
@@ -497,6 +560,89 @@ __global__ void __launch_bounds__(kThreads, 1)
                     stage = 0;
                     phase ^= 1u;
                 }
+            }
+        }
+    } else if constexpr (ADJ) {
+        // ---------------- adjoint epilogue ----------------
+        // Row r = 2 i + c of the tile holds component c of G_l[i] for the tile's
+        // 256 lags.  Lanes 2k and 2k + 1 of a warp hold the two components of one
+        // sample, so each lane gets its partner's value by a shuffle and adds
+        //   c = 0: sr G_r + si G_i,   c = 1: sr G_i - si G_r
+        // (conj(sigma(c_l[i])) G_l[i], sigma(c_l[i]) = (sr, si)) over the lags in
+        // order; the unit's per-row sums go to its slice of the partials.  The
+        // weights depend on i - l only: for each row half each warp stages the
+        // 16 + 255 it needs in its own 4 KB of shared memory (warp-level
+        // synchronisation only, so a warp that gives up on a wait cannot leave
+        // another one blocked).
+        const int quarter = warp & 3;
+        float2 *wts = reinterpret_cast<float2 *>(smem + T::kSmemStage + 4096 * quarter);
+        uint32_t chain = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
+            const Work w = decode(u, single, probs, units, rank, CL);
+            const int N = w.P.N;
+            const int i_lo = w.mt * (T::kRows / 2);  // first sample of the tile
+            const int col_lo = w.nt * TN;             // first lag column of the tile
+            float acc[MH];
+#pragma unroll
+            for (int h = 0; h < MH; ++h) acc[h] = 0.f;
+            const float csign = (lane & 1) ? -1.f : 1.f;
+            for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
+                const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
+                if (!(ok = mbar_wait(&tmem_full[buf], tpar, s_abort, err))) break;
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < MH; ++h) {
+                    const int il0 = 64 * h + 16 * quarter;  // the warp's first sample in the tile
+                    const int il = il0 + (lane >> 1);       // this lane's sample
+                    // wts[k] = sigma(c) at i - l = i_lo + il0 - lag0 - col_lo - 255 + k
+                    const int64_t d0 = (int64_t)i_lo + il0 - (w.P.lag0 + col_lo) - (TN - 1);
+                    __syncwarp();
+                    for (int k = lane; k < 16 + TN - 1; k += 32) {
+                        int64_t jj = d0 + k;
+                        float2 wv = make_float2(0.f, 0.f);
+                        if (w.P.flags & NDFT_F_CIRCULAR_LAG) {
+                            jj %= N;
+                            if (jj < 0) jj += N;
+                        }
+                        if (jj >= 0 && jj < N) {
+                            const float2 r = w.P.sref[jj];
+                            const float cr = (r.x > 0.f) ? 1.f : (r.x < 0.f ? -1.f : 0.f);
+                            const float cq = (r.y > 0.f) ? 1.f : (r.y < 0.f ? -1.f : 0.f);
+                            wv = make_float2(cr, (w.P.flags & NDFT_F_NO_CONJ_REF) ? cq : -cq);  // sigma(c)
+                        }
+                        wts[k] = wv;
+                    }
+                    __syncwarp();
+#pragma unroll 1
+                    for (int g = 0; g < TN / 16; ++g) {
+                        uint32_t r[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf + h) * TN + g * 16), r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float v = __uint_as_float(r[j]);
+                            const float o = __shfl_xor_sync(0xffffffffu, v, 1);
+                            const int cl = g * 16 + j;  // lag column within the tile
+                            if (col_lo + cl < w.P.ncols) {
+                                const float2 wv = wts[(il - il0) - cl + (TN - 1)];
+                                acc[h] = fmaf(wv.x, v, acc[h]);
+                                acc[h] = fmaf(csign * wv.y, o, acc[h]);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+            }
+            if (!ok) break;
+            // partial slice (n-tile, split) of the [slices][2N] partials
+            const int64_t slice = (int64_t)(w.nt * w.P.nsplit + w.split) * 2LL * N;
+#pragma unroll
+            for (int h = 0; h < MH; ++h) {
+                const int64_t row = (int64_t)w.mt * T::kRows + 128 * h + 32 * quarter + lane;
+                if (row < 2LL * N) out_base[slice + row] = acc[h];
             }
         }
     } else {
@@ -779,6 +925,26 @@ __global__ void __launch_bounds__(256) k_pack_tiles(const PackProb *__restrict__
     }
 }
 
+// Adjoint B operand: row (kb, l) holds bins 16 kb .. 16 kb + 15 of dA[l] as four
+// bf16 each, [hi_r, lo_r, hi_i, lo_i] (hi = bf16(a), lo = bf16(a - hi)); bins
+// past nbins are zero.  One 8-byte entry per thread, coalesced over the bins.
+__global__ void __launch_bounds__(256) k_pack_adjoint(const float2 *__restrict__ dA, int nbins, int nlags,
+                                                       int kblocks, uint2 *__restrict__ B) {
+    const int64_t total = (int64_t)nlags * kblocks * 16;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = e / ((int64_t)kblocks * 16);
+        const int p = (int)(e - l * kblocks * 16);
+        const float2 a = p < nbins ? dA[l * nbins + p] : make_float2(0.f, 0.f);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(a.x, a.y);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(a.x - __low2float(hi), a.y - __high2float(hi));
+        const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi);
+        const uint32_t ul = *reinterpret_cast<const uint32_t *>(&lo);
+        const int kb = p >> 4, k = p & 15;
+        B[((int64_t)kb * nlags + l) * 16 + k] = make_uint2(__byte_perm(uh, ul, 0x5410), __byte_perm(uh, ul, 0x7632));
+    }
+}
+
 // Two-level angle table: entry j < nth is (cos, sin)((pi/2) 256 j / N), entry
 // nth + j (j < 256) is (cos, sin)((pi/2) j / N); fp64, rounded to fp32.
 __global__ void k_angles(int N, int nth, float2 *__restrict__ ang) {
@@ -881,11 +1047,11 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH, int CL, bool BT = false>
+template <int MH, int CL, bool BT = false, bool ADJ = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
-    auto kern = k_ternary_gemm<MH, CL, BT>;
+    auto kern = k_ternary_gemm<MH, CL, BT, ADJ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(CL == 2 ? p.tmap_host2 : p.tmap_host);
@@ -1063,6 +1229,56 @@ cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, i
     pp.ncols = nlags;
     pp.kblocks = (p.d.n + 7) / 8;
     return run_single(p, pp, true, nlags, s_surv, s_ref, A, s, launches);
+}
+
+// Adjoint of the CAF on the tensor cores: G_l[i] = sum_p conj(S[p][i]) dA[l][p]
+// as a contraction with rows = (sample, Re/Im), columns = lags and K = bins x
+// [dA_hi_r, dA_lo_r, dA_hi_i, dA_lo_i], then ds[i] = sum_l conj(sigma(c_l[i]))
+// G_l[i] in the epilogue.  Partials per (lag tile, split) are summed in order.
+// Returns cudaErrorNotSupported when the plan's workspace cannot hold it (the
+// caller then uses the CUDA-core kernel).
+cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nlags, const void *dA, void *ds,
+                                   cudaStream_t s, int *launches) {
+    const int N = p.d.n, nb = p.d.nbins;
+    const int kblocks = (nb + 15) / 16;
+    const size_t b_need = (size_t)kblocks * nlags * 128;
+    Problem P{};
+    P.N = N;
+    P.p0 = p.d.p0;
+    P.nbins = nb;
+    P.ncols = nlags;
+    P.kblocks = kblocks;
+    P.mtiles = (2 * N + 255) / 256;
+    P.ntiles = (nlags + TN - 1) / TN;
+    const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+    // split the bins only while tiles are scarce, keeping >= 16 K blocks per unit
+    // (each unit's epilogue weighs and folds 256 lag columns per row)
+    P.nsplit = tiles >= p.sm_count
+                   ? 1
+                   : (int)std::max<int64_t>(1, std::min<int64_t>(kblocks / 16, (2LL * p.sm_count + tiles - 1) / tiles));
+    const int64_t slices = (int64_t)P.ntiles * P.nsplit;
+    const size_t part_need = (size_t)slices * 2 * N * sizeof(float);
+    if (b_need > p.b_bytes || part_need > p.part_bytes) return cudaErrorNotSupported;
+    P.b_row0 = 0;
+    P.ld = 0;
+    P.split_stride = 0;
+    P.out_off = 0;
+    P.sref = static_cast<const float2 *>(s_ref);
+    P.lag0 = lag0;
+    P.flags = p.d.flags;
+    const int64_t total = (int64_t)nlags * kblocks * 16;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p.sm_count * 16);
+    k_pack_adjoint<<<blocks, 256, 0, s>>>(static_cast<const float2 *>(dA), nb, nlags, kblocks,
+                                          static_cast<uint2 *>(p.ws));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + p.b_bytes);
+    if ((e = launch_gemm<2, 1, false, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
+        cudaSuccess)
+        return e;
+    *launches += 2;
+    return launch_reduce_splits(part, (int)slices, 2LL * N, static_cast<float *>(ds), s);
 }
 
 // Batched CPIs: per-CPI angle tables, packed-B regions and a work list of

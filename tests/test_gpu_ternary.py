@@ -180,3 +180,20 @@ def test_plan_allocation_failure_is_reported(api):
     x = scenes.cn(np.random.default_rng(52), (4, 64)).astype(np.complex64)
     q = api.Plan(64, max_batch=4, form="ternary", prec="bf16x2")
     assert relerr(q.ndft(dev(x)).cpu().numpy(), oracle.ndft(x.astype(np.complex128))) < TOL
+
+
+@pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [(700, 2, 70, -20, 40, 0), (4133, -3, 300, -48, 96, 0),
+                                                         (2048, 10, 257, 0, 512, 1), (1500, 1400, 33, -7, 17, 2)])
+def test_ternary_adjoint_tensor_cores(api, N, lag0, nlags, p0, nbins, flags):
+    """caf_backward on a tensor-core plan runs the transposed ternary contraction
+    on tcgen05 (dA as bf16 hi + lo against exact signs); against the fp64 oracle
+    adjoint within the fp32 bar, ragged tiles and the flags included."""
+    sc = scenes.radar_scene(N=N, nlags=nlags, nbins=min(nbins, 64), seed=53 + N % 7)
+    rng = np.random.default_rng(54)
+    dA = scenes.cn(rng, (nlags, nbins))
+    want = oracle.caf_adjoint(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, dA, flags=flags)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="ternary", prec="bf16x2")
+    got = p.caf_backward(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags, dev(dA.astype(np.complex64))).cpu().numpy()
+    p.query_error()
+    assert p.last_launches() == 3  # pack, contraction, ordered sum of the partials
+    assert relerr(got, want) < TOL
