@@ -132,7 +132,18 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
     out["nfft_1024_x65536"] = {"ms": ms, "vectors_per_s": x.shape[0] / (ms / 1e3),
                                "hbm_gbs": moved / (ms / 1e3) / 1e9, "hbm_frac": moved / (ms / 1e3) / 1e9 / hbm_peak_gbs,
                                "butterflies_per_s": x.shape[0] * 512 * 10 / (ms / 1e3)}
-    del x, y
+    # the NDFT of the same batch, both forms (the transform the NFFT approximates
+    # faster), with the share of vectors whose NFFT and NDFT peaks coincide
+    X = torch.empty_like(x)
+    for form, prec in (("ternary", "bf16x2"), ("direct", "fp32")):
+        p = api.Plan(1024, max_batch=x.shape[0], form=form, prec=prec, device=dev)
+        ms = _time_ms(lambda: p.ndft(x, out=X), 3 if form == "ternary" else 1, flush)
+        out[f"ndft_1024_x65536_{form}"] = {"ms": ms, "vectors_per_s": x.shape[0] / (ms / 1e3),
+                                           "otimes_per_s": x.shape[0] * 1024 * 1024 / (ms / 1e3)}
+    i_nfft, _ = api.argmax(y)
+    i_ndft, _ = api.argmax(X)
+    out["nfft_vs_ndft_peak_agreement"] = float((i_nfft == i_ndft).float().mean().item())
+    del x, y, X
     # NDFT of the N=64 tone batch
     xt = torch.from_numpy(scenes.tone_batch()).to(dev)
     for form, prec in (("direct", "fp32"), ("ternary", "bf16x2")):
@@ -225,7 +236,20 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
         s = torch.from_numpy(sc.s_surv).to(dev).requires_grad_(True)
         api.caf_autograd(s, sr, plan, 0, 512).abs()[mask].sum().backward()
     ms = _time_ms(fb, 5)
-    out["caf_16384_fwd_bwd"] = {"ms": ms, "cells": 512 * 512}
+    # the adjoint alone (transposed ternary contraction on the tensor cores)
+    ss = torch.from_numpy(sc.s_surv).to(dev)
+    dA = torch.randn(512, 512, dtype=torch.complex64, device=dev)
+    ds = torch.empty(sc.N, dtype=torch.complex64, device=dev)
+    plan.caf_backward(ss, sr, 0, 512, dA, out=ds)
+    torch.cuda.synchronize()
+    plan.timer_start(20)
+    for _ in range(20):
+        plan.caf_backward(ss, sr, 0, 512, dA, out=ds)
+    bms, bn = plan.timer_read()
+    bwd_ms = bms / max(bn, 1)
+    issued = 2.0 * (2 * sc.N) * 512 * (4 * 512)  # rows x lags x K (bins x hi/lo x re/im), 2 flop per MAC
+    out["caf_16384_fwd_bwd"] = {"ms": ms, "cells": 512 * 512, "backward_kernel_ms": bwd_ms,
+                                "backward_issued_tflops": issued / (bwd_ms / 1e3) / 1e12}
     return out
 
 
