@@ -23,7 +23,8 @@ Every function states the passage of the paper it follows:
 ``caf_nfft``           Eq. 12a with the NFFT over samples (Sec. 5)
 ``caf_12b``            Eq. 12b, (x) lag product then the linear DFT
 ``*_q14``              the same in Q1.14 integers, sums modulo 2^32
-``caf_adjoint``        derivative of Eq. 1-2 chained through Eq. 6, 12a
+``caf_adjoint``        derivative of Eq. 1-2 chained through Eq. 6, 12a (s_surv)
+``caf_adjoint_ref``    the same with respect to s_ref
 =====================  ====================================================
 """
 from __future__ import annotations
@@ -85,11 +86,12 @@ def _load():
             lib.oracle_ndft_q14.argtypes = [P, i64, i64, i64, i64, P, P]
             lib.oracle_caf_q14.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
             lib.oracle_caf_adjoint.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
+            lib.oracle_caf_adjoint_ref.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
             lib.oracle_num_threads.restype = i32
             for name in ("oracle_ndft", "oracle_nfft", "oracle_nfft_f32", "oracle_nfft_dif",
                          "oracle_nfft_dif_f32", "oracle_lagprod",
                          "oracle_lagprod_f32", "oracle_caf", "oracle_caf_cells", "oracle_ndft_q14",
-                         "oracle_caf_q14", "oracle_caf_adjoint"):
+                         "oracle_caf_q14", "oracle_caf_adjoint", "oracle_caf_adjoint_ref"):
                 getattr(lib, name).restype = i32
             _lib = lib
     return _lib
@@ -304,6 +306,18 @@ def caf_adjoint(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, dA, f
     ds = np.zeros(ss.size, np.complex128)
     _check(_load().oracle_caf_adjoint(_ptr(ss), _ptr(sr), ss.size, lag0, nlags, p0, nbins, flags,
                                       _ptr(g), _ptr(ds)), "caf_adjoint")
+    return ds
+
+
+def caf_adjoint_ref(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, dA, flags: int = 0):
+    """dL/ds_ref (as dRe + j dIm) given dA = dL/dRe A + j dL/dIm A, shape [nlags, nbins]:
+    the chain rule of Eq. 1-2 with d(a (x) b)/db = sgn(a), through Eq. 6 and Eq. 12a."""
+    ss, sr = _c128(s_surv), _c128(s_ref)
+    g = _c128(dA)
+    assert g.shape == (nlags, nbins)
+    ds = np.zeros(sr.size, np.complex128)
+    _check(_load().oracle_caf_adjoint_ref(_ptr(ss), _ptr(sr), ss.size, lag0, nlags, p0, nbins, flags,
+                                          _ptr(g), _ptr(ds)), "caf_adjoint_ref")
     return ds
 
 

@@ -640,6 +640,54 @@ int oracle_caf_adjoint(const double *s_surv, const double *s_ref, int64_t N, int
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the CAF with respect to s_ref, by the same chain rule with the */
+/* other operand of the lag product: d(a (x) b)/db = sgn(a) where b != 0.    */
+/*  stage 1 (s (x) c):  dz_r/dc_r = sgn(s_r), dz_r/dc_i = -sgn(s_i),        */
+/*                      dz_i/dc_r = sgn(s_i), dz_i/dc_i =  sgn(s_r)         */
+/*  and c = conj(s_ref[j]) (s_ref[j] with the no-conjugate flag) negates    */
+/*  the imaginary component.  For each j the lags l that read s_ref[j] are  */
+/*  those with ref_index(i, l) = j, i.e. i = j + l (modulo N when the lag   */
+/*  is circular; otherwise only 0 <= i < N).                                */
+/* dref[j] = dL/dRe s_ref[j] + j dL/dIm s_ref[j].                            */
+/* ------------------------------------------------------------------------ */
+int oracle_caf_adjoint_ref(const double *s_surv, const double *s_ref, int64_t N, int64_t lag0, int64_t nlags,
+                           int64_t p0, int64_t nbins, uint32_t flags, const double *dA, double *dref) {
+    if (N <= 0 || nlags < 0 || nbins < 0) return 1;
+    double *W = twiddle_table64(N);
+    if (!W) return 2;
+    (void)s_ref;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < N; ++j) {
+        double gr = 0.0, gi = 0.0;
+        for (int64_t a = 0; a < nlags; ++a) {
+            int64_t l = lag0 + a;
+            int64_t i = j + l;
+            if (flags & ORACLE_F_CIRCULAR_LAG) i = mod_pos(i, N);
+            else if (i < 0 || i >= N) continue; /* no sample reads s_ref[j] at this lag */
+            /* dL/dz_r, dL/dz_i of z_l[i], accumulated over the bins of this lag */
+            double gzr = 0.0, gzi = 0.0;
+            for (int64_t k = 0; k < nbins; ++k) {
+                int64_t p = mod_pos(p0 + k, N);
+                int64_t m = (i * p) % N;
+                double swr = sgn(W[2 * m]), swi = sgn(W[2 * m + 1]);
+                double ar = dA[2 * (a * nbins + k)], ai = dA[2 * (a * nbins + k) + 1];
+                gzr += ar * swr + ai * swi;
+                gzi += ar * (-swi) + ai * swr;
+            }
+            double ssr = sgn(s_surv[2 * i]), ssi = sgn(s_surv[2 * i + 1]);
+            double gcr = gzr * ssr + gzi * ssi;    /* dL/dc_r */
+            double gci = gzr * (-ssi) + gzi * ssr; /* dL/dc_i */
+            gr += gcr;
+            gi += (flags & ORACLE_F_NO_CONJ_REF) ? gci : -gci;
+        }
+        dref[2 * j] = gr;
+        dref[2 * j + 1] = gi;
+    }
+    free(W);
+    return 0;
+}
+
 /* Threads the OpenMP runtime will use (reported by the CPU baseline). */
 #ifdef _OPENMP
 #include <omp.h>

@@ -531,3 +531,85 @@ def test_adjoint_finite_differences(oracle):
             assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (i, comp, fd, an)
             checked += 1
     assert checked >= 40
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+def test_adjoint_ref_finite_differences(oracle, flags):
+    """dL/ds_ref against central differences of the fp64 forward (Eq. 12a)."""
+    rng = np.random.default_rng(40 + flags)
+    N, lag0, nlags, p0, nbins = 40, -2, 7, -3, 9
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    A = oracle.caf(ss, sr, lag0, nlags, p0, nbins, flags=flags)
+    mask = np.zeros(A.shape, bool)
+    mask[1:6, 1:8] = True
+    L, gA = oracle.masked_abs_loss_grad(A, mask)
+    dref = oracle.caf_adjoint_ref(ss, sr, lag0, nlags, p0, nbins, gA, flags=flags)
+    zs = np.stack([oracle.lagprod(ss, sr, l, flags=flags) for l in range(lag0, lag0 + nlags)])
+    zr = np.abs(zs.real[zs.real != 0]).min()
+    zi = np.abs(zs.imag[zs.imag != 0]).min()
+    checked = 0
+    for j in range(N):
+        margin = min(abs(sr[j].real), abs(sr[j].imag), zr, zi)
+        h = min(0.25 * margin, 1e-4)
+        if h < 1e-7:
+            continue
+        for comp, unit in ((0, 1.0), (1, 1j)):
+            rp, rm = sr.copy(), sr.copy()
+            rp[j] += h * unit
+            rm[j] -= h * unit
+            Lp = np.sum(np.abs(oracle.caf(ss, rp, lag0, nlags, p0, nbins, flags=flags))[mask])
+            Lm = np.sum(np.abs(oracle.caf(ss, rm, lag0, nlags, p0, nbins, flags=flags))[mask])
+            fd = (Lp - Lm) / (2 * h)
+            an = dref[j].real if comp == 0 else dref[j].imag
+            assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (j, comp, fd, an)
+            checked += 1
+    assert checked >= 30
+    # the non-circular window leaves the first and last samples of s_ref unread at some lags
+    assert np.any(dref != 0)
+
+
+def test_adjoints_against_torch_autograd(oracle):
+    """Both adjoints against torch autograd through a plain elementwise forward of
+    Eq. 1-2 / 6 / 12a (sign and abs only: autograd's own derivative rules)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(77)
+    N, lag0, nlags, p0, nbins = 24, -3, 6, 2, 7
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    gA = scenes.cn(rng, (nlags, nbins))
+
+    def ot(a, b):  # Eq. 1-2
+        return torch.sign(a * b) * (torch.abs(a) + torch.abs(b))
+
+    def cot(ar, ai, br, bi):  # Eq. 6
+        return ot(ar, br) - ot(ai, bi), ot(ar, bi) + ot(ai, br)
+
+    t = lambda v: torch.tensor(v, dtype=torch.float64, requires_grad=True)
+    sr_r, sr_i, ss_r, ss_i = t(sr.real), t(sr.imag), t(ss.real), t(ss.imag)
+    n = torch.arange(N, dtype=torch.float64)
+    loss = 0.0
+    for a in range(nlags):
+        l = lag0 + a
+        idx = [i - l for i in range(N)]
+        ok = torch.tensor([0 <= j < N for j in idx])
+        jj = torch.tensor([min(max(j, 0), N - 1) for j in idx])
+        cr = torch.where(ok, sr_r[jj], torch.zeros(()))
+        ci = torch.where(ok, -sr_i[jj], torch.zeros(()))
+        zr, zi = cot(ss_r, ss_i, cr, ci)
+        for k in range(nbins):
+            p = p0 + k
+            th = 2 * np.pi * ((n * p) % N) / N
+            wr, wi = torch.cos(th), -torch.sin(th)
+            # the axis twiddles are exactly 0 (a (x) 0 = 0), not the 1e-16 of cos/sin
+            wr = torch.where(wr.abs() < 1e-12, torch.zeros(()), wr)
+            wi = torch.where(wi.abs() < 1e-12, torch.zeros(()), wi)
+            Ar, Ai = cot(zr, zi, wr, wi)
+            loss = loss + gA[a, k].real * Ar.sum() + gA[a, k].imag * Ai.sum()
+    loss.backward()
+    want_ref = sr_r.grad.numpy() + 1j * sr_i.grad.numpy()
+    want_surv = ss_r.grad.numpy() + 1j * ss_i.grad.numpy()
+    got_ref = oracle.caf_adjoint_ref(ss, sr, lag0, nlags, p0, nbins, gA)
+    got_surv = oracle.caf_adjoint(ss, sr, lag0, nlags, p0, nbins, gA)
+    np.testing.assert_allclose(got_ref, want_ref, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(got_surv, want_surv, rtol=0, atol=1e-9)
