@@ -171,6 +171,25 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
 ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                          int32_t nlags, const void *dA, void *ds, cudaStream_t stream);
 
+/* Adjoint of caf_exec with respect to both inputs (complex64 plans).  With
+ * G_l[i] = sum_p conj(S[p][i]) dA[l][p] as for caf_backward:
+ *   ds_surv[i] = sum_l conj(sigma(c_l[i])) G_l[i]                  (= caf_backward)
+ *   ds_ref[j]  = sum_l conj(conj(sigma(s_surv[i])) G_l[i]),  i = j + l
+ * (i taken modulo N with NDFT_F_CIRCULAR_LAG, else only 0 <= i < N; with
+ * NDFT_F_NO_CONJ_REF the outer conj is dropped): the derivative
+ * d(a (x) b)/db = sgn(a) of Eq. 1-2 for the s_ref operand of the lag product,
+ * chained through Eq. 6 and Eq. 12a.  ds_ref[j] = dL/dRe s_ref[j] + j dL/dIm
+ * s_ref[j].  ds_surv may be NULL (then only ds_ref is formed); with ds_ref NULL
+ * the call is caf_backward.  G is formed once for both, lag chunks as large as
+ * the plan's workspace holds (the tensor cores on the ternary form, else CUDA
+ * cores), then folded by a deterministic kernel.  s_surv, s_ref, ds_*: [N]
+ * complex64; dA: [nlags][nbins] complex64; all device pointers, 16-byte
+ * aligned (NDFT_E_INVALID otherwise).  NDFT_E_UNSUPPORTED on Q1.14,
+ * NDFT_FORM_NFFT and NDFT_FORM_FFT plans. */
+ndft_status caf_backward_inputs(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
+                                int32_t nlags, const void *dA, void *ds_surv, void *ds_ref,
+                                cudaStream_t stream);
+
 /* Allocation-free variant of caf_exec for the direct fp32 form (the paper has
  * no counterpart: this serves callers that cannot allocate device memory at
  * the point of use, such as a real-time loop that forbids cudaMalloc after

@@ -87,11 +87,13 @@ def _load():
             lib.oracle_caf_q14.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
             lib.oracle_caf_adjoint.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
             lib.oracle_caf_adjoint_ref.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, P]
+            lib.oracle_caf_adjoint_at.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, i32, P, i64, P]
             lib.oracle_num_threads.restype = i32
             for name in ("oracle_ndft", "oracle_nfft", "oracle_nfft_f32", "oracle_nfft_dif",
                          "oracle_nfft_dif_f32", "oracle_lagprod",
                          "oracle_lagprod_f32", "oracle_caf", "oracle_caf_cells", "oracle_ndft_q14",
-                         "oracle_caf_q14", "oracle_caf_adjoint", "oracle_caf_adjoint_ref"):
+                         "oracle_caf_q14", "oracle_caf_adjoint", "oracle_caf_adjoint_ref",
+                         "oracle_caf_adjoint_at"):
                 getattr(lib, name).restype = i32
             _lib = lib
     return _lib
@@ -319,6 +321,20 @@ def caf_adjoint_ref(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, d
     _check(_load().oracle_caf_adjoint_ref(_ptr(ss), _ptr(sr), ss.size, lag0, nlags, p0, nbins, flags,
                                           _ptr(g), _ptr(ds)), "caf_adjoint_ref")
     return ds
+
+
+def caf_adjoint_at(s_surv, s_ref, lag0: int, nlags: int, p0: int, nbins: int, dA, which: str, idx,
+                   flags: int = 0):
+    """caf_adjoint (which="surv") or caf_adjoint_ref (which="ref") at the listed indices only."""
+    ss, sr = _c128(s_surv), _c128(s_ref)
+    g = _c128(dA)
+    assert g.shape == (nlags, nbins)
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(ix.size, np.complex128)
+    _check(_load().oracle_caf_adjoint_at(_ptr(ss), _ptr(sr), ss.size, lag0, nlags, p0, nbins, flags, _ptr(g),
+                                         {"surv": 0, "ref": 1}[which], _ptr(ix), ix.size, _ptr(out)),
+           "caf_adjoint_at")
+    return out
 
 
 def masked_abs_loss_grad(A: np.ndarray, mask: np.ndarray):

@@ -602,6 +602,45 @@ int oracle_caf_q14(const int16_t *s_surv, const int16_t *s_ref, int64_t N, int64
 /* ------------------------------------------------------------------------ */
 static double sgn(double v) { return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0); }
 
+/* dL/dz_r, dL/dz_i of z_l[i] (l = lag0 + a): the stage-2 partials summed over */
+/* the bins of lag a. */
+static void adj_gz(const double *W, int64_t N, int64_t i, int64_t a, int64_t p0, int64_t nbins,
+                   const double *dA, double *gzr, double *gzi) {
+    double r = 0.0, q = 0.0;
+    for (int64_t k = 0; k < nbins; ++k) {
+        int64_t p = mod_pos(p0 + k, N);
+        int64_t m = (i * p) % N;
+        double swr = sgn(W[2 * m]), swi = sgn(W[2 * m + 1]);
+        double ar = dA[2 * (a * nbins + k)], ai = dA[2 * (a * nbins + k) + 1];
+        r += ar * swr + ai * swi;
+        q += ar * (-swi) + ai * swr;
+    }
+    *gzr = r;
+    *gzi = q;
+}
+
+/* ds[i] (with respect to s_surv) */
+static void adj_surv_at(const double *s_ref, const double *W, int64_t N, int64_t lag0, int64_t nlags, int64_t p0,
+                        int64_t nbins, uint32_t flags, const double *dA, int64_t i, double *out) {
+    double gr = 0.0, gi = 0.0;
+    for (int64_t a = 0; a < nlags; ++a) {
+        int64_t l = lag0 + a;
+        int64_t j = ref_index(i, l, N, flags);
+        double cr = 0.0, ci = 0.0;
+        if (j >= 0) {
+            cr = s_ref[2 * j];
+            ci = (flags & ORACLE_F_NO_CONJ_REF) ? s_ref[2 * j + 1] : -s_ref[2 * j + 1];
+        }
+        double gzr, gzi;
+        adj_gz(W, N, i, a, p0, nbins, dA, &gzr, &gzi);
+        double scr = sgn(cr), sci = sgn(ci);
+        gr += gzr * scr + gzi * sci;
+        gi += gzr * (-sci) + gzi * scr;
+    }
+    out[0] = gr;
+    out[1] = gi;
+}
+
 int oracle_caf_adjoint(const double *s_surv, const double *s_ref, int64_t N, int64_t lag0, int64_t nlags,
                        int64_t p0, int64_t nbins, uint32_t flags, const double *dA, double *ds) {
     if (N <= 0 || nlags < 0 || nbins < 0) return 1;
@@ -609,33 +648,7 @@ int oracle_caf_adjoint(const double *s_surv, const double *s_ref, int64_t N, int
     if (!W) return 2;
     (void)s_surv;
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < N; ++i) {
-        double gr = 0.0, gi = 0.0;
-        for (int64_t a = 0; a < nlags; ++a) {
-            int64_t l = lag0 + a;
-            int64_t j = ref_index(i, l, N, flags);
-            double cr = 0.0, ci = 0.0;
-            if (j >= 0) {
-                cr = s_ref[2 * j];
-                ci = (flags & ORACLE_F_NO_CONJ_REF) ? s_ref[2 * j + 1] : -s_ref[2 * j + 1];
-            }
-            /* dL/dz_r, dL/dz_i accumulated over the bins of this lag */
-            double gzr = 0.0, gzi = 0.0;
-            for (int64_t k = 0; k < nbins; ++k) {
-                int64_t p = mod_pos(p0 + k, N);
-                int64_t m = (i * p) % N;
-                double swr = sgn(W[2 * m]), swi = sgn(W[2 * m + 1]);
-                double ar = dA[2 * (a * nbins + k)], ai = dA[2 * (a * nbins + k) + 1];
-                gzr += ar * swr + ai * swi;
-                gzi += ar * (-swi) + ai * swr;
-            }
-            double scr = sgn(cr), sci = sgn(ci);
-            gr += gzr * scr + gzi * sci;
-            gi += gzr * (-sci) + gzi * scr;
-        }
-        ds[2 * i] = gr;
-        ds[2 * i + 1] = gi;
-    }
+    for (int64_t i = 0; i < N; ++i) adj_surv_at(s_ref, W, N, lag0, nlags, p0, nbins, flags, dA, i, ds + 2 * i);
     free(W);
     return 0;
 }
@@ -651,6 +664,27 @@ int oracle_caf_adjoint(const double *s_surv, const double *s_ref, int64_t N, int
 /*  is circular; otherwise only 0 <= i < N).                                */
 /* dref[j] = dL/dRe s_ref[j] + j dL/dIm s_ref[j].                            */
 /* ------------------------------------------------------------------------ */
+/* dref[j] (with respect to s_ref) */
+static void adj_ref_at(const double *s_surv, const double *W, int64_t N, int64_t lag0, int64_t nlags, int64_t p0,
+                       int64_t nbins, uint32_t flags, const double *dA, int64_t j, double *out) {
+    double gr = 0.0, gi = 0.0;
+    for (int64_t a = 0; a < nlags; ++a) {
+        int64_t l = lag0 + a;
+        int64_t i = j + l;
+        if (flags & ORACLE_F_CIRCULAR_LAG) i = mod_pos(i, N);
+        else if (i < 0 || i >= N) continue; /* no sample reads s_ref[j] at this lag */
+        double gzr, gzi;
+        adj_gz(W, N, i, a, p0, nbins, dA, &gzr, &gzi);
+        double ssr = sgn(s_surv[2 * i]), ssi = sgn(s_surv[2 * i + 1]);
+        double gcr = gzr * ssr + gzi * ssi;    /* dL/dc_r */
+        double gci = gzr * (-ssi) + gzi * ssr; /* dL/dc_i */
+        gr += gcr;
+        gi += (flags & ORACLE_F_NO_CONJ_REF) ? gci : -gci;
+    }
+    out[0] = gr;
+    out[1] = gi;
+}
+
 int oracle_caf_adjoint_ref(const double *s_surv, const double *s_ref, int64_t N, int64_t lag0, int64_t nlags,
                            int64_t p0, int64_t nbins, uint32_t flags, const double *dA, double *dref) {
     if (N <= 0 || nlags < 0 || nbins < 0) return 1;
@@ -658,31 +692,25 @@ int oracle_caf_adjoint_ref(const double *s_surv, const double *s_ref, int64_t N,
     if (!W) return 2;
     (void)s_ref;
 #pragma omp parallel for schedule(static)
-    for (int64_t j = 0; j < N; ++j) {
-        double gr = 0.0, gi = 0.0;
-        for (int64_t a = 0; a < nlags; ++a) {
-            int64_t l = lag0 + a;
-            int64_t i = j + l;
-            if (flags & ORACLE_F_CIRCULAR_LAG) i = mod_pos(i, N);
-            else if (i < 0 || i >= N) continue; /* no sample reads s_ref[j] at this lag */
-            /* dL/dz_r, dL/dz_i of z_l[i], accumulated over the bins of this lag */
-            double gzr = 0.0, gzi = 0.0;
-            for (int64_t k = 0; k < nbins; ++k) {
-                int64_t p = mod_pos(p0 + k, N);
-                int64_t m = (i * p) % N;
-                double swr = sgn(W[2 * m]), swi = sgn(W[2 * m + 1]);
-                double ar = dA[2 * (a * nbins + k)], ai = dA[2 * (a * nbins + k) + 1];
-                gzr += ar * swr + ai * swi;
-                gzi += ar * (-swi) + ai * swr;
-            }
-            double ssr = sgn(s_surv[2 * i]), ssi = sgn(s_surv[2 * i + 1]);
-            double gcr = gzr * ssr + gzi * ssi;    /* dL/dc_r */
-            double gci = gzr * (-ssi) + gzi * ssr; /* dL/dc_i */
-            gr += gcr;
-            gi += (flags & ORACLE_F_NO_CONJ_REF) ? gci : -gci;
-        }
-        dref[2 * j] = gr;
-        dref[2 * j + 1] = gi;
+    for (int64_t j = 0; j < N; ++j) adj_ref_at(s_surv, W, N, lag0, nlags, p0, nbins, flags, dA, j, dref + 2 * j);
+    free(W);
+    return 0;
+}
+
+/* Either adjoint at listed indices only (which = 0: s_surv, 1: s_ref), for */
+/* sampled checks of large transforms. */
+int oracle_caf_adjoint_at(const double *s_surv, const double *s_ref, int64_t N, int64_t lag0, int64_t nlags,
+                          int64_t p0, int64_t nbins, uint32_t flags, const double *dA, int32_t which,
+                          const int64_t *idx, int64_t nidx, double *out) {
+    if (N <= 0 || nlags < 0 || nbins < 0 || nidx < 0 || (which != 0 && which != 1)) return 1;
+    for (int64_t e = 0; e < nidx; ++e)
+        if (idx[e] < 0 || idx[e] >= N) return 1;
+    double *W = twiddle_table64(N);
+    if (!W) return 2;
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t e = 0; e < nidx; ++e) {
+        if (which == 0) adj_surv_at(s_ref, W, N, lag0, nlags, p0, nbins, flags, dA, idx[e], out + 2 * e);
+        else adj_ref_at(s_surv, W, N, lag0, nlags, p0, nbins, flags, dA, idx[e], out + 2 * e);
     }
     free(W);
     return 0;

@@ -18,7 +18,7 @@ F_NO_CONJ_REF, F_CIRCULAR_LAG, F_NFFT_DIF = 0x1, 0x2, 0x4
 
 # every symbol include/ndft.h declares
 EXPORTS = ("ndft_plan", "ndft_plan_batched", "ndft_plan_destroy", "ndft_exec", "nfft_exec", "caf_exec",
-           "caf_exec_batched", "caf_backward", "ndft_argmax", "ndft_query_error", "ndft_get_twiddles",
+           "caf_exec_batched", "caf_backward", "caf_backward_inputs", "ndft_argmax", "ndft_query_error", "ndft_get_twiddles",
            "ndft_plan_bytes", "ndft_last_launches", "ndft_set_tuning", "ndft_timer_start", "ndft_timer_read",
            "ndft_status_string", "ndft_version", "ndft_last_cuda_error", "caf_exec_noalloc")
 
@@ -66,6 +66,7 @@ def load() -> ctypes.CDLL:
         "caf_exec": (i32, [P, P, P, i32, i32, P, P]),
         "caf_exec_batched": (i32, [P, P, P, P, P]),
         "caf_backward": (i32, [P, P, P, i32, i32, P, P, P]),
+        "caf_backward_inputs": (i32, [P, P, P, i32, i32, P, P, P, P]),
         "ndft_argmax": (i32, [P, i64, i64, P, P, P]),
         "ndft_query_error": (i32, [P, P]),
         "ndft_get_twiddles": (i32, [P, i32, P, P]),

@@ -187,6 +187,19 @@ class Plan:
         return out
 
 
+    def caf_backward_inputs(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int,
+                            dA: torch.Tensor, surv: bool = True):
+        """(dL/ds_surv or None, dL/ds_ref), each dRe + j dIm, from one adjoint contraction."""
+        _need(s_surv, torch.complex64, "s_surv")
+        _need(s_ref, torch.complex64, "s_ref")
+        _need(dA, torch.complex64, "dA")
+        ds_ref = torch.empty(self.n, dtype=torch.complex64, device=s_ref.device)
+        ds_surv = torch.empty(self.n, dtype=torch.complex64, device=s_ref.device) if surv else None
+        L.check(self.lib.caf_backward_inputs(self.handle, _ptr(s_surv), _ptr(s_ref), int(lag0), int(nlags),
+                                             _ptr(dA), _ptr(ds_surv) if surv else None, _ptr(ds_ref),
+                                             _stream(s_ref.device)), "caf_backward_inputs")
+        return ds_surv, ds_ref
+
 class BatchedPlan:
     """caf_exec_batched over a fixed list of CPIs (one persistent launch sequence).
 
@@ -257,9 +270,10 @@ def argmax(X: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
 
 
 class CafFunction(torch.autograd.Function):
-    """A = CAF(s_surv; s_ref) (Eq. 12a) with the hand-written adjoint as its backward.
+    """A = CAF(s_surv; s_ref) (Eq. 12a) with the hand-written adjoints as its backward.
 
-    Gradient convention is PyTorch's for complex inputs: s_surv.grad = dL/dRe + j dL/dIm."""
+    Gradient convention is PyTorch's for complex inputs: s_surv.grad = dL/dRe + j dL/dIm
+    (s_ref likewise)."""
 
     @staticmethod
     def forward(ctx, s_surv, s_ref, plan: Plan, lag0: int, nlags: int):
@@ -271,8 +285,14 @@ class CafFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dA):
         s_surv, s_ref = ctx.saved_tensors
-        ds = ctx.plan.caf_backward(s_surv.detach().contiguous(), s_ref.detach().contiguous(), ctx.lag0, ctx.nlags,
-                                   dA.contiguous())
+        ss, sr, g = s_surv.detach().contiguous(), s_ref.detach().contiguous(), dA.contiguous()
+        want_surv, want_ref = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if want_ref:
+            ds, dr = ctx.plan.caf_backward_inputs(ss, sr, ctx.lag0, ctx.nlags, g, surv=want_surv)
+            return ds, dr, None, None, None
+        if not want_surv:
+            return None, None, None, None, None
+        ds = ctx.plan.caf_backward(ss, sr, ctx.lag0, ctx.nlags, g)
         return ds, None, None, None, None
 
 

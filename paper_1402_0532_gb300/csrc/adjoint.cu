@@ -1,16 +1,22 @@
 // adjoint.cu -- gradient of the nonlinear ambiguity surface (Eq. 12a) with
-// respect to the surveillance signal.
+// respect to its inputs.
 //
-// Where no operand is 0, d(a (x) b)/da = sgn(b) (from Eq. 1-2).  Through Eq. 6
-// this makes z (x) W act on dz as multiplication by S = sigma(W) and s (x) c
-// act on ds as multiplication by sigma(c), sigma(v) = sgn(v_r) + j sgn(v_i).
-// So, with dA = dL/dRe A + j dL/dIm A,
-//     G_l[i] = sum_k conj(S[p_k][i]) dA[l][k]            (transposed ternary contraction)
-//     ds[i]  = sum_l conj(sigma(c_l[i])) G_l[i],  c_l[i] = conj(s_ref[i - l]).
-// One block owns 64 samples x 64 lags, walks the bins in chunks of 16, then
-// folds its lags into one partial per sample; the partials of the lag tiles
-// are summed in order by the split-K reduction.
+// Where no operand is 0, d(a (x) b)/da = sgn(b) and d(a (x) b)/db = sgn(a)
+// (from Eq. 1-2).  Through Eq. 6 this makes z (x) W act on dz as
+// multiplication by S = sigma(W) and s (x) c act on ds as multiplication by
+// sigma(c) (on dc by sigma(s)), sigma(v) = sgn(v_r) + j sgn(v_i).  So, with
+// dA = dL/dRe A + j dL/dIm A,
+//     G_l[i]      = sum_k conj(S[p_k][i]) dA[l][k]       (transposed ternary contraction)
+//     ds_surv[i]  = sum_l conj(sigma(c_l[i])) G_l[i],    c_l[i] = conj(s_ref[i - l])
+//     ds_ref[j]   = sum_l conj(conj(sigma(s_surv[i])) G_l[i]),  i = j + l
+// (without the conjugation of s_ref: no outer conj in ds_ref).
+// k_caf_backward: one block owns 64 samples x 64 lags and walks the bins in
+// chunks of 16; it either folds its lags into one ds_surv partial per sample
+// (the partials of the lag tiles are summed in order by the split-K
+// reduction) or stores G for k_grad_fold, which forms both gradients.
 #include "internal.cuh"
+
+#include <algorithm>
 
 namespace ndft {
 
@@ -20,6 +26,7 @@ constexpr int TI = 64, TL = 64, KB = 16;
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
+template <bool STORE_G>
 __global__ void __launch_bounds__(256)
     k_caf_backward(const float2 *__restrict__ tw, const float2 *__restrict__ sref, int N, int p0, int nbins,
                    int lag0, int nlags, uint32_t flags, const float2 *__restrict__ dA, float2 *__restrict__ part) {
@@ -88,6 +95,19 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
     }
 
+    if constexpr (STORE_G) {
+        // G[l][i] for this thread's 4 lags x 4 samples (part is [nlags][N])
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = l0 + ty * 4 + q;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = i0 + tx + 16 * j;
+                if (l < nlags && i < N) part[(int64_t)l * N + i] = acc[q][j];
+            }
+        }
+        return;
+    }
     // multiply by conj(sigma(c_l[i])) and fold this thread's 4 lags
     float2 fold[4];
 #pragma unroll
@@ -125,7 +145,144 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Both gradients from G ([nsplit][nc][N] complex, split partials summed here)
+// for the nc lags lag_first .. lag_first + nc - 1.  A block owns 32
+// consecutive indices t (one per lane) and warp w takes the lags w, w + 8, ...;
+// the eight warp sums are added in warp order, so the result is deterministic.
+// ds_surv[t] uses G at sample t, ds_ref[t] at sample t + l.  accumulate = 0
+// stores, 1 adds to the previous chunk's values (in chunk order).
+__device__ __forceinline__ float2 sigma2(float2 v) { return make_float2(sgnf(v.x), sgnf(v.y)); }
+
+template <bool SURV, bool REF>
+__global__ void __launch_bounds__(256)
+    k_grad_fold(const float2 *__restrict__ G, int nsplit, int64_t split_stride, int N, int lag_first, int nc,
+                uint32_t flags, const float2 *__restrict__ s_surv, const float2 *__restrict__ s_ref,
+                float2 *__restrict__ ds_surv, float2 *__restrict__ ds_ref, int accumulate) {
+    __shared__ float2 red[2][8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + lane;
+    const bool circ = flags & NDFT_F_CIRCULAR_LAG, noconj = flags & NDFT_F_NO_CONJ_REF;
+    float2 gs = make_float2(0.f, 0.f), gr = make_float2(0.f, 0.f);
+    if (t < N) {
+#pragma unroll 4
+        for (int a = w; a < nc; a += 8) {
+            const int64_t l = (int64_t)lag_first + a;
+            const float2 *Ga = G + (int64_t)a * N;
+            if (SURV) {
+                int64_t j = t - l;  // the s_ref sample that meets s_surv[t] at lag l
+                if (circ) {
+                    j %= N;
+                    if (j < 0) j += N;
+                }
+                if (j >= 0 && j < N) {
+                    float2 g = Ga[t];
+                    for (int sp = 1; sp < nsplit; ++sp) {
+                        const float2 h = Ga[sp * split_stride + t];
+                        g.x += h.x;
+                        g.y += h.y;
+                    }
+                    const float2 r = __ldg(&s_ref[j]);
+                    const float cr = sgnf(r.x), ci = noconj ? sgnf(r.y) : -sgnf(r.y);  // sigma(c)
+                    gs.x += cr * g.x + ci * g.y;  // conj(sigma(c)) G
+                    gs.y += cr * g.y - ci * g.x;
+                }
+            }
+            if (REF) {
+                int64_t i = t + l;  // the s_surv sample that meets s_ref[t] at lag l
+                if (circ) {
+                    i %= N;
+                    if (i < 0) i += N;
+                }
+                if (i >= 0 && i < N) {
+                    float2 g = Ga[i];
+                    for (int sp = 1; sp < nsplit; ++sp) {
+                        const float2 h = Ga[sp * split_stride + i];
+                        g.x += h.x;
+                        g.y += h.y;
+                    }
+                    const float2 sg = sigma2(__ldg(&s_surv[i]));
+                    const float dr = sg.x * g.x + sg.y * g.y;  // conj(sigma(s)) G = dL/dc
+                    const float di = sg.x * g.y - sg.y * g.x;
+                    gr.x += dr;
+                    gr.y += noconj ? di : -di;  // c = conj(s_ref): conjugate back
+                }
+            }
+        }
+    }
+    red[0][w][lane] = gs;
+    red[1][w][lane] = gr;
+    __syncthreads();
+    if (w < 2 && t < N) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v.x += red[w][k][lane].x;
+            v.y += red[w][k][lane].y;
+        }
+        float2 *dst = w == 0 ? (SURV ? ds_surv : nullptr) : (REF ? ds_ref : nullptr);
+        if (dst) {
+            if (accumulate) {
+                const float2 o = dst[t];
+                v.x += o.x;
+                v.y += o.y;
+            }
+            dst[t] = v;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_caf_backward_inputs(Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
+                                       const void *dA, void *ds_surv, void *ds_ref, cudaStream_t s,
+                                       int *launches) {
+    const int N = p.d.n, nb = p.d.nbins ? p.d.nbins : N;
+    const float2 *dA2 = static_cast<const float2 *>(dA);
+    // lags per pass: as many as the workspace holds G for
+    bool tern = p.d.form == NDFT_FORM_TERNARY_GEMM;
+    int chunk = tern ? ternary_adjoint_g_lags(p, nlags) : 0;
+    if (chunk < 1) {
+        tern = false;
+        chunk = (int)std::min<int64_t>(nlags, (int64_t)(p.ws_alloc / ((size_t)N * sizeof(float2))));
+    }
+    if (chunk < 1) return cudaErrorNotSupported;
+    cudaError_t e = cudaSuccess;
+    for (int a0 = 0; a0 < nlags; a0 += chunk) {
+        const int nc = std::min(chunk, nlags - a0);
+        const float2 *G = nullptr;
+        int nsplit = 1;
+        int64_t sstride = 0;
+        if (tern) {
+            if ((e = launch_ternary_adjoint_g(p, nc, dA2 + (int64_t)a0 * nb, &G, &nsplit, &sstride, s, launches)) !=
+                cudaSuccess)
+                return e;
+        } else {
+            dim3 grid((N + TI - 1) / TI, (nc + TL - 1) / TL);
+            timer_begin(p, s);
+            k_caf_backward<true><<<grid, 256, 0, s>>>(p.tw32, nullptr, N, p.d.p0, nb, 0, nc, p.d.flags,
+                                                      dA2 + (int64_t)a0 * nb, static_cast<float2 *>(p.ws));
+            timer_end(p, s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            *launches += 1;
+            G = static_cast<const float2 *>(p.ws);
+        }
+        const int blocks = (N + 31) / 32;
+        auto *ss = static_cast<const float2 *>(s_surv);
+        auto *sr = static_cast<const float2 *>(s_ref);
+        auto *os = static_cast<float2 *>(ds_surv);
+        auto *orf = static_cast<float2 *>(ds_ref);
+        const int acc = a0 > 0;
+        if (ds_surv)
+            k_grad_fold<true, true><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss, sr,
+                                                           os, orf, acc);
+        else
+            k_grad_fold<false, true><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss,
+                                                            sr, os, orf, acc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 1;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_caf_backward(const Plan &p, const void *s_ref, int lag0, int nlags, const void *dA, void *ds,
                                 cudaStream_t s, int *launches) {
@@ -134,7 +291,7 @@ cudaError_t launch_caf_backward(const Plan &p, const void *s_ref, int lag0, int 
     dim3 grid((N + TI - 1) / TI, ltiles);
     float2 *part = (ltiles == 1) ? static_cast<float2 *>(ds) : static_cast<float2 *>(p.ws);
     timer_begin(p, s);
-    k_caf_backward<<<grid, 256, 0, s>>>(p.tw32, static_cast<const float2 *>(s_ref), N, p.d.p0, nb, lag0, nlags,
+    k_caf_backward<false><<<grid, 256, 0, s>>>(p.tw32, static_cast<const float2 *>(s_ref), N, p.d.p0, nb, lag0, nlags,
                                         p.d.flags, static_cast<const float2 *>(dA), part);
     timer_end(p, s);
     *launches += 1;

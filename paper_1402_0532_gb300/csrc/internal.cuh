@@ -44,7 +44,8 @@ struct Plan {
     float2 *comb = nullptr;      // 2N: comb-major copies of s_surv, s_ref (two-kernel DIT CAF)
     // workspace
     void *ws = nullptr;
-    size_t ws_bytes = 0;
+    size_t ws_alloc = 0;         // bytes of ws itself
+    size_t ws_bytes = 0;         // every workspace buffer of the plan
     int32_t *err = nullptr;      // device error word
     size_t table_bytes = 0;
     // batched
@@ -175,6 +176,9 @@ cudaError_t launch_argmax(const float2 *X, int64_t rows, int64_t cols, int64_t *
 // adjoint.cu
 cudaError_t launch_caf_backward(const Plan &p, const void *s_ref, int lag0, int nlags, const void *dA,
                                 void *ds, cudaStream_t s, int *launches);
+cudaError_t launch_caf_backward_inputs(Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
+                                       const void *dA, void *ds_surv, void *ds_ref, cudaStream_t s,
+                                       int *launches);
 
 // ternary.cu
 bool ternary_supported(const ndft_desc &d);
@@ -189,5 +193,8 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
                                    int *launches);
 cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nlags, const void *dA, void *ds,
                                    cudaStream_t s, int *launches);
+int ternary_adjoint_g_lags(const Plan &p, int nlags);
+cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const float2 **G, int *nsplit,
+                                     int64_t *split_stride, cudaStream_t s, int *launches);
 
 }  // namespace ndft

@@ -148,6 +148,7 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
         if (!fft_form(p.d.form)) ws = std::max(direct_ws_bytes(p.d, p.sm_count), backward_ws_bytes(p.d));
         if (tern) ws = std::max(ws, ternary_ws_bytes(p.d, p.sm_count));
         p.ws_bytes = ws;
+        p.ws_alloc = ws;
         if (ws && (e = cudaMalloc(&p.ws, ws)) != cudaSuccess) goto fail;
         const size_t nws = nfft_ws_bytes(p.d, &p.nfft_chunk);
         if (nws && (e = cudaMalloc(&p.nfft_ws, nws)) != cudaSuccess) goto fail;
@@ -246,6 +247,23 @@ ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref
         p.last_launches = 0;
     }
     return from_cuda(launch_caf_backward(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches));
+}
+
+ndft_status caf_backward_inputs(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
+                                int32_t nlags, const void *dA, void *ds_surv, void *ds_ref, cudaStream_t stream) {
+    if (!ds_ref) return ds_surv ? caf_backward(plan, s_surv, s_ref, lag0, nlags, dA, ds_surv, stream) : NDFT_E_INVALID;
+    const Range range("caf_backward_inputs");
+    if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
+    Plan &p = plan->p;
+    if (p.d.prec == NDFT_PREC_Q14 || fft_form(p.d.form)) return NDFT_E_UNSUPPORTED;
+    if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(dA) || !aligned16(ds_ref) ||
+        (ds_surv && !aligned16(ds_surv)))
+        return NDFT_E_INVALID;
+    p.last_launches = 0;
+    const cudaError_t e =
+        launch_caf_backward_inputs(p, s_surv, s_ref, lag0, nlags, dA, ds_surv, ds_ref, stream, &p.last_launches);
+    if (e == cudaErrorNotSupported) return NDFT_E_UNSUPPORTED;
+    return from_cuda(e);
 }
 
 ndft_status ndft_argmax(const void *X, int64_t rows, int64_t cols, int64_t *idx, float *val, cudaStream_t stream) {

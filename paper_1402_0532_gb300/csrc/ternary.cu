@@ -354,13 +354,16 @@ struct Tile {
 // loads half of the shared 256-column B tile and multicasts it to both, and
 // each stage is refilled only after both CTAs' MMAs released it.  `tmap` then
 // has a 128-row box.
-template <int MH, int CL, bool BT, bool ADJ>
+// ADJ selects the adjoint contractions (rows = samples, columns = lags, K =
+// bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
+// forward epilogue on a [lags][2N] fp32 output).
+template <int MH, int CL, bool BT, int ADJ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
                    int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
     static_assert(CL == 1 || (CL == 2 && MH == 1), "the cluster variant uses 128-row tiles");
-    static_assert(!ADJ || (MH == 2 && CL == 1 && !BT), "the adjoint runs on the 256-row tile");
+    static_assert(ADJ == 0 || (MH == 2 && CL == 1 && !BT), "the adjoint runs on the 256-row tile");
     using T = Tile<MH>;
     const int rank = CL == 2 ? (int)cluster_rank() : 0;
     constexpr int STG = T::kStages;
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        if constexpr (ADJ) {
+        if constexpr (ADJ != 0) {
             for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
                 const Work w = decode(u, single, probs, units, rank, CL);
                 const uint32_t N = (uint32_t)w.P.N;
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if constexpr (ADJ) {
+    } else if constexpr (ADJ == 1) {
         // ---------------- adjoint epilogue ----------------
         // Row r = 2 i + c of the tile holds component c of G_l[i] for the tile's
         // 256 lags.  Lanes 2k and 2k + 1 of a warp hold the two components of one
@@ -652,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
             const Work w = decode(u, single, probs, units, rank, CL);
-            const int64_t limit_m = 2LL * w.P.nbins;
+            const int64_t limit_m = ADJ == 2 ? 2LL * w.P.N : 2LL * w.P.nbins;  // output rows
             for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
                 const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
                 if (!(ok = mbar_wait(&tmem_full[buf], tpar, s_abort, err))) break;
@@ -1047,7 +1050,7 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH, int CL, bool BT = false, bool ADJ = false>
+template <int MH, int CL, bool BT = false, int ADJ = 0>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
@@ -1274,11 +1277,78 @@ cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nla
     if (e != cudaSuccess) return e;
     *launches += 1;
     float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + p.b_bytes);
-    if ((e = launch_gemm<2, 1, false, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
+    if ((e = launch_gemm<2, 1, false, 1>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
         cudaSuccess)
         return e;
     *launches += 2;
     return launch_reduce_splits(part, (int)slices, 2LL * N, static_cast<float *>(ds), s);
+}
+
+// The adjoint contraction alone: G_l[i] = sum_p conj(S[p][i]) dA[l][p] for the
+// `nc` lags of dA ([nc][nbins] complex), stored as fp32 complex
+// [nsplit][nc][N] in the workspace after the packed dA (the forward epilogue
+// with rows = (sample, Re/Im) and columns = lags).  The split partials are left
+// for the caller, whose fold over lags is linear in G.
+namespace {
+size_t adjoint_g_offset(int nb, int nc) {
+    const size_t b_need = (size_t)((nb + 15) / 16) * nc * 128;
+    return (b_need + 1023) & ~(size_t)1023;
+}
+size_t adjoint_g_need(int N, int nb, int nc, int nsplit) {
+    return adjoint_g_offset(nb, nc) + (size_t)nsplit * nc * N * sizeof(float2);
+}
+}  // namespace
+
+int ternary_adjoint_g_lags(const Plan &p, int nlags) {
+    const int N = p.d.n, nb = p.d.nbins;
+    int nc = nlags;
+    while (nc > 0 && adjoint_g_need(N, nb, nc, 1) > p.ws_alloc) nc = nc > 256 ? (nc - 1) / 256 * 256 : nc / 2;
+    return nc;
+}
+
+cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const float2 **G, int *nsplit,
+                                     int64_t *split_stride, cudaStream_t s, int *launches) {
+    const int N = p.d.n, nb = p.d.nbins;
+    const int kblocks = (nb + 15) / 16;
+    if (nc < 1 || adjoint_g_need(N, nb, nc, 1) > p.ws_alloc) return cudaErrorNotSupported;
+    Problem P{};
+    P.N = N;
+    P.p0 = p.d.p0;
+    P.nbins = nb;
+    P.ncols = nc;
+    P.kblocks = kblocks;
+    P.mtiles = (2 * N + 255) / 256;
+    P.ntiles = (nc + TN - 1) / TN;
+    const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+    // split the bins only while tiles are scarce (>= 16 K blocks per unit) and the splits fit
+    int ns = tiles >= p.sm_count
+                 ? 1
+                 : (int)std::max<int64_t>(1, std::min<int64_t>(kblocks / 16, (2LL * p.sm_count + tiles - 1) / tiles));
+    ns = std::min(ns, kMaxSplit);
+    while (ns > 1 && adjoint_g_need(N, nb, nc, ns) > p.ws_alloc) --ns;
+    P.nsplit = ns;
+    P.b_row0 = 0;
+    P.ld = 2LL * N;
+    P.split_stride = (int64_t)nc * 2 * N;
+    P.out_off = 0;
+    const int64_t total = (int64_t)nc * kblocks * 16;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p.sm_count * 16);
+    k_pack_adjoint<<<blocks, 256, 0, s>>>(static_cast<const float2 *>(dA), nb, nc, kblocks,
+                                          static_cast<uint2 *>(p.ws));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    float *g = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + adjoint_g_offset(nb, nc));
+    alignas(64) CUtensorMap omap;
+    const bool tma_out = (N % 2 == 0) && p.tune_drain == 0 && make_out_map(g, N, nc, ns, &omap) == cudaSuccess;
+    if ((e = launch_gemm<2, 1, false, 2>(p, P, nullptr, nullptr, tiles * ns, g, tma_out ? &omap : nullptr, s)) !=
+        cudaSuccess)
+        return e;
+    *launches += 1;
+    *G = reinterpret_cast<const float2 *>(g);
+    *nsplit = ns;
+    *split_stride = (int64_t)nc * N;  // complex elements
+    return cudaSuccess;
 }
 
 // Batched CPIs: per-CPI angle tables, packed-B regions and a work list of

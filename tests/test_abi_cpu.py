@@ -29,7 +29,7 @@ def header_functions():
 def test_header_lists_the_boundary():
     names = header_functions()
     for must in ("ndft_plan", "ndft_exec", "nfft_exec", "caf_exec", "caf_exec_batched", "caf_backward",
-                 "ndft_plan_destroy", "ndft_status_string", "ndft_query_error"):
+                 "caf_backward_inputs", "ndft_plan_destroy", "ndft_status_string", "ndft_query_error"):
         assert must in names
     assert sorted(L.EXPORTS) == names
 
@@ -61,6 +61,10 @@ def test_argument_errors_without_gpu(lib):
     assert lib.caf_exec(None, None, None, 0, 1, None, None) == L.E_INVALID
     assert lib.caf_exec_batched(None, None, None, None, None) == L.E_INVALID
     assert lib.caf_backward(None, None, None, 0, 1, None, None, None) == L.E_INVALID
+    # no output at all, or no plan
+    assert lib.caf_backward_inputs(None, None, None, 0, 1, None, None, None, None) == L.E_INVALID
+    buf = ctypes.create_string_buffer(64)
+    assert lib.caf_backward_inputs(None, None, None, 0, 1, None, None, ctypes.addressof(buf), None) == L.E_INVALID
     assert lib.ndft_argmax(None, -1, 4, None, None, None) == L.E_INVALID
     assert lib.ndft_argmax(None, 0, 4, None, None, None) == L.OK  # nothing to do
     assert lib.ndft_set_tuning(None, 0, 1) == L.E_INVALID

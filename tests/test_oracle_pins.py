@@ -613,3 +613,20 @@ def test_adjoints_against_torch_autograd(oracle):
     got_surv = oracle.caf_adjoint(ss, sr, lag0, nlags, p0, nbins, gA)
     np.testing.assert_allclose(got_ref, want_ref, rtol=0, atol=1e-9)
     np.testing.assert_allclose(got_surv, want_surv, rtol=0, atol=1e-9)
+
+
+def test_adjoint_sampled_matches_full(oracle):
+    """The sampled adjoints return the full adjoints' values at the listed indices."""
+    rng = np.random.default_rng(91)
+    N, lag0, nlags, p0, nbins = 57, -4, 9, 5, 11
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    gA = scenes.cn(rng, (nlags, nbins))
+    idx = np.array([0, 3, 17, 56, 40])
+    for flags in (0, 3):
+        full_s = oracle.caf_adjoint(ss, sr, lag0, nlags, p0, nbins, gA, flags=flags)
+        full_r = oracle.caf_adjoint_ref(ss, sr, lag0, nlags, p0, nbins, gA, flags=flags)
+        assert np.array_equal(oracle.caf_adjoint_at(ss, sr, lag0, nlags, p0, nbins, gA, "surv", idx, flags),
+                              full_s[idx])
+        assert np.array_equal(oracle.caf_adjoint_at(ss, sr, lag0, nlags, p0, nbins, gA, "ref", idx, flags),
+                              full_r[idx])
