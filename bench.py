@@ -250,6 +250,40 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
     issued = 2.0 * (2 * sc.N) * 512 * (4 * 512)  # rows x lags x K (bins x hi/lo x re/im), 2 flop per MAC
     out["caf_16384_fwd_bwd"] = {"ms": ms, "cells": 512 * 512, "backward_kernel_ms": bwd_ms,
                                 "backward_issued_tflops": issued / (bwd_ms / 1e3) / 1e12}
+    del plan, ss, sr, dA, ds
+    # both gradients of the headline surface (N = 65536, 1024 lags x 1024 bins) on
+    # the tensor cores: dL/ds_surv alone (fused fold), and dL/ds_surv with dL/ds_ref
+    # (G stored once, then one fold)
+    sc = scenes.radar_scene(N=65536)
+    ss = torch.from_numpy(sc.s_surv).to(dev)
+    sr = torch.from_numpy(sc.s_ref).to(dev)
+    ph = api.Plan(65536, p0=-512, nbins=1024, max_lags=1024, form="ternary", prec="bf16x2", device=dev)
+    dA = torch.randn(1024, 1024, dtype=torch.complex64, device=dev)
+    ds = torch.empty(65536, dtype=torch.complex64, device=dev)
+    ms_s = _time_ms(lambda: ph.caf_backward(ss, sr, 0, 1024, dA, out=ds), 5, flush)
+    ms_b = _time_ms(lambda: ph.caf_backward_inputs(ss, sr, 0, 1024, dA), 5, flush)
+    ph.timer_start(5)
+    for _ in range(5):
+        ph.caf_backward_inputs(ss, sr, 0, 1024, dA)
+    cms, cn = ph.timer_read()
+    c_ms = cms / max(cn, 1)
+    issued = 2.0 * (2 * 65536) * 1024 * (4 * 1024)
+    out["caf_65536_backward"] = {"surv_ms": ms_s, "surv_and_ref_ms": ms_b, "contraction_ms": c_ms,
+                                 "contraction_issued_tflops": issued / (c_ms / 1e3) / 1e12,
+                                 "launches": ph.last_launches()}
+    del ph, ss, sr, dA, ds
+    # the detection study of Sec. 5.2 on the stereo-FM scene (3 environments x 4
+    # noise cases; Eq. 12a on the tensor cores and through the NFFT, Eq. 12b, and
+    # the linear Eq. 11 by torch.fft for context): obstacles detected and the
+    # side-lobe floor in dB per surface
+    from paper_1402_0532_gb300 import detection
+    study = {}
+    for r in detection.fm_study(device=dev):
+        study[f"{r['env']}/{r['noise']}"] = {
+            k: f"{sum(v['detected'])}/{len(v['detected'])} {v['floor_db']:.2f} dB"
+               + (f" masked: {','.join(v['masked'])}" if v["masked"] else "")
+            for k, v in r.items() if k not in ("env", "noise")}
+    out["fm_scene_detection"] = study
     return out
 
 

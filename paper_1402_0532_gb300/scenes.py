@@ -136,3 +136,105 @@ def differentiation_mask(scene: Scene, half: int = 16) -> np.ndarray:
     b0 = scene.dopplers[0] - scene.p0 - half
     m[max(l0, 0):l0 + 2 * half, max(b0, 0):b0 + 2 * half] = True
     return m
+
+
+# ---------------------------------------------------------------------------
+# The paper's own scene (Sec. 5): a stereo-FM illuminator, Eq. 11-12, echoes
+# of targets and clutter placed by a bistatic geometry (Eq. 13-16, Table 3),
+# additive white Gaussian or epsilon-contaminated Gaussian noise, s_ref noise
+# free.  Quantities the paper leaves open are fixed here and listed with the
+# scene: the distribution of the channel data x1, x2 (i.i.d. uniform on
+# [-1, 1] per sample), the modulation index k_f (0.5), the CPI length
+# (65536 samples), integer-sample delays (the bistatic delay rounded to the
+# nearest sample at fs), the SNR reference (noise power relative to one echo
+# of unit power), and the positions of the obstacles beyond Table 3.
+# ---------------------------------------------------------------------------
+FS_HZ = 200e3        # sampling frequency (Sec. 5)
+PILOT_HZ = 19e3      # stereo pilot f_p (Eq. 11)
+C_KM_S = 299792.458  # propagation speed
+TX_KM = (0.0, 10.0)  # Table 3
+RX_KM = (0.0, 0.0)
+
+# (x km, y km, Doppler Hz); clutter has Doppler 0.  "2t1c" is Table 3; the other
+# two environments of Tables 1-2 have no published geometry and are chosen here.
+FM_ENVIRONMENTS = {
+    "2t1c": [(10.0, 0.0, 200.0), (20.0, 0.0, 157.0), (28.0, 33.0, 0.0)],
+    "4t2c": [(10.0, 0.0, 200.0), (20.0, 0.0, 157.0), (6.0, -18.0, -120.0), (5.0, 12.0, 80.0),
+             (28.0, 33.0, 0.0), (-12.0, 20.0, 0.0)],
+    "1t3c": [(10.0, 0.0, 200.0), (28.0, 33.0, 0.0), (-12.0, 20.0, 0.0), (-20.0, -5.0, 0.0)],
+}
+
+# noise cases of Tables 1-2: AWGN at an SNR in dB, or epsilon-contaminated
+# Gaussian (eps, sigma1, sigma2)
+FM_NOISES = {"awgn3": ("awgn", 3.0), "awgn6": ("awgn", 6.0),
+             "eps0.9": ("eps", (0.9, 0.25, 10.0)), "eps0.8": ("eps", (0.8, 0.5, 20.0))}
+
+
+def fm_stereo_message(x1: np.ndarray, x2: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """Eq. 11: sum / difference channels, the difference on the 2 f_p subcarrier,
+    plus the 3 f_p and f_p tones."""
+    fp = PILOT_HZ
+    return (0.9 * (x1 + x2) + 0.5 * (x1 - x2) * np.cos(2 * np.pi * 2 * fp * t)
+            + 0.25 * np.cos(2 * np.pi * 3 * fp * t) + 0.1 * np.cos(2 * np.pi * fp * t))
+
+
+def fm_stereo(rng: np.random.Generator, n: int, kf: float = 0.5, t0: int = 0) -> np.ndarray:
+    """Eq. 12: s = cos(2 pi k_f m) + j sin(2 pi k_f m) at fs, samples t0 .. t0 + n - 1
+    (complex128, unit modulus).  x1, x2 i.i.d. uniform on [-1, 1]."""
+    t = (t0 + np.arange(n)) / FS_HZ
+    x1 = rng.uniform(-1.0, 1.0, n)
+    x2 = rng.uniform(-1.0, 1.0, n)
+    return np.exp(1j * 2 * np.pi * kf * fm_stereo_message(x1, x2, t))
+
+
+def bistatic_delay_samples(x_km: float, y_km: float) -> float:
+    """Excess path |Tx P| + |P Rx| - |Tx Rx| over the propagation speed, in samples at fs."""
+    d = lambda a, b: float(np.hypot(a[0] - b[0], a[1] - b[1]))
+    p = (x_km, y_km)
+    return (d(TX_KM, p) + d(p, RX_KM) - d(TX_KM, RX_KM)) / C_KM_S * FS_HZ
+
+
+def eps_contaminated(rng: np.random.Generator, n: int, eps: float, s1: float, s2: float) -> np.ndarray:
+    """Real samples of the mixture eps N(0, s1^2) + (1 - eps) N(0, s2^2): each sample
+    is nominal with probability eps and an outlier otherwise."""
+    nominal = rng.random(n) < eps
+    return np.where(nominal, rng.normal(0.0, s1, n), rng.normal(0.0, s2, n))
+
+
+@dataclass
+class FMScene:
+    s_surv: np.ndarray  # complex64 [N], the input gain applied
+    s_ref: np.ndarray   # complex64 [N], noise free
+    N: int
+    obstacles: list     # (delay samples, Doppler Hz, Doppler bin p = f N / fs, "target" | "clutter")
+    gain: float
+    kf: float
+    noise: str
+
+
+def fm_scene(env: str = "2t1c", noise: str = "eps0.9", N: int = 65536, kf: float = 0.5, gain: float = 64.0,
+             seed: int = 9) -> FMScene:
+    """Eq. 16: s_surv = sum_m K s_ref(t - tau_m) exp(j 2 pi f_m t) + noise, K = 1, scaled by
+    `gain` (the x64 input level of Sec. 5.2); s_ref = s(t) of Eq. 12 without noise.  The
+    illuminator is drawn for the 64 samples before the CPI as well, so that every echo
+    has a full record."""
+    rng = np.random.default_rng(seed)
+    pre = 64
+    s = fm_stereo(rng, N + pre, kf, t0=-pre)
+    s_ref = s[pre:]
+    t = np.arange(N) / FS_HZ
+    s_surv = np.zeros(N, np.complex128)
+    obstacles = []
+    for x, y, fd in FM_ENVIRONMENTS[env]:
+        d = int(round(bistatic_delay_samples(x, y)))
+        assert 0 <= d < pre
+        s_surv += s[pre - d: pre - d + N] * np.exp(2j * np.pi * fd * t)
+        obstacles.append((d, fd, fd * N / FS_HZ, "clutter" if fd == 0.0 else "target"))
+    kind, par = FM_NOISES[noise]
+    if kind == "awgn":
+        pw = 10.0 ** (-par / 10.0)
+        s_surv += np.sqrt(pw) * cn(rng, (N,))
+    else:
+        s_surv += eps_contaminated(rng, N, *par) + 1j * eps_contaminated(rng, N, *par)
+    return FMScene((gain * s_surv).astype(np.complex64), s_ref.astype(np.complex64), N, obstacles, gain, kf,
+                   noise)
