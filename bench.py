@@ -57,6 +57,8 @@ def parse():
                     help="time the tensor-core steps only (no direct form, e2e, error or CPU legs)")
     ap.add_argument("--no-others", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile/split settings (no autotuner)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="tensor-core tile (tuning key 1: 256, 128, 129, 258 = 2-SM pair); implies --no-tune")
     ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
@@ -477,6 +479,9 @@ def main():
     A = torch.empty(NLAGS, NBINS, dtype=torch.complex64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     cells = NLAGS * NBINS
+    if args.tile:
+        args.no_tune = True
+        plan.set_tuning(1, args.tile)
     tuned = {} if args.no_tune else autotune.tune_caf(plan, ss, sr, 0, NLAGS, out=A)
 
     def step():

@@ -22,7 +22,7 @@ _lock = threading.Lock()
 
 SPLIT, ROWS, CHUNK, DRAIN = 0, 1, 2, 3
 
-TERNARY_SPACE = {ROWS: [256, 128], CHUNK: [64, 32], SPLIT: [0, 8, 16, 19, 24, 32]}
+TERNARY_SPACE = {ROWS: [256, 128, 258], CHUNK: [64, 32], SPLIT: [0, 8, 16, 19, 24, 32]}
 DIRECT_SPACE = {SPLIT: [0, 2, 4, 6, 8, 12, 16]}
 # batched tensor-core plans: one persistent contraction over all CPIs, no split;
 # the knobs are the chain length and the fold-out path

@@ -272,40 +272,66 @@ __device__ __forceinline__ Work decode(int64_t u, const Problem &single, const P
 
 // ---- A generation: one (bin, sample) pair -> rows 2 pl and 2 pl + 1 ------------
 // u = 4 m, m = (p i) mod N; theta = 2 pi m / N = q pi/2 + a with q = floor(u / N),
-// a = (pi/2) r / N, r = u - q N.  cos a, sin a from the two-level table.
-// The 8 K entries of the Re row go to re[], those of the Im row to im[]; the
-// caller stores them after all of its pairs are computed, so the table loads of
-// every pair are in flight together.
-__device__ __forceinline__ void gen_pair(uint32_t u, uint32_t N, const float2 *__restrict__ thi,
-                                         const float2 *__restrict__ tlo, uint4 &re, uint4 &im) {
+// a = (pi/2) r / N, r = u - q N.  cos a, sin a from the two-level table (explicit
+// shared loads: the aligned dynamic shared-memory base is reached through
+// integer arithmetic, so plain pointer loads would take the generic path).
+// The producers compute all of their pairs of a K block before storing any.
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// The twiddle W = cos(theta) - j sin(theta) at u = 4 ((p i) mod N) from the
+// two-level table (full plane; exact 0 / +-1 on the axes).  Used to seed the
+// rotation below and for the rotation step itself.
+__device__ __forceinline__ float2 tw_table(uint32_t u, uint32_t N, uint32_t thi, uint32_t tlo) {
     const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
     const uint32_t r = u - q * N;
-    const float2 h = thi[r >> 8];
-    const float2 l = tlo[r & (R_LO - 1)];
-    const float c = fmaf(h.x, l.x, -(h.y * l.y));  // cos a >= 0
-    const float s = fmaf(h.y, l.x, h.x * l.y);     // sin a >= 0, 0 only for r = 0
-    // W = cos(theta) - j sin(theta):
+    const float2 h = lds_f2(thi + (r >> 8) * 8u);
+    const float2 l = lds_f2(tlo + (r & (R_LO - 1)) * 8u);
+    const float c = fmaf(h.x, l.x, -(h.y * l.y));
+    const float s = fmaf(h.y, l.x, h.x * l.y);
     //   q0: ( c, -s)   q1: (-s, -c)   q2: (-c,  s)   q3: ( s,  c)
-    const bool odd = q & 1u;
-    const float mr = odd ? s : c;
-    const float mi = odd ? c : s;
-    const uint32_t neg_r = (q == 1u || q == 2u) ? 0x80008000u : 0u;
-    const uint32_t neg_i = (q <= 1u) ? 0x80008000u : 0u;
-    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(mr, mi);
-    const float hr = __low2float(hi2), hii = __high2float(hi2);
-    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(mr - hr, mi - hii);
+    return q == 0u ? make_float2(c, -s) : q == 1u ? make_float2(-s, -c) : q == 2u ? make_float2(-c, s)
+                                                                            : make_float2(s, c);
+}
+
+// The 8 K entries of one (bin, sample) pair: the Re row's to re[], the Im
+// row's to im[] (layout in the file header), with F taken from a given value
+// of W (the rotated twiddle) and the ternary signs S from the integer quadrant
+// rule on u, so the signs stay exact (0 on the axes) whatever the rounding of W.
+__device__ __forceinline__ void gen_pair_w(uint32_t u, uint32_t N, float2 W, uint4 &re, uint4 &im) {
+    constexpr uint32_t P1 = 0x3F803F80u, M1 = 0xBF80BF80u;
+    const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
+    const bool axis = u == q * N;
+    // Re W = cos: + in quadrants 0, 3, - in 1, 2, 0 at u = N, 3N
+    const uint32_t sr = (axis && (q & 1u)) ? 0u : ((q == 0u || q == 3u) ? P1 : M1);
+    // Im W = -sin: - in quadrants 0, 1, + in 2, 3, 0 at u = 0, 2N
+    const uint32_t si = (axis && !(q & 1u)) ? 0u : (q <= 1u ? M1 : P1);
+    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(W.x, W.y);
+    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(W.x - __low2float(hi2), W.y - __high2float(hi2));
     const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi2);
     const uint32_t ul = *reinterpret_cast<const uint32_t *>(&lo2);
-    const uint32_t wr = __byte_perm(uh, ul, 0x5410) ^ neg_r;  // [F_hi_r, F_lo_r]
-    const uint32_t wi = __byte_perm(uh, ul, 0x7632) ^ neg_i;  // [F_hi_i, F_lo_i]
-    // ternary sign pattern, exact: 0 where the magnitude is exactly 0
-    const uint32_t sr = (mr == 0.f) ? 0u : (0x3F803F80u ^ neg_r);  // [S_r, S_r]
-    const uint32_t si = (mi == 0.f) ? 0u : (0x3F803F80u ^ neg_i);  // [S_i, S_i]
+    const uint32_t wr = __byte_perm(uh, ul, 0x5410);  // [F_hi_r, F_lo_r]
+    const uint32_t wi = __byte_perm(uh, ul, 0x7632);  // [F_hi_i, F_lo_i]
     re = make_uint4(sr, si ^ 0x80008000u, wr, wi ^ 0x80008000u);
     im = make_uint4(si, sr, wi, wr);
 }
 
-// ---- adjoint A generation: sample i, bins p and p + 1 -> rows 2 i and 2 i + 1 --
+// W <- W * R (fp32 complex product)
+__device__ __forceinline__ float2 cmul_f2(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// A producers advance each (bin, sample) twiddle by W^(8p) per K block and
+// re-seed it from the table every kReseed blocks: the table gathers (bank
+// conflicted, the largest share of the shared-memory wavefronts) drop to
+// 1/kReseed, and the rotation's drift stays near 1e-6, below the 2^-17
+// resolution of the bf16 hi + lo split of F.
+constexpr int kReseed = 16;
+
+// ---- adjoint A generation: sample i, bins p and p + 1 -> rows 2 i and 2 i + 1 --// ---- adjoint A generation: sample i, bins p and p + 1 -> rows 2 i and 2 i + 1 --
 // The adjoint contraction G_l[i] = sum_p conj(S[p][i]) dA[l][p] runs with rows =
 // (sample, Re/Im), columns = lags, K = bins x [dA_hi_r, dA_lo_r, dA_hi_i,
 // dA_lo_i].  Per bin the Re row holds [S_r, S_r, S_i, S_i] and the Im row
@@ -534,7 +560,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             gen_bar();
             if (!ok) continue;
             const uint32_t N = (uint32_t)w.P.N;
+            const uint32_t thi = smem_u32(s_thi), tlo = smem_u32(s_tlo);
             uint32_t uu[PPT], dd[PPT];
+            float2 wv[PPT], rot[PPT];
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
                 const int k = w.mt * (T::kRows / 2) + pg + 32 * j;  // bin index
@@ -543,14 +571,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t i0 = (int64_t)w.kb0 * 8 + t;
                 uu[j] = 4u * (uint32_t)((pm * (i0 % (int64_t)N)) % (int64_t)N);
                 dd[j] = 4u * (uint32_t)((8 * pm) % (int64_t)N);
+                rot[j] = tw_table(dd[j], N, thi, tlo);  // W^(8p)
             }
             for (int kb = w.kb0; kb < w.kb1; ++kb) {
                 if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                 const uint32_t a_st = a_base + stage * T::kABytes;
+                const bool seed = ((kb - w.kb0) % kReseed) == 0;
                 uint4 vre[PPT], vim[PPT];
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    gen_pair(uu[j], N, s_thi, s_tlo, vre[j], vim[j]);
+                    if (seed) wv[j] = tw_table(uu[j], N, thi, tlo);
+                    gen_pair_w(uu[j], N, wv[j], vre[j], vim[j]);
+                    wv[j] = cmul_f2(wv[j], rot[j]);
                     uu[j] += dd[j];
                     if (uu[j] >= 4u * N) uu[j] -= 4u * N;
                 }
@@ -793,6 +825,340 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// ---- the 2-SM tile (tcgen05 cta_group::2) ---------------------------------------------
+// A CTA pair computes one 256 x 256 tile with M = 256 MMAs issued by the even
+// CTA: each CTA generates its own 128 rows of A and loads its own 128 columns
+// of B into the same shared-memory offsets, and each CTA's tensor memory holds
+// its 128 rows of the accumulator.  A stage is then 32 KiB per CTA (half of
+// the 256-row tile's 64 KiB), so six stages fit, and the 256 accumulator
+// columns per chain leave room for two accumulators used in turn: the fold-out
+// of one chain overlaps the MMAs of the next.
+//   full[s]       (even CTA) 1 arrival with 32 KiB expected (its TMA thread),
+//                 16 KiB from each CTA's TMA, and 8 producer warps of each CTA
+//   empty[s]      (both) one MMA commit, multicast to the pair
+//   tmem_full[b]  (both) one MMA commit, multicast to the pair
+//   tmem_empty[b] (even CTA) the 4 epilogue warps of each CTA
+// Arrivals on the even CTA's barriers from the odd CTA are remote
+// (shared::cluster addresses from mapa).
+namespace pair2 {
+constexpr int kStages = 6;
+constexpr int kABytes = 128 * 128;  // 128 rows x 64 K bf16
+constexpr int kBBytes = 128 * 128;  // 128 columns x 64 K bf16
+constexpr size_t kSmemA = 0;
+constexpr size_t kSmemB = kSmemA + (size_t)kStages * kABytes;
+constexpr size_t kSmemTab = kSmemB + (size_t)kStages * kBBytes;
+constexpr size_t kSmemStage = (kSmemTab + (size_t)(kMaxThi + R_LO) * sizeof(float2) + 127) / 128 * 128;
+constexpr size_t kSmemBar = kSmemStage + 4 * 4096;
+constexpr size_t kSmemTotal = kSmemBar + 256 + 1024;
+static_assert(kSmemTotal <= 232448, "shared memory of one CTA");
+// kind::f16, D fp32, A/B bf16, both K-major, N = 256, M = 256 (the pair)
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(256 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+// arrival on the even CTA's barrier with the default (release, CTA-scope)
+// semantics; a cluster-scope release here costs a fence per arrival (it made the
+// whole pipeline about 2x slower)
+__device__ __forceinline__ void arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// TMA load of this CTA's B half, completion signalled on the even CTA's barrier
+__device__ __forceinline__ void tma_load_b_pair(uint32_t dst, const CUtensorMap *map, int32_t row, uint32_t bar_cl) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar_cl)
+        : "memory");
+}
+__device__ __forceinline__ void umma2(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void commit2_mc(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)0x3)
+        : "memory");
+}
+}  // namespace pair2
+
+// `tmap` has a 128-row box (one CTA's B half).  Forward single-surface
+// contraction only (the batched and adjoint modes keep the one-CTA tile).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_ternary_gemm_pair(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap,
+                        int out_tma, Problem single, int64_t nunits, int chunk, int starve, float *__restrict__ out_base,
+                        int32_t *err) {
+    using namespace pair2;
+    const uint32_t rank = cluster_rank();
+    const bool lead = rank == 0;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float2 *s_thi = reinterpret_cast<float2 *>(smem + kSmemTab);
+    float2 *s_tlo = s_thi + kMaxThi;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSmemBar);
+    uint64_t *empty = full + kStages;
+    uint64_t *tmem_full = empty + kStages;  // [2]
+    uint64_t *tmem_empty = tmem_full + 2;   // [2]
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tmem_empty + 2);
+    volatile int32_t *s_abort = reinterpret_cast<volatile int32_t *>(s_tmem + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t a_base = smem_u32(smem + kSmemA), b_base = smem_u32(smem + kSmemB);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1 + 2 * kGenWarps);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tmem_full[b], 1);
+            mbar_init(&tmem_empty[b], 8);
+        }
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    }
+    if (warp == 1) {
+        // one warp of each CTA of the pair allocates, collectively
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // both CTAs' barriers are initialised before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp == 0) {
+        // ---------------- TMA producer (each CTA its B half) ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
+                const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                    if (starve) continue;
+                    if (lead) mbar_arrive_tx(&full[stage], 2 * kBBytes);
+                    const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN + rank * (TN / 2);
+                    tma_load_b_pair(b_base + stage * kBBytes, &tmap, (int32_t)row,
+                                    peer_addr(smem_u32(&full[stage]), 0u));
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (even CTA) ----------------
+        if (lead && lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, chain = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
+                const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+                for (int c0 = w.kb0; c0 < w.kb1 && ok; c0 += chunk, ++chain) {
+                    const int c1 = min(c0 + chunk, w.kb1);
+                    const uint32_t buf = chain & 1u, tpar = (chain >> 1) & 1u;
+                    if (!(ok = mbar_wait(&tmem_empty[buf], tpar ^ 1u, s_abort, err))) break;
+                    tc_fence_after();
+                    const uint32_t d0 = tmem + buf * (uint32_t)TN;
+                    for (int kb = c0; kb < c1; ++kb) {
+                        if (!(ok = mbar_wait(&full[stage], phase, s_abort, err))) break;
+                        tc_fence_after();
+                        const uint32_t a_st = a_base + stage * kABytes, b_st = b_base + stage * kBBytes;
+#pragma unroll
+                        for (int k = 0; k < KB / 16; ++k)
+                            umma2(d0, umma_desc(a_st + k * 32), umma_desc(b_st + k * 32), (kb > c0 || k > 0) ? 1u : 0u);
+                        commit2_mc(&empty[stage]);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    commit2_mc(&tmem_full[buf]);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp < kEpiWarp0) {
+        // ---------------- A producers: this CTA's 64 bins (128 rows) ----------------
+        const int g = threadIdx.x - 64;  // 0..255
+        const int t = g & 7, pg = g >> 3;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x / 2; u < nunits; u += gridDim.x / 2) {
+            const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+            gen_bar();
+            for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
+                const float2 v = w.P.ang[e];
+                if (e < w.P.nth) s_thi[e] = v;
+                else s_tlo[e - w.P.nth] = v;
+            }
+            gen_bar();
+            if (!ok) continue;
+            const uint32_t N = (uint32_t)w.P.N;
+            const uint32_t thi = smem_u32(s_thi), tlo = smem_u32(s_tlo);
+            uint32_t uu[2], dd[2];
+            float2 wv[2], rot[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = w.mt * 128 + (int)rank * 64 + pg + 32 * j;  // bin index
+                int64_t pm = ((int64_t)w.P.p0 + k) % (int64_t)N;
+                if (pm < 0) pm += N;
+                const int64_t i0 = (int64_t)w.kb0 * 8 + t;
+                uu[j] = 4u * (uint32_t)((pm * (i0 % (int64_t)N)) % (int64_t)N);
+                dd[j] = 4u * (uint32_t)((8 * pm) % (int64_t)N);
+                rot[j] = tw_table(dd[j], N, thi, tlo);
+            }
+            for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                const uint32_t a_st = a_base + stage * kABytes;
+                const bool seed = ((kb - w.kb0) % kReseed) == 0;
+                uint4 vre[2], vim[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (seed) wv[j] = tw_table(uu[j], N, thi, tlo);
+                    gen_pair_w(uu[j], N, wv[j], vre[j], vim[j]);
+                    wv[j] = cmul_f2(wv[j], rot[j]);
+                    uu[j] += dd[j];
+                    if (uu[j] >= 4u * N) uu[j] -= 4u * N;
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) store_pair(a_st, pg + 32 * j, t, vre[j], vim[j]);
+                // the even CTA's MMA reads this CTA's tile through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    if (lead) mbar_arrive(&full[stage]);
+                    else arrive_remote(peer_addr(smem_u32(&full[stage]), 0u));
+                }
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: this CTA's 128 rows ----------------
+        const int quarter = warp & 3;
+        uint32_t chain = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
+            const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+            const int64_t limit_m = 2LL * w.P.nbins;
+            for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
+                const uint32_t buf = chain & 1u, tpar = (chain >> 1) & 1u;
+                if (!(ok = mbar_wait(&tmem_full[buf], tpar, s_abort, err))) break;
+                tc_fence_after();
+                const bool first = (c0 == w.kb0);
+                const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+                const int mrow = w.mt * 256 + (int)rank * 128 + 32 * quarter;
+                auto release = [&]() {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (lead) mbar_arrive(&tmem_empty[buf]);
+                        else arrive_remote(peer_addr(smem_u32(&tmem_empty[buf]), 0u));
+                    }
+                };
+                if (out_tma) {
+                    // as the one-CTA epilogue: 16-column groups through two 2 KB staging
+                    // buffers to bulk tensor stores (first chain) or adds (later chains),
+                    // every address receiving its chain sums in order
+                    const uint32_t wst = smem_u32(smem + kSmemStage) + (uint32_t)quarter * 4096u;
+                    constexpr int NG = TN / 16;
+                    auto drain = [&](const uint32_t (&r)[16], int g) {
+                        const uint32_t sb = wst + (uint32_t)(g & 1) * 2048u;
+                        if (lane == 0) {
+                            if (g == 0) bulk_wait_all();
+                            else bulk_wait_read1();
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(sb + (uint32_t)(j * 32 + lane) * 4u), "r"(r[j])
+                                         : "memory");
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) {
+                            const int col = w.nt * TN + g * 16;
+                            if (first) tma_store_out(&omap, sb, mrow, col, w.split);
+                            else tma_reduce_out(&omap, sb, mrow, col, w.split);
+                            bulk_commit();
+                        }
+                    };
+                    uint32_t ra[16], rb[16];
+                    const uint32_t tc0 = trow + buf * (uint32_t)TN;
+                    tmem_ld16(tc0, ra);
+                    tmem_wait_ld();
+#pragma unroll 1
+                    for (int g = 0; g < NG; g += 2) {
+                        tmem_ld16(tc0 + (uint32_t)(g + 1) * 16u, rb);
+                        drain(ra, g);
+                        tmem_wait_ld();
+                        const bool more = g + 2 < NG;
+                        if (more) tmem_ld16(tc0 + (uint32_t)(g + 2) * 16u, ra);
+                        else release();
+                        drain(rb, g + 1);
+                        if (more) tmem_wait_ld();
+                    }
+                    continue;
+                }
+                const int64_t m = (int64_t)mrow + lane;
+#pragma unroll 1
+                for (int cc = 0; cc < TN; cc += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(trow + buf * (uint32_t)TN + (uint32_t)cc, r);
+                    tmem_wait_ld();
+                    const int64_t col0 = (int64_t)w.nt * TN + cc;
+                    if (m < limit_m) {
+                        float *dst = out_base + w.out_off + col0 * w.P.ld + m;
+                        const int64_t left = w.P.ncols - col0;
+                        const int nj = left < 32 ? (int)left : 32;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < nj) {
+                                if (first) dst[j * w.P.ld] = __uint_as_float(r[j]);
+                                else red_add_f32(dst + j * w.P.ld, __uint_as_float(r[j]));
+                            }
+                    }
+                }
+                release();
+            }
+        }
+        if (out_tma && lane == 0) bulk_wait_all();
+    }
+
+    __syncthreads();
+    if (*s_abort) {
+        const long long t0 = clock64();
+        while (clock64() - t0 < 200000) {
+        }
+    }
+    // neither CTA leaves while the pair's MMAs may still use its shared or tensor memory
+    cluster_sync();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
@@ -1089,11 +1455,44 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
     return e;
 }
 
-// Tile shape: 256 rows in one CTA (one accumulator pair, the default), or
+// The 2-SM pair tile: one unit per pair, 2 x min(units, SMs / 2) CTAs in clusters of 2.
+cudaError_t launch_gemm_pair(const Plan &p, const Problem &single, int64_t nunits, float *out_base,
+                             const CUtensorMap *omap, cudaStream_t s) {
+    constexpr size_t smem = pair2::kSmemTotal;
+    cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host2);  // 128-row box
+    const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    const CUtensorMap &om = omap ? *omap : none;
+    const int out_tma = omap ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(nunits, p.sm_count / 2)));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    timer_begin(p, s);
+    e = cudaLaunchKernelEx(&cfg, k_ternary_gemm_pair, *map, om, out_tma, single, nunits, chunk, p.test_starve,
+                           out_base, p.err);
+    timer_end(p, s);
+    return e;
+}
+
+// Tile shape: 256 rows in one CTA (one accumulator pair, the default), or// Tile shape: 256 rows in one CTA (one accumulator pair, the default), or
 // 128 rows per CTA in 2-CTA clusters sharing B by multicast (two
 // accumulators used in turn), or 128 rows without the cluster.
+// 258: the 256 x 256 tile on a 2-SM pair (cta_group::2).
 int tile_halves(const Plan &p) { return (p.tune_cols == 128 || p.tune_cols == 129) ? 1 : 2; }
 int tile_cluster(const Plan &p) { return p.tune_cols == 129 ? 2 : 1; }
+bool tile_pair(const Plan &p) { return p.tune_cols == 258; }
 
 struct TernLayout {
     int kblocks;
@@ -1180,14 +1579,16 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     P.nbins = nb;
     P.ncols = ncols;
     P.kblocks = L.kblocks;
-    const int MH = tile_halves(p), CL = tile_cluster(p);
+    const bool pair = tile_pair(p);
+    const int MH = tile_halves(p), CL = pair ? 2 : tile_cluster(p);
     const int rows = 128 * MH;
     P.mtiles = (2 * nb + rows - 1) / rows;
     P.ntiles = (ncols + TN - 1) / TN;
-    // scheduled units per split and the slots that run them (a 2-CTA pair per unit in the cluster variant)
-    const int64_t tiles = (CL == 2 ? (P.mtiles + 1) / 2 : P.mtiles) * (int64_t)P.ntiles;
+    // scheduled units per split and the slots that run them (a 2-CTA pair per unit in
+    // the cluster variant and the pair tile)
+    const int64_t tiles = (CL == 2 && !pair ? (P.mtiles + 1) / 2 : P.mtiles) * (int64_t)P.ntiles;
     const int slots = CL == 2 ? p.sm_count / 2 : p.sm_count;
-    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * CL * TN * sizeof(float)));
+    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * (pair ? 1 : CL) * TN * sizeof(float)));
     P.nsplit = choose_split(tiles, L.kblocks, slots, p.tune_split, cap_units);
     P.b_row0 = 0;
     P.ld = 2LL * nb;
@@ -1203,7 +1604,8 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     const bool tma_out = (nb % 2 == 0) && p.tune_drain == 0 &&
                          make_out_map(out_base, nb, ncols, P.nsplit, &omap) == cudaSuccess;
     const CUtensorMap *om = tma_out ? &omap : nullptr;
-    if (MH == 2) e = launch_gemm<2, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
+    if (pair) e = launch_gemm_pair(p, P, nunits, out_base, om, s);
+    else if (MH == 2) e = launch_gemm<2, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     else if (CL == 2) e = launch_gemm<1, 2>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     else e = launch_gemm<1, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     if (e != cudaSuccess) return e;
