@@ -30,6 +30,7 @@ __device__ __forceinline__ uint32_t nzmask_f(float v) { return (__float_as_uint(
 
 // ---- precision traits ---------------------------------------------------------
 struct PrecF32 {
+    static constexpr bool kTwoLevel = true;  // see direct_tile
     using In = float2;
     using Tw = float2;
     using V = float2;
@@ -59,6 +60,7 @@ struct PrecF32 {
 };
 
 struct PrecQ14 {
+    static constexpr bool kTwoLevel = false;  // integer sums are exact (modulo 2^32)
     using In = short2;
     using Tw = short2;
     using V = int2;
@@ -133,10 +135,23 @@ struct Smem {
     // [KC][BP + 2] magnitudes and [KC][BP + 1] sign/zero words, twiddles then data.
     static constexpr int kMagStride = BP + 2;
     static constexpr int kSgnStride = BP + 1;
-    static constexpr size_t bytes(size_t mag_size) {
+    __host__ __device__ static constexpr size_t bytes(size_t mag_size) {
         return 2 * (KC * kMagStride * mag_size + KC * kSgnStride * sizeof(uint4));
     }
+    // fp32: each thread's 16 outer accumulators [cell][thread] after the staging
+    static constexpr size_t kOuter = 16 * kThreads * sizeof(float2);
+    template <class P>
+    static constexpr size_t bytes_for() {
+        return bytes(sizeof(typename P::Mag)) + (P::kTwoLevel ? kOuter : 0);
+    }
 };
+
+// fp32 sums run in two levels: the register accumulators take kFlushChunks
+// chunks (1024 samples) and are then added into per-thread outer sums in
+// shared memory, so no single fp32 running sum takes more than
+// max(1024, N / 1024) terms (a single level over 2^20 incoherent terms
+// exceeded 1e-5 of max|X|).
+constexpr int kFlushChunks = 64;
 
 // One 64 x 64 tile over samples [n_begin, n_end).  out points at the tile's
 // [col][bin] destination with row stride ldo.
@@ -174,6 +189,13 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = P::acc0();
+    // outer sums: only this thread touches its 16 entries, so no barrier is needed
+    float2 *outer = reinterpret_cast<float2 *>(smem + Smem::bytes(sizeof(Mag)));
+    if constexpr (P::kTwoLevel) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) outer[c * kThreads + tid] = make_float2(0.f, 0.f);
+    }
+    int chunk_count = 0;
 
     for (int64_t n0 = n_begin; n0 < n_end; n0 += KC) {
 #pragma unroll
@@ -220,6 +242,28 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
                 for (int j = 0; j < 4; ++j) P::mac(acc[i][j], wm[i], ws[i], vm[j], vs[j]);
         }
         __syncthreads();
+        if constexpr (P::kTwoLevel) {
+            if (++chunk_count == kFlushChunks) {
+                chunk_count = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float2 &o = outer[(i * 4 + j) * kThreads + tid];
+                        o = make_float2(__fadd_rn(o.x, acc[i][j].x), __fadd_rn(o.y, acc[i][j].y));
+                        acc[i][j] = P::acc0();
+                    }
+            }
+        }
+    }
+    if constexpr (P::kTwoLevel) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 o = outer[(i * 4 + j) * kThreads + tid];
+                acc[i][j] = make_float2(__fadd_rn(o.x, acc[i][j].x), __fadd_rn(o.y, acc[i][j].y));
+            }
     }
 
 #pragma unroll
@@ -317,7 +361,7 @@ cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t ba
     if (grid.y > 65535) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (p.d.prec == NDFT_PREC_FP32) {
-        const size_t sm = Smem::bytes(sizeof(float2));
+        const size_t sm = Smem::bytes_for<PrecF32>();
         auto k = k_direct<PrecF32, NdftSrc<PrecF32>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         timer_begin(p, s);
@@ -326,7 +370,7 @@ cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t ba
                                      static_cast<float2 *>(X));
         timer_end(p, s);
     } else {
-        const size_t sm = Smem::bytes(sizeof(int2));
+        const size_t sm = Smem::bytes_for<PrecQ14>();
         auto k = k_direct<PrecQ14, NdftSrc<PrecQ14>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         timer_begin(p, s);
@@ -350,7 +394,7 @@ cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_r
     cudaError_t e;
     const bool direct_out = (ns == 1);
     if (p.d.prec == NDFT_PREC_FP32) {
-        const size_t sm = Smem::bytes(sizeof(float2));
+        const size_t sm = Smem::bytes_for<PrecF32>();
         auto k = k_direct<PrecF32, CafSrc<PrecF32>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         float2 *dst = direct_out ? static_cast<float2 *>(A) : static_cast<float2 *>(p.ws);
@@ -367,7 +411,7 @@ cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_r
                                         static_cast<float *>(A), s);
         }
     } else {
-        const size_t sm = Smem::bytes(sizeof(int2));
+        const size_t sm = Smem::bytes_for<PrecQ14>();
         auto k = k_direct<PrecQ14, CafSrc<PrecQ14>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         uint2 *dst = direct_out ? static_cast<uint2 *>(A) : static_cast<uint2 *>(p.ws);
@@ -393,7 +437,7 @@ cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *r
     if (e != cudaSuccess) return e;
     const int grid = p.sm_count * 2;
     if (p.d.prec == NDFT_PREC_FP32) {
-        const size_t sm = Smem::bytes(sizeof(float2));
+        const size_t sm = Smem::bytes_for<PrecF32>();
         auto k = k_direct_batched<PrecF32>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         timer_begin(p, s);
@@ -403,7 +447,7 @@ cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *r
                                      static_cast<float2 *>(out), p.d.flags);
         timer_end(p, s);
     } else {
-        const size_t sm = Smem::bytes(sizeof(int2));
+        const size_t sm = Smem::bytes_for<PrecQ14>();
         auto k = k_direct_batched<PrecQ14>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         timer_begin(p, s);

@@ -180,10 +180,10 @@ ndft_status ndft_plan_destroy(ndft_plan_t plan) {
 ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream) {
     const Range range("ndft_exec");
     if (!plan || plan->p.batched || batch < 0 || batch > plan->p.d.max_batch) return NDFT_E_INVALID;
-    if (batch == 0) return NDFT_OK;
-    if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
+    if (batch == 0) return NDFT_OK;
+    if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
     cudaError_t e;
     if (p.d.form == NDFT_FORM_DIRECT) {
         if (batch > 65535LL * 64) return NDFT_E_UNSUPPORTED;
@@ -206,9 +206,9 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
         p.d.p0 % p.d.n != 0)
         return NDFT_E_INVALID;
     if ((p.d.flags & NDFT_F_NFFT_DIF) && p.d.n > 65536) return NDFT_E_UNSUPPORTED;
+    p.last_launches = 0;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
-    p.last_launches = 0;
     return from_cuda(launch_nfft(p, x, X, batch, stream, &p.last_launches));
 }
 
