@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile/split settings (no autotuner)")
     ap.add_argument("--tile", type=int, default=0,
                     help="tensor-core tile (tuning key 1: 256, 128, 129, 258 = 2-SM pair); implies --no-tune")
-    ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft"],
+    ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft", "adjoint"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
 
@@ -77,6 +77,17 @@ def profile_other(args, api, scenes, dev):
         step = lambda: plan.caf(ss, sr, 0, NLAGS, out=out)  # noqa: E731
         units = NLAGS * NBINS
         what = f"direct-form CAF, N={N}, {NLAGS} lags x {NBINS} bins"
+    elif args.profile_form == "adjoint":
+        # both gradients of the workload's surface on the tensor cores (the
+        # G-storing adjoint contraction and the fold)
+        scene = scenes.radar_scene(N=N)
+        ss = torch.from_numpy(scene.s_surv).to(dev)
+        sr = torch.from_numpy(scene.s_ref).to(dev)
+        plan = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="ternary", prec="bf16x2", device=dev)
+        dA = torch.randn(NLAGS, NBINS, dtype=torch.complex64, device=dev)
+        step = lambda: plan.caf_backward_inputs(ss, sr, 0, NLAGS, dA)  # noqa: E731
+        units = NLAGS * NBINS
+        what = f"both CAF gradients, tensor cores, N={N}, {NLAGS} lags x {NBINS} bins"
     else:
         x = torch.from_numpy(scenes.cn_batch()).to(dev)
         plan = api.Plan(1024, max_batch=x.shape[0], device=dev)

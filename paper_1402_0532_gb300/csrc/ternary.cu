@@ -297,18 +297,26 @@ __device__ __forceinline__ float2 tw_table(uint32_t u, uint32_t N, uint32_t thi,
                                                                             : make_float2(s, c);
 }
 
+// sigma(W) at u = 4 ((p i) mod N) in [0, 4N) as bf16 pairs, exact: Re W = cos
+// is < 0 for N < u < 3N and 0 at u = N, 3N; Im W = -sin is < 0 for 0 < u < 2N
+// and 0 at u = 0, 2N (the integer quadrant rule written as range tests).
+__device__ __forceinline__ void sign_bits(uint32_t u, uint32_t N, uint32_t &sr2, uint32_t &si2) {
+    constexpr uint32_t P1 = 0x3F803F80u, NEG = 0x80008000u;
+    const bool neg_r = (u - (N + 1u)) < (2u * N - 1u);  // unsigned: false for u <= N
+    const bool nz_r = (u != N) && (u != 3u * N);
+    const bool neg_i = u < 2u * N;
+    const bool nz_i = (u != 0u) && (u != 2u * N);
+    sr2 = nz_r ? (P1 | (neg_r ? NEG : 0u)) : 0u;
+    si2 = nz_i ? (P1 | (neg_i ? NEG : 0u)) : 0u;
+}
+
 // The 8 K entries of one (bin, sample) pair: the Re row's to re[], the Im
 // row's to im[] (layout in the file header), with F taken from a given value
 // of W (the rotated twiddle) and the ternary signs S from the integer quadrant
 // rule on u, so the signs stay exact (0 on the axes) whatever the rounding of W.
 __device__ __forceinline__ void gen_pair_w(uint32_t u, uint32_t N, float2 W, uint4 &re, uint4 &im) {
-    constexpr uint32_t P1 = 0x3F803F80u, M1 = 0xBF80BF80u;
-    const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
-    const bool axis = u == q * N;
-    // Re W = cos: + in quadrants 0, 3, - in 1, 2, 0 at u = N, 3N
-    const uint32_t sr = (axis && (q & 1u)) ? 0u : ((q == 0u || q == 3u) ? P1 : M1);
-    // Im W = -sin: - in quadrants 0, 1, + in 2, 3, 0 at u = 0, 2N
-    const uint32_t si = (axis && !(q & 1u)) ? 0u : (q <= 1u ? M1 : P1);
+    uint32_t sr, si;  // [S_r, S_r], [S_i, S_i]
+    sign_bits(u, N, sr, si);
     const __nv_bfloat162 hi2 = __floats2bfloat162_rn(W.x, W.y);
     const __nv_bfloat162 lo2 = __floats2bfloat162_rn(W.x - __low2float(hi2), W.y - __high2float(hi2));
     const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi2);
@@ -339,13 +347,7 @@ constexpr int kReseed = 16;
 // S = sigma(W^(p i)) read off u = 4 ((p i) mod N) by the integer quadrant rule
 // (exact zeros on the axes), as bf16 pairs.
 __device__ __forceinline__ void adj_signs(uint32_t u, uint32_t N, uint32_t &sr2, uint32_t &si2) {
-    const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
-    const bool axis = u == q * N;
-    constexpr uint32_t P1 = 0x3F803F80u, M1 = 0xBF80BF80u;
-    // cos: + in quadrants 0 and 3, - in 1 and 2, 0 at u = N, 3N
-    sr2 = (q == 0u) ? P1 : (q == 2u) ? M1 : axis ? 0u : (q == 1u ? M1 : P1);
-    // -sin: 0 at u = 0, 2N; - in quadrants 0 and 1, + in 2 and 3
-    si2 = (q == 1u) ? M1 : (q == 3u) ? P1 : axis ? 0u : (q == 0u ? M1 : P1);
+    sign_bits(u, N, sr2, si2);
 }
 
 // Rows 2 pl (Re) and 2 pl + 1 (Im), 16-byte chunk t of the 128-byte row, in the
