@@ -174,6 +174,54 @@ class Plan:
         torch.cuda.current_stream(self.device).synchronize()
         return out_host
 
+    def caf_from_host_many(self, inputs, lag0: int, nlags: int, outs, staging: dict | None = None):
+        """caf_from_host over a sequence of (s_surv_host, s_ref_host) pairs into the host
+        surfaces `outs` (one per pair, or one buffer reused), pipelined: two device buffer
+        sets, the inputs of step k copied in on one stream while step k - 1 computes on
+        the current stream, and the surface of step k - 1 copied out on a third while
+        step k computes.  Every step still copies its inputs in and its surface out.
+        Synchronises before returning."""
+        st = {} if staging is None else staging
+        dev = self.device
+        comp = torch.cuda.current_stream(dev)
+        if "h2d" not in st:
+            st["h2d"], st["d2h"] = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        inputs = list(inputs)
+        if not inputs:
+            return outs
+        hs0, hr0 = inputs[0]
+        if "pipe" not in st:
+            st["pipe"] = [dict(ss=torch.empty_like(hs0, device=dev), sr=torch.empty_like(hr0, device=dev),
+                               A=torch.empty((nlags,) + self._row_shape(self.nbins), dtype=self._out_dtype,
+                                             device=dev)) for _ in range(2)]
+        bufs = st["pipe"]
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        e_in, e_comp, e_out = [ev(), ev()], [None, None], [None, None]
+        single_out = not isinstance(outs, (list, tuple))
+        for k, (hs, hr) in enumerate(inputs):
+            b = k % 2
+            buf = bufs[b]
+            with torch.cuda.stream(st["h2d"]):
+                if e_comp[b] is not None:
+                    st["h2d"].wait_event(e_comp[b])  # step k - 2 is done reading this buffer
+                buf["ss"].copy_(hs, non_blocking=True)
+                buf["sr"].copy_(hr, non_blocking=True)
+                e_in[b].record(st["h2d"])
+            comp.wait_event(e_in[b])
+            if e_out[b] is not None:
+                comp.wait_event(e_out[b])  # the surface of step k - 2 has been copied out
+            self.caf(buf["ss"], buf["sr"], lag0, nlags, out=buf["A"])
+            e_comp[b] = ev()
+            e_comp[b].record(comp)
+            with torch.cuda.stream(st["d2h"]):
+                st["d2h"].wait_event(e_comp[b])
+                (outs if single_out else outs[k]).copy_(buf["A"], non_blocking=True)
+                e_out[b] = ev()
+                e_out[b].record(st["d2h"])
+        st["d2h"].synchronize()
+        comp.synchronize()
+        return outs
+
     def caf_backward(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int, dA: torch.Tensor,
                      out: torch.Tensor | None = None) -> torch.Tensor:
         """dL/ds_surv (dRe + j dIm) given dA = dL/dRe A + j dL/dIm A ([nlags, nbins] complex64)."""
