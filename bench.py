@@ -285,6 +285,40 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
                                  "contraction_issued_tflops": issued / (c_ms / 1e3) / 1e12,
                                  "launches": ph.last_launches()}
     del ph, ss, sr, dA, ds
+    # a stream of surfaces: two plans on two streams, so the lag-product packing of
+    # one surface runs under the contraction of the previous one (back to back, no
+    # L2 flush; the per-step figure of the headline keeps one surface per step)
+    sc = scenes.radar_scene(N=65536)
+    ss = torch.from_numpy(sc.s_surv).to(dev)
+    sr = torch.from_numpy(sc.s_ref).to(dev)
+    pl = [api.Plan(65536, p0=-512, nbins=1024, max_lags=1024, form="ternary", prec="bf16x2", device=dev)
+          for _ in range(2)]
+    outs = [torch.empty(1024, 1024, dtype=torch.complex64, device=dev) for _ in range(2)]
+    strm = [torch.cuda.Stream(dev) for _ in range(2)]
+
+    def stream_run(k_surfaces):
+        cur = torch.cuda.current_stream(dev)
+        for st_ in strm:
+            st_.wait_stream(cur)
+        for k in range(k_surfaces):
+            with torch.cuda.stream(strm[k % 2]):
+                pl[k % 2].caf(ss, sr, 0, 1024, out=outs[k % 2])
+                api.argmax(outs[k % 2])
+        for st_ in strm:
+            cur.wait_stream(st_)
+    stream_run(4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stream_run(100)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 100
+    for q in pl:
+        q.query_error()
+    out["caf_surface_stream_2_streams"] = {"ms_per_surface": ms, "cells_per_s": 1024 * 1024 / (ms / 1e3),
+                                           "surfaces": 100, "l2": "not flushed"}
+    del pl, outs, strm, ss, sr
     # the detection study of Sec. 5.2 on the stereo-FM scene (3 environments x 4
     # noise cases; Eq. 12a on the tensor cores and through the NFFT, Eq. 12b, and
     # the linear Eq. 11 by torch.fft for context): obstacles detected and the
