@@ -29,6 +29,8 @@
 
 #include "internal.cuh"
 
+#include <type_traits>
+
 namespace ndft {
 namespace {
 
@@ -407,6 +409,45 @@ __global__ void __launch_bounds__(256) k_fft_edge(Src src, Dst dst, const float2
     for (int j = 0; j < P; ++j) dst(o, u + (j << LA), r[j]);
 }
 
+// DIT tail when at most 2^LA bins are wanted (bins p0 .. p0 + nbins - 1 mod N):
+// every position u then feeds exactly one wanted bin, u + m 2^LA, so a thread
+// per wanted bin loads the 2^RB values of its u and runs only the butterflies
+// that feed output m (2^RB - 1 of RB 2^(RB-1)): stages hb .. RB-1 mix index
+// bits hb .. RB-1, so at stage hb those are the pairs whose bits below hb equal
+// m's, and they all take the one twiddle of index m mod 2^hb.  The same
+// butterflies on the same values as k_fft_edge, so the same bits.
+template <class Op, int L, int RB>
+__global__ void __launch_bounds__(256)
+    k_fft_edge_bins(SrcVec src, DstBins dst, const float2 *__restrict__ tw, int64_t nvec) {
+    constexpr int LA = L - RB, NA = 1 << LA, P = 1 << RB;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t o = gid / dst.nbins;
+    const int t = (int)(gid - o * dst.nbins);
+    if (o >= nvec) return;
+    const int pbin = (dst.p0 + t) & dst.mask;  // the bin, mod N
+    const int u = pbin & (NA - 1), m = pbin >> LA;
+    float2 r[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = src(o, u + (j << LA));
+#pragma unroll
+    for (int hb = 0; hb < RB; ++hb) {
+        const int b = LA + hb;
+        const int low = m & ((1 << hb) - 1);
+        const float4 w = Op::prep(__ldg(&tw[(u | (low << LA)) << (L - 1 - b)]));
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (j & (1 << hb)) continue;
+            if ((j & ((1 << hb) - 1)) != low) continue;  // does not feed output m
+            bfly<Op, false>(r[j], r[j | (1 << hb)], w);
+        }
+    }
+    float2 v = r[0];
+#pragma unroll
+    for (int j = 1; j < P; ++j)
+        if (j == m) v = r[j];
+    dst.A[o * dst.nbins + t] = v;
+}
+
 template <class Op, bool DIF, int L, int RB, class Src, class Dst>
 cudaError_t run_two_pass(const Plan &p, Src src, Dst dst, int64_t nvec, cudaStream_t s, int *launches) {
     constexpr int LA = L - RB;
@@ -427,8 +468,18 @@ cudaError_t run_two_pass(const Plan &p, Src src, Dst dst, int64_t nvec, cudaStre
             e = launch_reg<Op, false, LA, RB>(src.shift(a0), DstVec{Y, (int64_t)1 << LA}, p.tw32, n << RB,
                                               p.sm_count, s);
             if (e != cudaSuccess) return e;
-            k_fft_edge<Op, false, L, RB><<<(unsigned)(threads / 256), 256, 0, s>>>(
-                SrcVec{Y, (int64_t)1 << L}, dst.shift(a0), p.tw32, n);
+            bool pruned = false;
+            if constexpr (std::is_same_v<Dst, DstBins>) {
+                if (dst.nbins <= (1 << LA)) {
+                    const int64_t bt = n * dst.nbins;
+                    k_fft_edge_bins<Op, L, RB><<<(unsigned)((bt + 255) / 256), 256, 0, s>>>(
+                        SrcVec{Y, (int64_t)1 << L}, dst.shift(a0), p.tw32, n);
+                    pruned = true;
+                }
+            }
+            if (!pruned)
+                k_fft_edge<Op, false, L, RB><<<(unsigned)(threads / 256), 256, 0, s>>>(
+                    SrcVec{Y, (int64_t)1 << L}, dst.shift(a0), p.tw32, n);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         *launches += 2;
