@@ -9,10 +9,15 @@
 // 16.  Per chunk it stages, in shared memory, the 16 x 64 twiddles of its bins
 // (gathered from the plan's fp32 table at (p n) mod N, the index advanced
 // incrementally) and the 16 x 64 data values, both already split into the
-// pieces (x) needs: magnitude, sign word and nonzero mask.  Each thread then
-// accumulates a 4 x 4 register tile; one real (x) is an add of magnitudes, a
-// three-way XOR of the sign words and an AND with the two nonzero masks
-// (Eq. 1-2 with the zero case explicit), one complex (x) four of those (Eq. 6).
+// pieces (x) needs.  Each thread then accumulates a 4 x 4 register tile.
+// fp32: magnitude and sign as a float in {-1, 0, +1}; one real (x) accumulated
+// is an add of magnitudes, a product of the two signs and one fma into the
+// accumulator -- acc + (|a| + |b|) sgn(a) sgn(b), where the product by the
+// sign product is exact, so it rounds exactly as acc + (a (x) b) (Eq. 1-2,
+// the zero case explicit as a zero sign).  All three run on the fp32 pipe.
+// Q1.14: magnitude, sign mask and nonzero mask; one real (x) is an integer add
+// of magnitudes with the sign applied by XOR and the zero case by AND.  One
+// complex (x) is four real ones (Eq. 6).
 #include "internal.cuh"
 
 #include <algorithm>
@@ -26,7 +31,6 @@ constexpr int BC = 64;   // columns per block
 constexpr int KC = 16;   // samples per chunk
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ uint32_t nzmask_f(float v) { return (__float_as_uint(v) << 1) ? 0xffffffffu : 0u; }
 
 // ---- precision traits ---------------------------------------------------------
 struct PrecF32 {
@@ -35,25 +39,26 @@ struct PrecF32 {
     using Tw = float2;
     using V = float2;
     using Mag = float2;
+    using Sgn = float2;  // sgn(v.x), sgn(v.y) in {-1, 0, +1}
     using Acc = float2;
     __device__ static V load(const In *p, int64_t i) { return p[i]; }
     __device__ static V zero() { return make_float2(0.f, 0.f); }
     __device__ static V conj_(V v) { return make_float2(v.x, -v.y); }
     __device__ static V cox(V a, V b) { return cox_f32(a, b); }
-    __device__ static void ready(V v, Mag &m, uint4 &s) {
+    __device__ static float sgn1(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+    __device__ static void ready(V v, Mag &m, Sgn &s) {
         m = make_float2(fabsf(v.x), fabsf(v.y));
-        s = make_uint4(__float_as_uint(v.x) & kSignBit, __float_as_uint(v.y) & kSignBit, nzmask_f(v.x),
-                       nzmask_f(v.y));
+        s = make_float2(sgn1(v.x), sgn1(v.y));
     }
     __device__ static Acc acc0() { return make_float2(0.f, 0.f); }
-    // acc += w (x) v, Eq. 6: re += w_r(x)v_r - w_i(x)v_i, im += w_i(x)v_r + v_i(x)w_r
-    __device__ static void mac(Acc &acc, const Mag &wm, const uint4 &ws, const Mag &vm, const uint4 &vs) {
-        const float t1 = ox_ready(wm.x, ws.x, ws.z, vm.x, vs.x, vs.z);
-        const float t2 = ox_ready(wm.y, ws.y, ws.w, vm.y, vs.y, vs.w);
-        const float t3 = ox_ready(wm.y, ws.y, ws.w, vm.x, vs.x, vs.z);
-        const float t4 = ox_ready(vm.y, vs.y, vs.w, wm.x, ws.x, ws.z);
-        acc.x = __fsub_rn(__fadd_rn(acc.x, t1), t2);
-        acc.y = __fadd_rn(__fadd_rn(acc.y, t3), t4);
+    // acc += w (x) v, Eq. 6: re += w_r(x)v_r - w_i(x)v_i, im += w_i(x)v_r + v_i(x)w_r,
+    // each a (x) b as fma(|a| + |b|, sgn a sgn b, acc): the product is exact, so
+    // the result equals fl(acc + a (x) b) with a (x) b rounded once (Eq. 1)
+    __device__ static void mac(Acc &acc, const Mag &wm, const Sgn &ws, const Mag &vm, const Sgn &vs) {
+        acc.x = __fmaf_rn(__fadd_rn(wm.x, vm.x), __fmul_rn(ws.x, vs.x), acc.x);
+        acc.x = __fmaf_rn(__fadd_rn(wm.y, vm.y), -__fmul_rn(ws.y, vs.y), acc.x);
+        acc.y = __fmaf_rn(__fadd_rn(wm.y, vm.x), __fmul_rn(ws.y, vs.x), acc.y);
+        acc.y = __fmaf_rn(__fadd_rn(vm.y, wm.x), __fmul_rn(vs.y, ws.x), acc.y);
     }
     __device__ static float2 out(const Acc &a) { return a; }
     using Out = float2;
@@ -65,6 +70,7 @@ struct PrecQ14 {
     using Tw = short2;
     using V = int2;
     using Mag = int2;
+    using Sgn = uint4;  // sign masks, nonzero masks
     using Acc = uint2;  // two's complement wrap
     __device__ static V load(const In *p, int64_t i) {
         const short2 v = p[i];
@@ -73,7 +79,7 @@ struct PrecQ14 {
     __device__ static V zero() { return make_int2(0, 0); }
     __device__ static V conj_(V v) { return make_int2(v.x, -v.y); }
     __device__ static V cox(V a, V b) { return cox_i32(a, b); }
-    __device__ static void ready(V v, Mag &m, uint4 &s) {
+    __device__ static void ready(V v, Mag &m, Sgn &s) {
         m = make_int2(abs(v.x), abs(v.y));
         s = make_uint4(v.x < 0 ? 0xffffffffu : 0u, v.y < 0 ? 0xffffffffu : 0u, v.x ? 0xffffffffu : 0u,
                        v.y ? 0xffffffffu : 0u);
@@ -84,7 +90,7 @@ struct PrecQ14 {
         const uint32_t sx = as ^ bs;
         return ((m ^ sx) - sx) & az & bz;
     }
-    __device__ static void mac(Acc &acc, const Mag &wm, const uint4 &ws, const Mag &vm, const uint4 &vs) {
+    __device__ static void mac(Acc &acc, const Mag &wm, const Sgn &ws, const Mag &vm, const Sgn &vs) {
         const uint32_t t1 = ox(wm.x, ws.x, ws.z, vm.x, vs.x, vs.z);
         const uint32_t t2 = ox(wm.y, ws.y, ws.w, vm.y, vs.y, vs.w);
         const uint32_t t3 = ox(wm.y, ws.y, ws.w, vm.x, vs.x, vs.z);
@@ -135,14 +141,14 @@ struct Smem {
     // [KC][BP + 2] magnitudes and [KC][BP + 1] sign/zero words, twiddles then data.
     static constexpr int kMagStride = BP + 2;
     static constexpr int kSgnStride = BP + 1;
-    __host__ __device__ static constexpr size_t bytes(size_t mag_size) {
-        return 2 * (KC * kMagStride * mag_size + KC * kSgnStride * sizeof(uint4));
+    __host__ __device__ static constexpr size_t bytes(size_t mag_size, size_t sgn_size) {
+        return 2 * (KC * kMagStride * mag_size + KC * kSgnStride * sgn_size);
     }
     // fp32: each thread's 16 outer accumulators [cell][thread] after the staging
     static constexpr size_t kOuter = 16 * kThreads * sizeof(float2);
     template <class P>
     static constexpr size_t bytes_for() {
-        return bytes(sizeof(typename P::Mag)) + (P::kTwoLevel ? kOuter : 0);
+        return bytes(sizeof(typename P::Mag), sizeof(typename P::Sgn)) + (P::kTwoLevel ? kOuter : 0);
     }
 };
 
@@ -162,9 +168,10 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
                                             int64_t ldo) {
     using Mag = typename P::Mag;
     Mag *tM = reinterpret_cast<Mag *>(smem);
-    uint4 *tS = reinterpret_cast<uint4 *>(tM + KC * Smem::kMagStride);
+    using Sgn = typename P::Sgn;
+    Sgn *tS = reinterpret_cast<Sgn *>(tM + KC * Smem::kMagStride);
     Mag *vM = reinterpret_cast<Mag *>(tS + KC * Smem::kSgnStride);
-    uint4 *vS = reinterpret_cast<uint4 *>(vM + KC * Smem::kMagStride);
+    Sgn *vS = reinterpret_cast<Sgn *>(vM + KC * Smem::kMagStride);
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -190,7 +197,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = P::acc0();
     // outer sums: only this thread touches its 16 entries, so no barrier is needed
-    float2 *outer = reinterpret_cast<float2 *>(smem + Smem::bytes(sizeof(Mag)));
+    float2 *outer = reinterpret_cast<float2 *>(smem + Smem::bytes(sizeof(Mag), sizeof(Sgn)));
     if constexpr (P::kTwoLevel) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) outer[c * kThreads + tid] = make_float2(0.f, 0.f);
@@ -204,7 +211,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
             const bool ok = bin_ok && (n0 + kk < n_end);
             typename P::V w = ok ? load_tw<P>(tw, m[j]) : P::zero();
             Mag mg;
-            uint4 sg;
+            Sgn sg;
             P::ready(w, mg, sg);
             tM[kk * Smem::kMagStride + sb] = mg;
             tS[kk * Smem::kSgnStride + sb] = sg;
@@ -217,7 +224,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
             const int64_t n = n0 + dk;
             typename P::V v = (n < n_end && col0 + c < ncols) ? src(col0 + c, n) : P::zero();
             Mag mg;
-            uint4 sg;
+            Sgn sg;
             P::ready(v, mg, sg);
             vM[dk * Smem::kMagStride + c] = mg;
             vS[dk * Smem::kSgnStride + c] = sg;
@@ -226,7 +233,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
 #pragma unroll 2
         for (int kk = 0; kk < KC; ++kk) {
             Mag wm[4], vm[4];
-            uint4 ws[4], vs[4];
+            Sgn ws[4], vs[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 // bins ty*4 + i: two distinct per warp (broadcast); columns tx + 16 i:
