@@ -136,6 +136,16 @@ __device__ __forceinline__ float sgnf(float v) {
     return __fsub_rn(g, l);
 }
 
+// sgn(v) in two instructions: 1.0f where v != 0 (set.ne), with v's sign bit
+// copied in; a zero v gives a zero of v's sign.  cox_ready only multiplies it
+// by a twiddle magnitude and adds v back, and its outer fma's +0 addend turns
+// every zero into +0, so the result has the same bits as with sgnf.
+__device__ __forceinline__ float sgn_mul(float v) {
+    float nz;
+    asm("set.ne.f32.f32 %0, %1, 0f00000000;" : "=f"(nz) : "f"(v));
+    return __uint_as_float(__float_as_uint(nz) | (__float_as_uint(v) & 0x80000000u));
+}
+
 // Eq. 6 with the twiddle in "ready" form (|Re|, |Im|, sgn Re, sgn Im).  Each
 // real a (x) b = sgn(a) sgn(b) (|a| + |b|) is formed as
 // fma(sgn a, fma(sgn b, |a|, b), +0): the inner fma rounds sgn(b)(|a| + |b|)
@@ -143,7 +153,7 @@ __device__ __forceinline__ float sgnf(float v) {
 // sgn a, and the +0 addend turns every zero product into +0, as the
 // definition's 0 for a zero operand.  Same bits as cox_f32.
 __device__ __forceinline__ float2 cox_ready(float4 w, float2 o) {
-    const float sx = sgnf(o.x), sy = sgnf(o.y);
+    const float sx = sgn_mul(o.x), sy = sgn_mul(o.y);
     const float t1 = __fmaf_rn(w.z, __fmaf_rn(sx, w.x, o.x), 0.f);  // Wr (x) Or
     const float t2 = __fmaf_rn(w.w, __fmaf_rn(sy, w.y, o.y), 0.f);  // Wi (x) Oi
     const float t3 = __fmaf_rn(w.w, __fmaf_rn(sx, w.y, o.x), 0.f);  // Wi (x) Or
