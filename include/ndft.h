@@ -15,6 +15,9 @@
  *    pairs (value = q / 2^14) in, interleaved int32 pairs out.
  *  - Arrays are dense and row-major as stated per call; base pointers must be
  *    16-byte aligned, otherwise NDFT_E_INVALID.
+ *  - Outputs must not overlap inputs or each other, except where a call says
+ *    so (nfft_exec may run in place); calls reject outputs that start at an
+ *    input's or another output's address with NDFT_E_INVALID.
  *  - Argument errors are returned synchronously and launch nothing.  CUDA
  *    launch errors are returned as NDFT_E_CUDA.  Errors detected inside a
  *    kernel (a bounded wait that ran out, an internal check) are recorded in

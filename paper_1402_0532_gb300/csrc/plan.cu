@@ -183,7 +183,7 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
     Plan &p = plan->p;
     p.last_launches = 0;
     if (batch == 0) return NDFT_OK;
-    if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
+    if (!aligned16(x) || !aligned16(X) || x == X) return NDFT_E_INVALID;
     cudaError_t e;
     if (p.d.form == NDFT_FORM_DIRECT) {
         if (batch > 65535LL * 64) return NDFT_E_UNSUPPORTED;
@@ -217,6 +217,7 @@ ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, in
     const Range range("caf_exec");
     if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(A)) return NDFT_E_INVALID;
+    if (A == s_surv || A == s_ref) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
     cudaError_t e;
@@ -239,6 +240,7 @@ ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref
     Plan &p = plan->p;
     if (p.d.prec == NDFT_PREC_Q14 || fft_form(p.d.form)) return NDFT_E_UNSUPPORTED;
     if (!aligned16(s_ref) || !aligned16(dA) || !aligned16(ds)) return NDFT_E_INVALID;
+    if (ds == s_ref || ds == dA) return NDFT_E_INVALID;
     p.last_launches = 0;
     if (p.d.form == NDFT_FORM_TERNARY_GEMM) {
         // the transposed ternary contraction on the tensor cores (CUDA cores if it does not fit)
@@ -259,6 +261,9 @@ ndft_status caf_backward_inputs(ndft_plan_t plan, const void *s_surv, const void
     if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(dA) || !aligned16(ds_ref) ||
         (ds_surv && !aligned16(ds_surv)))
         return NDFT_E_INVALID;
+    if (ds_ref == s_surv || ds_ref == s_ref || ds_ref == dA || ds_surv == ds_ref || ds_surv == s_surv ||
+        ds_surv == s_ref || ds_surv == dA)
+        return NDFT_E_INVALID;  // the fold reads both inputs while it writes the gradients
     p.last_launches = 0;
     const cudaError_t e =
         launch_caf_backward_inputs(p, s_surv, s_ref, lag0, nlags, dA, ds_surv, ds_ref, stream, &p.last_launches);
@@ -505,6 +510,7 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
     const Range range("caf_exec_batched");
     if (!plan || !plan->p.batched) return NDFT_E_INVALID;
     if (!aligned16(surv_base) || !aligned16(ref_base) || !aligned16(out_base)) return NDFT_E_INVALID;
+    if (out_base == surv_base || out_base == ref_base) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
     if (p.d.form == NDFT_FORM_TERNARY_GEMM)

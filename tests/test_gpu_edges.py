@@ -1,6 +1,8 @@
 """Edge cases of the CUDA path against the oracle: the largest transform each
 form accepts, an empty batch, a lag window entirely outside the samples
 (exact zeros), a single lag, and the adjoints at the same degenerate inputs."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -121,3 +123,24 @@ def test_n1_both_forms(api):
         got = p.ndft(dev(x)).cpu().numpy()
         p.query_error()
         assert relerr(got, oracle.ndft(x)) < TOL
+
+
+def test_outputs_aliasing_inputs_are_rejected(api):
+    """Outputs that start at an input's address are argument errors: nothing launches."""
+    from paper_1402_0532_gb300 import _lib as L
+    N = 256
+    lib = L.load()
+    p = api.Plan(N, p0=-4, nbins=8, max_lags=4, max_batch=4, form="ternary", prec="bf16x2")
+    x = torch.zeros(4 * N, dtype=torch.complex64, device="cuda")
+    y = torch.zeros(4 * N, dtype=torch.complex64, device="cuda")
+    dA = torch.zeros(4 * 8, dtype=torch.complex64, device="cuda")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.ndft_exec(p.handle, ptr(x), ptr(x), 4, s) == L.E_INVALID
+    assert lib.caf_exec(p.handle, ptr(x), ptr(y), 0, 4, ptr(x), s) == L.E_INVALID
+    assert lib.caf_exec(p.handle, ptr(x), ptr(y), 0, 4, ptr(y), s) == L.E_INVALID
+    assert lib.caf_backward(p.handle, ptr(x), ptr(y), 0, 4, ptr(dA), ptr(y), s) == L.E_INVALID
+    assert lib.caf_backward_inputs(p.handle, ptr(x), ptr(y), 0, 4, ptr(dA), ptr(dA), ptr(x), s) == L.E_INVALID
+    out = torch.zeros(4 * N, dtype=torch.complex64, device="cuda")
+    assert lib.caf_backward_inputs(p.handle, ptr(x), ptr(y), 0, 4, ptr(dA), ptr(out), ptr(out), s) == L.E_INVALID
+    p.query_error()
