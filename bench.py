@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-others", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile/split settings (no autotuner)")
     ap.add_argument("--tile", type=int, default=0,
-                    help="tensor-core tile (tuning key 1: 256, 128, 129, 258 = 2-SM pair); implies --no-tune")
+                    help="tensor-core tile (tuning key 1: 256, 128, 258 = 2-SM pair); implies --no-tune")
     ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft", "adjoint"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()

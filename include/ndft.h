@@ -240,10 +240,9 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
 /* Tile / split choice for the plan's kernels: key 0 = split count along the
  * sample axis (0 = automatic); key 1 = ternary-GEMM tile (256: 256 rows in one
  * CTA with one tensor-memory accumulator pair, the default; 128: 128 rows with
- * two accumulators used in turn; 129: the 128-row tile in 2-CTA clusters that
- * share each operand tile by TMA multicast; 258: the 256-row tile on a 2-SM
- * pair, M = 256 MMAs with each CTA holding half of A and of B and two
- * tensor-memory accumulators used in turn); key 2 = ternary-GEMM K blocks
+ * two accumulators used in turn; 258: the 256-row tile on a 2-SM pair, M = 256
+ * MMAs with each CTA holding half of A and of B and two tensor-memory
+ * accumulators used in turn); key 2 = ternary-GEMM K blocks
  * (8 samples each) per tensor-memory accumulation chain before it is folded
  * into the fp32 result (0 = 64); key 3 = ternary-GEMM fold path (0: bulk
  * tensor stores/adds, 1: per-element adds).  Used by the autotuner; affects

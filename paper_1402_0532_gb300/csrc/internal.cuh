@@ -69,7 +69,7 @@ struct Plan {
     mutable int tcount = 0;
     // ternary GEMM: TMA descriptor storage (host copy + device copy)
     void *tmap_host = nullptr;
-    void *tmap_host2 = nullptr;  // same buffer, 128-row box (2-CTA cluster variant)
+    void *tmap_host2 = nullptr;  // same buffer, 128-row box (one CTA's half of B in the pair tile)
     void *tmap_dev = nullptr;
     size_t b_bytes = 0;          // packed-B region of the workspace
     size_t part_bytes = 0;       // split-K partials region of the workspace

@@ -372,7 +372,7 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
         if (value > 4096) return NDFT_E_INVALID;
         plan->p.tune_split = value;
     } else if (key == 1) {
-        if (value != 0 && value != 128 && value != 129 && value != 256 && value != 258) return NDFT_E_INVALID;
+        if (value != 0 && value != 128 && value != 256 && value != 258) return NDFT_E_INVALID;
         plan->p.tune_cols = value;
     } else if (key == 2) {
         if (value > 1 << 20) return NDFT_E_INVALID;

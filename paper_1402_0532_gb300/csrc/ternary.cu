@@ -143,9 +143,7 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-// 2-CTA cluster helpers: this CTA's rank, a cluster-wide barrier, a TMA load
-// whose data and mbarrier signal go to the same offsets in every CTA of
-// `mask`, and an MMA commit that arrives on the barrier in every CTA of `mask`.
+// 2-CTA cluster helpers (the pair tile): this CTA's rank and a cluster-wide barrier.
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -153,21 +151,6 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 }
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tma_load_b_mc(uint32_t dst, const CUtensorMap *map, int32_t row, uint64_t *bar,
-                                              uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -228,25 +211,11 @@ struct Work {
     int64_t out_off;  // floats from the launch's output base
 };
 
-// Unit u of the launch.  With a 2-CTA cluster (cl = 2) a unit is a pair of
-// neighbouring m-tiles sharing one B tile; CTA `rank` of the pair takes
-// m-tile 2 mp + rank (single problems only).
-__device__ __forceinline__ Work decode(int64_t u, const Problem &single, const Problem *probs, const Unit *units,
-                                       int rank, int cl) {
+// Unit u of the launch: from the work list of a batched plan, or (single
+// problem) split-major with m-tiles fastest.
+__device__ __forceinline__ Work decode(int64_t u, const Problem &single, const Problem *probs, const Unit *units) {
     Work w;
-    if (cl == 2) {
-        w.P = single;
-        const int mp = (single.mtiles + 1) / 2;
-        const int64_t tiles = (int64_t)mp * single.ntiles;
-        const int split = (int)(u / tiles);
-        const int64_t t = u - (int64_t)split * tiles;
-        w.mt = 2 * (int)(t % mp) + rank;
-        w.nt = (int)(t / mp);
-        w.kb0 = (int)((int64_t)split * single.kblocks / single.nsplit);
-        w.kb1 = (int)((int64_t)(split + 1) * single.kblocks / single.nsplit);
-        w.split = split;
-        w.out_off = single.out_off + (int64_t)split * single.split_stride;
-    } else if (units) {
+    if (units) {
         const Unit un = units[u];
         w.P = probs[un.prob];
         w.mt = un.mt;
@@ -378,22 +347,16 @@ struct Tile {
     static constexpr size_t kSmemTotal = kSmemBar + 160 + 1024;  // barriers, flags, alignment slack
 };
 
-// CL = 2 (with MH = 1): a 2-CTA cluster on neighbouring m-tiles; each CTA
-// loads half of the shared 256-column B tile and multicasts it to both, and
-// each stage is refilled only after both CTAs' MMAs released it.  `tmap` then
-// has a 128-row box.
 // ADJ selects the adjoint contractions (rows = samples, columns = lags, K =
 // bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
 // forward epilogue on a [lags][2N] fp32 output).
-template <int MH, int CL, bool BT, int ADJ>
+template <int MH, bool BT, int ADJ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
                    int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
-    static_assert(CL == 1 || (CL == 2 && MH == 1), "the cluster variant uses 128-row tiles");
-    static_assert(ADJ == 0 || (MH == 2 && CL == 1 && !BT), "the adjoint runs on the 256-row tile");
+    static_assert(ADJ == 0 || (MH == 2 && !BT), "the adjoint runs on the 256-row tile");
     using T = Tile<MH>;
-    const int rank = CL == 2 ? (int)cluster_rank() : 0;
     constexpr int STG = T::kStages;
     constexpr int NB = T::kBufs;
     extern __shared__ unsigned char smem_raw[];
@@ -414,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STG; ++s) {
             mbar_init(&full[s], 1 + kGenWarps);
-            mbar_init(&empty[s], CL);  // one MMA commit per CTA of the cluster
+            mbar_init(&empty[s], 1);  // one MMA commit
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(&tmem_full[b], 1);
@@ -432,7 +395,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (CL == 2) cluster_sync();  // the peer's barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
@@ -442,18 +404,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
-                const Work w = decode(u, single, probs, units, rank, CL);
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     if (starve) continue;  // tests: the stage never fills, every wait runs out
                     mbar_arrive_tx(&full[stage], B_BYTES);
                     const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN;
-                    if (CL == 2)
-                        tma_load_b_mc(b_base + stage * B_BYTES + rank * (B_BYTES / 2), &tmap,
-                                      (int32_t)(row + rank * (TN / 2)), &full[stage], (uint16_t)0x3);
-                    else
-                        tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
+                    tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
                     if (++stage == STG) {
                         stage = 0;
                         phase ^= 1u;
@@ -467,8 +425,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0, chain = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
-                const Work w = decode(u, single, probs, units, rank, CL);
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
                 // one accumulation chain per chunk of `chunk` K blocks; the epilogue
                 // folds each chain into the destination in fp32 (round to nearest)
                 for (int c0 = w.kb0; c0 < w.kb1 && ok; c0 += chunk, ++chain) {
@@ -489,8 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             for (int h = 0; h < MH; ++h)
                                 umma(d0 + h * TN, umma_desc(a_st + h * 128 * 128 + k * 32), bd, acc);
                         }
-                        if (CL == 2) umma_commit_mc(&empty[stage], (uint16_t)0x3);
-                        else umma_commit(&empty[stage]);
+                        umma_commit(&empty[stage]);
                         if (++stage == STG) {
                             stage = 0;
                             phase ^= 1u;
@@ -511,8 +468,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t phase = 0;
         bool ok = true;
         if constexpr (ADJ != 0) {
-            for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
-                const Work w = decode(u, single, probs, units, rank, CL);
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
                 const uint32_t N = (uint32_t)w.P.N;
                 uint32_t ua[PPT], ub[PPT], dd[PPT];
 #pragma unroll
@@ -551,8 +508,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         } else
-        for (int64_t u = blockIdx.x / CL; u < nunits; u += gridDim.x / CL) {
-            const Work w = decode(u, single, probs, units, rank, CL);
+        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const Work w = decode(u, single, probs, units);
             gen_bar();  // every producer is done with the previous table
             for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
                 const float2 v = w.P.ang[e];
@@ -615,8 +572,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         float2 *wts = reinterpret_cast<float2 *>(smem + T::kSmemStage + 4096 * quarter);
         uint32_t chain = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
-            const Work w = decode(u, single, probs, units, rank, CL);
+        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const Work w = decode(u, single, probs, units);
             const int N = w.P.N;
             const int i_lo = w.mt * (T::kRows / 2);  // first sample of the tile
             const int col_lo = w.nt * TN;             // first lag column of the tile
@@ -687,8 +644,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quarter = warp & 3;
         uint32_t chain = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x / CL; u < nunits && ok; u += gridDim.x / CL) {
-            const Work w = decode(u, single, probs, units, rank, CL);
+        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const Work w = decode(u, single, probs, units);
             const int64_t limit_m = ADJ == 2 ? 2LL * w.P.N : 2LL * w.P.nbins;  // output rows
             for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
                 const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
@@ -821,9 +778,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         while (clock64() - t0 < 200000) {
         }
     }
-    // neither CTA of a pair leaves while the other may still multicast into its
-    // shared memory or arrive on its barriers
-    if (CL == 2) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
@@ -952,7 +906,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
-                const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+                const Work w = decode(u, single, nullptr, nullptr);
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     if (starve) continue;
@@ -974,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0, chain = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
-                const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+                const Work w = decode(u, single, nullptr, nullptr);
                 for (int c0 = w.kb0; c0 < w.kb1 && ok; c0 += chunk, ++chain) {
                     const int c1 = min(c0 + chunk, w.kb1);
                     const uint32_t buf = chain & 1u, tpar = (chain >> 1) & 1u;
@@ -1008,7 +962,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t phase = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x / 2; u < nunits; u += gridDim.x / 2) {
-            const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+            const Work w = decode(u, single, nullptr, nullptr);
             gen_bar();
             for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
                 const float2 v = w.P.ang[e];
@@ -1065,7 +1019,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t chain = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
-            const Work w = decode(u, single, nullptr, nullptr, 0, 1);
+            const Work w = decode(u, single, nullptr, nullptr);
             const int64_t limit_m = 2LL * w.P.nbins;
             for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
                 const uint32_t buf = chain & 1u, tpar = (chain >> 1) & 1u;
@@ -1418,41 +1372,24 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH, int CL, bool BT = false, int ADJ = 0>
+template <int MH, bool BT = false, int ADJ = 0>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
-    auto kern = k_ternary_gemm<MH, CL, BT, ADJ>;
+    auto kern = k_ternary_gemm<MH, BT, ADJ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const CUtensorMap *map = static_cast<const CUtensorMap *>(CL == 2 ? p.tmap_host2 : p.tmap_host);
+    const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
     const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
     const CUtensorMap &om = omap ? *omap : none;
     const int out_tma = omap ? 1 : 0;
     timer_begin(p, s);
-    if (CL == 1) {
-        const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
-        kern<<<grid, kThreads, smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
-                                          out_base, p.err);
-        e = cudaGetLastError();
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(nunits, p.sm_count / 2)));
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, *map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
-                               out_base, p.err);
-    }
+    const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
+    kern<<<grid, kThreads, smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
+                                      out_base, p.err);
+    e = cudaGetLastError();
     timer_end(p, s);
     return e;
 }
@@ -1488,12 +1425,10 @@ cudaError_t launch_gemm_pair(const Plan &p, const Problem &single, int64_t nunit
     return e;
 }
 
-// Tile shape: 256 rows in one CTA (one accumulator pair, the default), or// Tile shape: 256 rows in one CTA (one accumulator pair, the default), or
-// 128 rows per CTA in 2-CTA clusters sharing B by multicast (two
-// accumulators used in turn), or 128 rows without the cluster.
-// 258: the 256 x 256 tile on a 2-SM pair (cta_group::2).
-int tile_halves(const Plan &p) { return (p.tune_cols == 128 || p.tune_cols == 129) ? 1 : 2; }
-int tile_cluster(const Plan &p) { return p.tune_cols == 129 ? 2 : 1; }
+// Tile shape (tuning key 1): 256 rows in one CTA (one accumulator pair, the
+// default), 128 rows with two accumulators used in turn (128), or the 256 x 256
+// tile on a 2-SM pair (258, cta_group::2).
+int tile_halves(const Plan &p) { return p.tune_cols == 128 ? 1 : 2; }
 bool tile_pair(const Plan &p) { return p.tune_cols == 258; }
 
 struct TernLayout {
@@ -1562,7 +1497,7 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
     if ((e = make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
         cudaSuccess)
         return e;
-    p.tmap_host2 = std::aligned_alloc(64, sizeof(CUtensorMap));  // 128-row box for the 2-CTA variant
+    p.tmap_host2 = std::aligned_alloc(64, sizeof(CUtensorMap));  // 128-row box for the pair tile
     if (!p.tmap_host2) return cudaErrorMemoryAllocation;
     return make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host2), TN / 2);
 }
@@ -1582,15 +1517,15 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     P.ncols = ncols;
     P.kblocks = L.kblocks;
     const bool pair = tile_pair(p);
-    const int MH = tile_halves(p), CL = pair ? 2 : tile_cluster(p);
+    const int MH = tile_halves(p);
     const int rows = 128 * MH;
     P.mtiles = (2 * nb + rows - 1) / rows;
     P.ntiles = (ncols + TN - 1) / TN;
-    // scheduled units per split and the slots that run them (a 2-CTA pair per unit in
-    // the cluster variant and the pair tile)
-    const int64_t tiles = (CL == 2 && !pair ? (P.mtiles + 1) / 2 : P.mtiles) * (int64_t)P.ntiles;
-    const int slots = CL == 2 ? p.sm_count / 2 : p.sm_count;
-    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * (pair ? 1 : CL) * TN * sizeof(float)));
+    // scheduled units per split and the slots that run them (a 2-SM pair per unit
+    // with the pair tile)
+    const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+    const int slots = pair ? p.sm_count / 2 : p.sm_count;
+    const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * TN * sizeof(float)));
     P.nsplit = choose_split(tiles, L.kblocks, slots, p.tune_split, cap_units);
     P.b_row0 = 0;
     P.ld = 2LL * nb;
@@ -1607,9 +1542,8 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
                          make_out_map(out_base, nb, ncols, P.nsplit, &omap) == cudaSuccess;
     const CUtensorMap *om = tma_out ? &omap : nullptr;
     if (pair) e = launch_gemm_pair(p, P, nunits, out_base, om, s);
-    else if (MH == 2) e = launch_gemm<2, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
-    else if (CL == 2) e = launch_gemm<1, 2>(p, P, nullptr, nullptr, nunits, out_base, om, s);
-    else e = launch_gemm<1, 1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
+    else if (MH == 2) e = launch_gemm<2>(p, P, nullptr, nullptr, nunits, out_base, om, s);
+    else e = launch_gemm<1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
     if (P.nsplit > 1) {
@@ -1681,7 +1615,7 @@ cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nla
     if (e != cudaSuccess) return e;
     *launches += 1;
     float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + p.b_bytes);
-    if ((e = launch_gemm<2, 1, false, 1>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
+    if ((e = launch_gemm<2, false, 1>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
         cudaSuccess)
         return e;
     *launches += 2;
@@ -1745,7 +1679,7 @@ cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const floa
     float *g = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + adjoint_g_offset(nb, nc));
     alignas(64) CUtensorMap omap;
     const bool tma_out = (N % 2 == 0) && p.tune_drain == 0 && make_out_map(g, N, nc, ns, &omap) == cudaSuccess;
-    if ((e = launch_gemm<2, 1, false, 2>(p, P, nullptr, nullptr, tiles * ns, g, tma_out ? &omap : nullptr, s)) !=
+    if ((e = launch_gemm<2, false, 2>(p, P, nullptr, nullptr, tiles * ns, g, tma_out ? &omap : nullptr, s)) !=
         cudaSuccess)
         return e;
     *launches += 1;
@@ -1866,7 +1800,7 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
     alignas(64) CUtensorMap omap;
     const bool tma_out = p.bt_rows > 0 && p.tune_drain == 0 && ((uintptr_t)out & 15u) == 0 &&
                          make_out_map(out, p.bt_nbins, (int)p.bt_rows, 1, &omap) == cudaSuccess;
-    if ((e = launch_gemm<2, 1, true>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out),
+    if ((e = launch_gemm<2, true>(p, Problem{}, probs, units, p.nwork, static_cast<float *>(out),
                                tma_out ? &omap : nullptr, s)) != cudaSuccess)
         return e;
     *launches += 1;
