@@ -660,6 +660,7 @@ def main():
                            "parallelism": f"{world} independent surface(s), one per GPU",
                            "tuning": {"ternary": {str(k): v for k, v in tuned.items()},
                                       "direct": {str(k): v for k, v in tuned_direct.items()}}},
+                "otimes_per_s": value * N,  # complex (x) per second: every cell sums N of them
                 "roofline": roofline, "direct": direct, "speedup_vs_direct": value / world / direct["value"],
                 "max_err_vs_fp64": err, "e2e": e2e, "gpu_launches": launches_per_step * K,
                 "clocks": clocks, "cpu_baseline": base, "other_workloads": others}
