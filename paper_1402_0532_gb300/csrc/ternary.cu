@@ -368,7 +368,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *empty = full + STG;
     uint64_t *tmem_full = empty + STG;    // [NB]
     uint64_t *tmem_empty = tmem_full + NB;  // [NB]
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tmem_empty + NB);
+    // MH = 2: the epilogue also signals when it has read row half 0 (TMEM
+    // columns 0 .. 255), so the next chain's half-0 MMAs can start while it
+    // still reads half 1
+    uint64_t *tmem_half0 = tmem_empty + NB;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tmem_half0 + 1);
     volatile int32_t *s_abort = reinterpret_cast<volatile int32_t *>(s_tmem + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -383,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&tmem_full[b], 1);
             mbar_init(&tmem_empty[b], 4);
         }
+        mbar_init(tmem_half0, 4);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
@@ -432,10 +437,51 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int c0 = w.kb0; c0 < w.kb1 && ok; c0 += chunk, ++chain) {
                     const int c1 = min(c0 + chunk, w.kb1);
                     const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
-                    if (!(ok = mbar_wait(&tmem_empty[buf], tpar ^ 1u, s_abort, err))) break;
-                    tc_fence_after();
                     const uint32_t d0 = tmem + buf * (uint32_t)TN;
-                    for (int kb = c0; kb < c1; ++kb) {
+                    int kb = c0;
+                    if constexpr (MH == 2) {
+                        // Half 0 of the accumulator is free first: run its MMAs for the
+                        // stages already loaded while the epilogue still reads half 1 of
+                        // the previous chain, then half 1's for the same stages.  Each
+                        // half still accumulates its K blocks in order.
+                        if (!(ok = mbar_wait(tmem_half0, tpar ^ 1u, s_abort, err))) break;
+                        tc_fence_after();
+                        const int npro = min(STG, c1 - c0);
+                        int st = stage;
+                        uint32_t ph = phase;
+                        for (int q = 0; q < npro; ++q) {
+                            if (!(ok = mbar_wait(&full[st], ph, s_abort, err))) break;
+                            tc_fence_after();
+                            const uint32_t a_st = a_base + st * T::kABytes, b_st = b_base + st * B_BYTES;
+#pragma unroll
+                            for (int k = 0; k < KB / 16; ++k)
+                                umma(d0, umma_desc(a_st + k * 32), umma_desc(b_st + k * 32), (q > 0 || k > 0) ? 1u : 0u);
+                            if (++st == STG) {
+                                st = 0;
+                                ph ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        if (!(ok = mbar_wait(&tmem_empty[buf], tpar ^ 1u, s_abort, err))) break;
+                        tc_fence_after();
+                        for (int q = 0; q < npro; ++q) {
+                            const uint32_t a_st = a_base + stage * T::kABytes, b_st = b_base + stage * B_BYTES;
+#pragma unroll
+                            for (int k = 0; k < KB / 16; ++k)
+                                umma(d0 + TN, umma_desc(a_st + 128 * 128 + k * 32), umma_desc(b_st + k * 32),
+                                     (q > 0 || k > 0) ? 1u : 0u);
+                            umma_commit(&empty[stage]);
+                            if (++stage == STG) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        kb = c0 + npro;
+                    } else {
+                        if (!(ok = mbar_wait(&tmem_empty[buf], tpar ^ 1u, s_abort, err))) break;
+                        tc_fence_after();
+                    }
+                    for (; kb < c1; ++kb) {
                         if (!(ok = mbar_wait(&full[stage], phase, s_abort, err))) break;
                         tc_fence_after();
                         const uint32_t a_st = a_base + stage * T::kABytes, b_st = b_base + stage * B_BYTES;
@@ -625,6 +671,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
+                    if (MH == 2 && h == 0) {  // half 0 read: its next chain may start
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tmem_half0);
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -725,6 +776,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_ld16(trow + tcol(g + 1), rb);
                         drain(ra, g);
                         tmem_wait_ld();
+                        if (MH == 2 && g + 2 == GPH) {  // every load of half 0 has completed
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(tmem_half0);
+                        }
                         const bool more = g + 2 < NG;
                         if (more) {
                             tmem_ld16(trow + tcol(g + 2), ra);
@@ -761,6 +817,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     if (j < nj) red_add_f32(dst + j * w.P.ld, __uint_as_float(r[j]));
                             }
                         }
+                    }
+                    if (MH == 2 && h == 0) {  // half 0 read: its next chain may start
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tmem_half0);
                     }
                 }
                 tc_fence_before();
