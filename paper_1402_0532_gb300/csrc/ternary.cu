@@ -18,11 +18,15 @@
 //               buffer, 128-byte swizzle, one mbarrier per stage;
 //   warp 1      TMEM allocator and single-thread tcgen05.mma issuer;
 //   warps 2-9   A producers: generate the 256 x 64 A tile of each stage in
-//               shared memory from a 2-level cos/sin table (the sign pattern
-//               S comes from integer quadrant arithmetic, so its zeros are
-//               exact), then fence.proxy.async and arrive;
+//               shared memory: F by complex rotation of each twiddle, re-seeded
+//               from a 2-level cos/sin table every 16 K blocks; the sign
+//               pattern S by range tests on the integer twiddle index, so its
+//               zeros are exact; then fence.proxy.async and arrive;
 //   warps 10-13 epilogue: tcgen05.ld the two 128 x 256 fp32 accumulators and
-//               store them (coalesced) to the output or split-K partials.
+//               fold them into the output or split-K partials by bulk tensor
+//               stores / adds, releasing row half 0 as soon as it is read.
+// The 2-SM pair variant (k_ternary_gemm_pair) and the adjoint modes are
+// described where they are defined.
 // Every mbarrier wait is bounded; a timeout records NDFT_E_TIMEOUT in the
 // plan's error word and the CTA drains and exits.
 #include "internal.cuh"
