@@ -67,11 +67,13 @@ def select(times: list[tuple[dict, float]]) -> dict:
 
 
 def tune(plan, run, key: str, space: dict, device_name: str, reps: int = 3, timer=None, path: str | None = None,
-         force: bool = False) -> dict:
+         force: bool = False, rounds: int = 2) -> dict:
     """Pick the fastest setting of `space` for `run()` on `plan`, cached under (device, key).
 
     `timer(run, reps)` returns seconds per call (default: CUDA events around the
-    calls); the chosen setting is applied to the plan and returned."""
+    calls); every candidate is timed in each of `rounds` passes over the space
+    and keeps its best time, so a transient slowdown during one pass does not
+    decide the choice.  The chosen setting is applied to the plan and returned."""
     path = path or cache_path()
     ckey = f"{device_name}|{key}"
     with _lock:
@@ -82,12 +84,16 @@ def tune(plan, run, key: str, space: dict, device_name: str, reps: int = 3, time
             plan.set_tuning(k, v)
         return setting
     timer = timer or _cuda_timer
-    results = []
-    for setting in candidates(space):
-        for k, v in setting.items():
-            plan.set_tuning(k, v)
-        run()  # warm
-        results.append((setting, timer(run, reps)))
+    cands = candidates(space)
+    best_t = [float("inf")] * len(cands)
+    for r in range(max(1, rounds)):
+        for i, setting in enumerate(cands):
+            for k, v in setting.items():
+                plan.set_tuning(k, v)
+            if r == 0:
+                run()  # warm
+            best_t[i] = min(best_t[i], timer(run, reps))
+    results = list(zip(cands, best_t))
     best = select(results)
     for k, v in best.items():
         plan.set_tuning(k, v)
