@@ -107,3 +107,33 @@ def test_nfft_and_ndft_in_a_graph(api):
     torch.cuda.synchronize()
     assert np.array_equal(y.cpu().numpy(), pn.nfft(x).cpu().numpy())
     assert np.array_equal(z.cpu().numpy(), pt.ndft(x).cpu().numpy())
+
+
+def test_autograd_forward_backward_in_a_graph(api):
+    """The differentiation workload (Eq. 12a forward, loss sum |A| over a mask,
+    backward through CafFunction) captured once and replayed: the gradient
+    equals the eager one bit for bit."""
+    sc = scenes.radar_scene(N=4096, seed=4, nlags=128, nbins=128)
+    plan = api.Plan(sc.N, p0=sc.p0, nbins=128, max_lags=128, form="ternary", prec="bf16x2")
+    mask = torch.from_numpy(scenes.differentiation_mask(sc).astype(np.float32)).cuda()
+    sr = torch.from_numpy(sc.s_ref).cuda()
+    s = torch.from_numpy(sc.s_surv).cuda().requires_grad_(True)
+
+    def step():
+        s.grad = None
+        (api.caf_autograd(s, sr, plan, 0, 128).abs() * mask).sum().backward()
+    step()
+    eager = s.grad.detach().clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    s.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        (api.caf_autograd(s, sr, plan, 0, 128).abs() * mask).sum().backward()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(s.grad, eager)
+    plan.query_error()
