@@ -58,7 +58,9 @@ def test_nfft_form_bins(api, N, batch, p0, nbins):
 @pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
     (8, -3, 12, 0, 0, 0), (256, 0, 40, -128, 256, 0), (1024, -5, 77, -512, 1024, 0),
     (4096, 100, 9, 7, 33, 1), (4096, 4000, 9, 0, 16, 2), (8192, 0, 21, -4096, 8192, 0),
-    (16384, 37, 5, -512, 1024, 0), (65536, 0, 3, -512, 1024, 0), (65536, 65530, 9, 0, 64, 2)])
+    (16384, 37, 5, -512, 1024, 0), (65536, 0, 3, -512, 1024, 0), (65536, 65530, 9, 0, 64, 2),
+    # the pruned tail at its limits: exactly 2^LA bins, and a window that wraps past bin 0
+    (8192, 5, 7, 100, 1024, 0), (16384, -2, 6, -300, 700, 1)])
 def test_nfft_form_caf(api, N, lag0, nlags, p0, nbins, flags):
     sc = scenes.radar_scene(N=N, nlags=max(nlags, 1), nbins=min(N, 64), seed=60 + N % 97)
     nb = nbins or N
