@@ -240,6 +240,10 @@ __global__ void k_fft_tiny(Src src, Dst dst, const float2 *__restrict__ tw, int 
 // swizzle of the low 4 index bits that keeps every exchange free of bank
 // conflicts.  Twiddles sit in shared memory as one table per stage, indexed
 // by k, prepared by the op, so a warp reads consecutive entries.
+// swz is linear over GF(2) (shifts, masks and XORs of p's bits), and a
+// thread's positions base | j << W have base and j << W on disjoint bits, so
+// swz(base | j << W) = swz(base) ^ swz(j << W): one XOR with a constant per
+// element once swz(base) is known.
 __device__ __forceinline__ int swz(int p) { return p ^ ((p >> 4) & 15) ^ ((p >> 8) & 15) ^ ((p >> 3) & 8); }
 
 __device__ __forceinline__ int rev3(int j) { return ((j & 1) << 2) | (j & 2) | ((j >> 2) & 1); }
@@ -282,7 +286,7 @@ __device__ __forceinline__ void dit_passes(float2 (&r)[8], float2 *s, int t, con
         } else {
             base = (t & ((1 << W) - 1)) | ((t >> W) << (W + 3));
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] = s[swz(base | (j << W))];
+            for (int j = 0; j < 8; ++j) r[j] = s[swz(base) ^ swz(j << W)];
         }
         reg_stages<Op, false, W, B0, W + 3>(r, base & ((1 << W) - 1), tab);
         if constexpr (last) {
@@ -292,7 +296,7 @@ __device__ __forceinline__ void dit_passes(float2 (&r)[8], float2 *s, int t, con
                 for (int j = 0; j < 8; ++j) dst(q, base | (j << W), r[j]);
         } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s[swz(base | (j << W))] = r[j];
+            for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
             __syncthreads();  // pass results visible before the next pass reads them
             dit_passes<Op, LOGN, SB, B0 + 3>(r, s, t, tab, src, dst, q, live);
         }
@@ -315,7 +319,7 @@ __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, con
             for (int j = 0; j < 8; ++j) r[j] = live ? src(q, base | (j << W)) : make_float2(0.f, 0.f);
         } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] = s[swz(base | (j << W))];
+            for (int j = 0; j < 8; ++j) r[j] = s[swz(base) ^ swz(j << W)];
         }
         reg_stages<Op, true, W, W, B1>(r, base & ((1 << W) - 1), tab);
         if constexpr (last) {
@@ -328,7 +332,7 @@ __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, con
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s[swz(base | (j << W))] = r[j];
+            for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
             __syncthreads();  // pass results visible before the next pass reads them
             dif_passes<Op, LOGN, SB, W>(r, s, t, tab, src, dst, q, live);
         }
