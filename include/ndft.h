@@ -148,7 +148,9 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
  *   A[a][k] = sum_i ( s_surv[i] (x) conj(s_ref[i - l]) ) (x) W^((i p) mod N),
  *   l = lag0 + a (0 <= a < nlags), p = p0 + k (0 <= k < nbins),
  * s_ref[j] = 0 outside [0, N) unless NDFT_F_CIRCULAR_LAG.
- * s_surv, s_ref: [N]; A: [nlags][nbins]; 1 <= nlags <= max_lags.
+ * s_surv, s_ref: [N]; A: [nlags][nbins]; 1 <= nlags <= max_lags and
+ * lag0 + nlags - 1 <= INT32_MAX (NDFT_E_INVALID otherwise; the same bound holds
+ * for caf_backward, caf_backward_inputs, caf_exec_noalloc and every batched CPI).
  * On an NDFT_FORM_NFFT plan the sum over i is the Sec. 3 NFFT of the lag
  * product z_l (computed in fp32 as above): A[a][k] = NFFT(z_l)[(p0 + k) mod N],
  * reproducible bit for bit.  On an NDFT_FORM_FFT plan it is the ordinary DFT

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256)
         for (int q = 0; q < 4; ++q) {
             const int l = l0 + ty * 4 + q;
             if (i >= N || l >= nlags) continue;
-            int64_t jj = (int64_t)i - (lag0 + l);
+            int64_t jj = (int64_t)i - ((int64_t)lag0 + l);
             if (flags & NDFT_F_CIRCULAR_LAG) {
                 jj %= N;
                 if (jj < 0) jj += N;

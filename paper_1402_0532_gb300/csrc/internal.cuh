@@ -13,6 +13,12 @@ namespace ndft {
 
 constexpr uint32_t kSignBit = 0x80000000u;
 
+// The lag window lag0 .. lag0 + nlags - 1 of a CAF call must be representable
+// in int32 so that every per-lag index (lag0 + a) is an int without overflow.
+inline bool lag_window_ok(int32_t lag0, int32_t nlags) {
+    return nlags >= 1 && (int64_t)lag0 + nlags - 1 <= (int64_t)INT32_MAX;
+}
+
 // Device error codes written to the plan's error word (first writer wins).
 enum DevErr : int32_t { kDevOk = 0, kDevTimeout = 5, kDevBadIndex = 7 };
 

@@ -60,7 +60,7 @@ using namespace ndft;
 
 extern "C" ndft_status caf_exec_noalloc(int32_t n, int32_t p0, int32_t nbins, const void *s_surv, const void *s_ref,
                                         int32_t lag0, int32_t nlags, uint32_t flags, void *A, cudaStream_t stream) {
-    if (n < 1 || n > kMaxNoallocN || nbins < 1 || nbins > n || nlags < 1 || nlags > (1 << 20)) return NDFT_E_INVALID;
+    if (n < 1 || n > kMaxNoallocN || nbins < 1 || nbins > n || !lag_window_ok(lag0, nlags) || nlags > (1 << 20)) return NDFT_E_INVALID;
     if (flags & ~(uint32_t)(NDFT_F_NO_CONJ_REF | NDFT_F_CIRCULAR_LAG)) return NDFT_E_INVALID;
     if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(A)) return NDFT_E_INVALID;
     void *scratch = nullptr;

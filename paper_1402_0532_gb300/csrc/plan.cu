@@ -215,7 +215,7 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
 ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags, void *A,
                      cudaStream_t stream) {
     const Range range("caf_exec");
-    if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
+    if (!plan || plan->p.batched || !lag_window_ok(lag0, nlags) || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(A)) return NDFT_E_INVALID;
     if (A == s_surv || A == s_ref) return NDFT_E_INVALID;
     Plan &p = plan->p;
@@ -236,7 +236,7 @@ ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref
                          const void *dA, void *ds, cudaStream_t stream) {
     const Range range("caf_backward");
     (void)s_surv;
-    if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
+    if (!plan || plan->p.batched || !lag_window_ok(lag0, nlags) || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     Plan &p = plan->p;
     if (p.d.prec == NDFT_PREC_Q14 || fft_form(p.d.form)) return NDFT_E_UNSUPPORTED;
     if (!aligned16(s_ref) || !aligned16(dA) || !aligned16(ds)) return NDFT_E_INVALID;
@@ -255,7 +255,7 @@ ndft_status caf_backward_inputs(ndft_plan_t plan, const void *s_surv, const void
                                 int32_t nlags, const void *dA, void *ds_surv, void *ds_ref, cudaStream_t stream) {
     if (!ds_ref) return ds_surv ? caf_backward(plan, s_surv, s_ref, lag0, nlags, dA, ds_surv, stream) : NDFT_E_INVALID;
     const Range range("caf_backward_inputs");
-    if (!plan || plan->p.batched || nlags < 1 || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
+    if (!plan || plan->p.batched || !lag_window_ok(lag0, nlags) || nlags > plan->p.d.max_lags) return NDFT_E_INVALID;
     Plan &p = plan->p;
     if (p.d.prec == NDFT_PREC_Q14 || fft_form(p.d.form)) return NDFT_E_UNSUPPORTED;
     if (!aligned16(s_surv) || !aligned16(s_ref) || !aligned16(dA) || !aligned16(ds_ref) ||
@@ -399,7 +399,7 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
     if (!valid_pair(form, prec) || fft_form(form)) return NDFT_E_UNSUPPORTED;
     for (int c = 0; c < ncpi; ++c) {
         const ndft_cpi &q = cpis[c];
-        if (q.n < 1 || q.n > kMaxN || q.nlags < 1 || q.nlags > (1 << 20) || q.nbins < 1 || q.nbins > q.n ||
+        if (q.n < 1 || q.n > kMaxN || !lag_window_ok(q.lag0, q.nlags) || q.nlags > (1 << 20) || q.nbins < 1 || q.nbins > q.n ||
             q.off_surv < 0 || q.off_ref < 0 || q.off_out < 0 || q.reserved)
             return NDFT_E_INVALID;
         // 16-byte alignment of each CPI's rows: offsets in elements of 8 bytes (complex64) or 4 (Q1.14)

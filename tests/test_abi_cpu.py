@@ -73,6 +73,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ndft_plan_batched(ctypes.byref(h), None, 0, 0, 0, 0, None) == L.E_INVALID
     cpi = (L.NdftCpi * 1)(L.NdftCpi(n=0, nlags=1, nbins=1))
     assert lib.ndft_plan_batched(ctypes.byref(h), cpi, 1, 0, 0, 0, None) == L.E_INVALID
+    # a lag window running past INT32_MAX is refused before any device call
+    cpi = (L.NdftCpi * 1)(L.NdftCpi(n=1024, lag0=2**31 - 3, nlags=4, nbins=8))
+    assert lib.ndft_plan_batched(ctypes.byref(h), cpi, 1, 0, 0, 0, None) == L.E_INVALID
 
 
 def test_binding_refuses_cpu_tensors():

@@ -1,6 +1,7 @@
 """Edge cases of the CUDA path against the oracle: the largest transform each
 form accepts, an empty batch, a lag window entirely outside the samples
-(exact zeros), a single lag, and the adjoints at the same degenerate inputs."""
+(exact zeros), lag windows at the int32 limits, a single lag, and the adjoints
+at the same degenerate inputs."""
 import ctypes
 
 import numpy as np
@@ -94,6 +95,57 @@ def test_lags_outside_the_samples_give_exact_zeros(api, form, prec):
     assert np.all(A == 0)
     B = p.caf(ss, sr, -N - 5, 3).cpu().numpy()
     assert np.all(B == 0)
+
+
+I32_MAX, I32_MIN = 2**31 - 1, -2**31
+
+
+@pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2"), ("nfft", "fp32"),
+                                       ("fft", "fp32")])
+def test_lag_windows_at_the_int32_limits(api, form, prec):
+    """Windows ending at INT32_MAX or starting at INT32_MIN: without
+    F_CIRCULAR_LAG the surface is exactly 0; with it the lags reduce modulo N
+    and the surface equals the one at the reduced window.  A window one lag
+    past INT32_MAX is an argument error."""
+    from paper_1402_0532_gb300 import _lib as L
+    N, nl = 1024, 4
+    rng = np.random.default_rng(84)
+    ss = dev(scenes.cn(rng, (N,)).astype(np.complex64))
+    sr = dev(scenes.cn(rng, (N,)).astype(np.complex64))
+    for lag0 in (I32_MAX - nl + 1, I32_MIN):
+        p = api.Plan(N, p0=-16, nbins=32, max_lags=nl, form=form, prec=prec)
+        assert torch.count_nonzero(p.caf(ss, sr, lag0, nl)).item() == 0
+        pc = api.Plan(N, p0=-16, nbins=32, max_lags=nl, form=form, prec=prec, flags=api.F_CIRCULAR_LAG)
+        got = pc.caf(ss, sr, lag0, nl).cpu().numpy()
+        ref = pc.caf(ss, sr, lag0 % N, nl).cpu().numpy()  # lag0 % N + nl <= N: no wrap inside
+        pc.query_error()
+        assert relerr(got, ref) < 1e-6
+    A = torch.zeros(nl * 32, dtype=torch.complex64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    st = p.lib.caf_exec(p.handle, ctypes.c_void_p(ss.data_ptr()), ctypes.c_void_p(sr.data_ptr()), I32_MAX - nl + 2,
+                        nl, ctypes.c_void_p(A.data_ptr()), s)
+    assert st == L.E_INVALID
+
+
+@pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2")])
+def test_adjoints_at_the_int32_lag_limits(api, form, prec):
+    """Both gradients at a circular window ending at INT32_MAX against the
+    oracle (which takes lags as int64), and exact zeros without wrap."""
+    N, nl, p0, nbins = 512, 3, -7, 16
+    lag0 = I32_MAX - nl + 1
+    rng = np.random.default_rng(85)
+    ss = scenes.cn(rng, (N,)).astype(np.complex64)
+    sr = scenes.cn(rng, (N,)).astype(np.complex64)
+    dA = scenes.cn(rng, (nl, nbins)).astype(np.complex64)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nl, form=form, prec=prec)
+    gs, gr = p.caf_backward_inputs(dev(ss), dev(sr), lag0, nl, dev(dA))
+    assert torch.count_nonzero(gs).item() == 0 and torch.count_nonzero(gr).item() == 0
+    f = api.F_CIRCULAR_LAG
+    pc = api.Plan(N, p0=p0, nbins=nbins, max_lags=nl, form=form, prec=prec, flags=f)
+    gs, gr = pc.caf_backward_inputs(dev(ss), dev(sr), lag0, nl, dev(dA))
+    pc.query_error()
+    assert relerr(gs.cpu().numpy(), oracle.caf_adjoint(ss, sr, lag0, nl, p0, nbins, dA, flags=f)) < TOL
+    assert relerr(gr.cpu().numpy(), oracle.caf_adjoint_ref(ss, sr, lag0, nl, p0, nbins, dA, flags=f)) < TOL
 
 
 @pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2")])
