@@ -55,6 +55,9 @@ class Plan:
         self.nbins = int(nbins) if nbins else int(n)
         self.max_lags, self.max_batch = int(max_lags), int(max_batch)
         self.form, self.prec, self.flags = form, prec, int(flags)
+        self._args = dict(p0=p0, nbins=nbins, max_lags=max_lags, max_batch=max_batch, form=form, prec=prec,
+                          flags=flags, device=self.device)
+        self._tuning = {}
         d = L.NdftDesc(n=self.n, p0=self.p0, nbins=int(nbins), max_lags=self.max_lags,
                        max_batch=self.max_batch, form=_FORMS[form], prec=_PRECS[prec], flags=self.flags)
         h = ctypes.c_void_p()
@@ -97,6 +100,16 @@ class Plan:
 
     def set_tuning(self, key: int, value: int):
         L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
+        self._tuning[int(key)] = int(value)
+
+    def twin(self) -> "Plan":
+        """A second plan with this plan's descriptor and tuning settings and its own
+        tables and workspace: same results bit for bit, and the two can run at once on
+        two streams."""
+        t = Plan(self.n, **self._args)
+        for k, v in self._tuning.items():
+            t.set_tuning(k, v)
+        return t
 
     def timer_start(self, capacity: int):
         """Arm device timing of the main kernel for the next `capacity` exec calls."""
@@ -174,13 +187,18 @@ class Plan:
         torch.cuda.current_stream(self.device).synchronize()
         return out_host
 
-    def caf_from_host_many(self, inputs, lag0: int, nlags: int, outs, staging: dict | None = None):
+    def caf_from_host_many(self, inputs, lag0: int, nlags: int, outs, staging: dict | None = None,
+                           overlap: bool = False):
         """caf_from_host over a sequence of (s_surv_host, s_ref_host) pairs into the host
         surfaces `outs` (one per pair, or one buffer reused), pipelined: two device buffer
-        sets, the inputs of step k copied in on one stream while step k - 1 computes on
-        the current stream, and the surface of step k - 1 copied out on a third while
-        step k computes.  Every step still copies its inputs in and its surface out.
-        Synchronises before returning."""
+        sets, the inputs of step k copied in on one stream while step k - 1 computes, and
+        the surface of step k - 1 copied out on another while step k computes.  Every step
+        still copies its inputs in and its surface out.  overlap=False: every step computes
+        on the current stream with this plan.  overlap=True: odd steps compute on a second
+        stream with a twin plan (``twin()``, kept in `staging`; its own workspace, about
+        ``nbytes()`` more device memory), so the surfaces of consecutive steps can overlap
+        on the GPU (the lag-product packing of step k under the contraction of step k - 1);
+        the surfaces are the same bit for bit.  Synchronises before returning."""
         st = {} if staging is None else staging
         dev = self.device
         comp = torch.cuda.current_stream(dev)
@@ -189,6 +207,16 @@ class Plan:
         inputs = list(inputs)
         if not inputs:
             return outs
+        if overlap:
+            if "twin" not in st:
+                st["twin"], st["comp2"] = self.twin(), torch.cuda.Stream(dev)
+            for k, v in self._tuning.items():  # follow tuning changes made since the twin was made
+                if st["twin"]._tuning.get(k) != v:
+                    st["twin"].set_tuning(k, v)
+            plans, comps = (self, st["twin"]), (comp, st["comp2"])
+            st["comp2"].wait_stream(comp)
+        else:
+            plans, comps = (self, self), (comp, comp)
         hs0, hr0 = inputs[0]
         if "pipe" not in st:
             st["pipe"] = [dict(ss=torch.empty_like(hs0, device=dev), sr=torch.empty_like(hr0, device=dev),
@@ -200,26 +228,31 @@ class Plan:
         single_out = not isinstance(outs, (list, tuple))
         for k, (hs, hr) in enumerate(inputs):
             b = k % 2
-            buf = bufs[b]
+            buf, cs = bufs[b], comps[b]
             with torch.cuda.stream(st["h2d"]):
                 if e_comp[b] is not None:
                     st["h2d"].wait_event(e_comp[b])  # step k - 2 is done reading this buffer
                 buf["ss"].copy_(hs, non_blocking=True)
                 buf["sr"].copy_(hr, non_blocking=True)
                 e_in[b].record(st["h2d"])
-            comp.wait_event(e_in[b])
+            cs.wait_event(e_in[b])
             if e_out[b] is not None:
-                comp.wait_event(e_out[b])  # the surface of step k - 2 has been copied out
-            self.caf(buf["ss"], buf["sr"], lag0, nlags, out=buf["A"])
+                cs.wait_event(e_out[b])  # the surface of step k - 2 has been copied out
+            with torch.cuda.stream(cs):
+                plans[b].caf(buf["ss"], buf["sr"], lag0, nlags, out=buf["A"])
             e_comp[b] = ev()
-            e_comp[b].record(comp)
+            e_comp[b].record(cs)
             with torch.cuda.stream(st["d2h"]):
                 st["d2h"].wait_event(e_comp[b])
                 (outs if single_out else outs[k]).copy_(buf["A"], non_blocking=True)
                 e_out[b] = ev()
                 e_out[b].record(st["d2h"])
         st["d2h"].synchronize()
-        comp.synchronize()
+        for cs in comps:
+            cs.synchronize()
+        if overlap:
+            comp.wait_stream(st["comp2"])
+            st["twin"].query_error()
         return outs
 
     def caf_backward(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int, dA: torch.Tensor,

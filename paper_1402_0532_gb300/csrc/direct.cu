@@ -10,11 +10,11 @@
 // (gathered from the plan's fp32 table at (p n) mod N, the index advanced
 // incrementally) and the 16 x 64 data values, both already split into the
 // pieces (x) needs.  Each thread then accumulates a 4 x 4 register tile.
-// fp32: magnitude and sign as a float in {-1, 0, +1}; one real (x) accumulated
-// is an add of magnitudes, a product of the two signs and one fma into the
-// accumulator -- acc + (|a| + |b|) sgn(a) sgn(b), where the product by the
-// sign product is exact, so it rounds exactly as acc + (a (x) b) (Eq. 1-2,
-// the zero case explicit as a zero sign).  All three run on the fp32 pipe.
+// fp32: the twiddle as magnitude and sign (a float in {-1, 0, +1}), the data
+// as its signed value and sign; one real (x) accumulated is two fmas:
+// fma(sgn a, fma(sgn b, |a|, b), acc) = acc + sgn(a) sgn(b)(|a| + |b|), the
+// inner sum rounded once and the product by sgn a exact, so it rounds exactly
+// as acc + (a (x) b) (Eq. 1-2, the zero case explicit as a zero sign).
 // Q1.14: magnitude, sign mask and nonzero mask; one real (x) is an integer add
 // of magnitudes with the sign applied by XOR and the zero case by AND.  One
 // complex (x) is four real ones (Eq. 6).
@@ -46,19 +46,29 @@ struct PrecF32 {
     __device__ static V conj_(V v) { return make_float2(v.x, -v.y); }
     __device__ static V cox(V a, V b) { return cox_f32(a, b); }
     __device__ static float sgn1(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+    // twiddle side: magnitudes and signs
     __device__ static void ready(V v, Mag &m, Sgn &s) {
         m = make_float2(fabsf(v.x), fabsf(v.y));
         s = make_float2(sgn1(v.x), sgn1(v.y));
     }
+    // data side: the signed value itself and its sign
+    __device__ static void ready_data(V v, Mag &m, Sgn &s) {
+        m = v;
+        s = make_float2(sgn1(v.x), sgn1(v.y));
+    }
     __device__ static Acc acc0() { return make_float2(0.f, 0.f); }
-    // acc += w (x) v, Eq. 6: re += w_r(x)v_r - w_i(x)v_i, im += w_i(x)v_r + v_i(x)w_r,
-    // each a (x) b as fma(|a| + |b|, sgn a sgn b, acc): the product is exact, so
-    // the result equals fl(acc + a (x) b) with a (x) b rounded once (Eq. 1)
-    __device__ static void mac(Acc &acc, const Mag &wm, const Sgn &ws, const Mag &vm, const Sgn &vs) {
-        acc.x = __fmaf_rn(__fadd_rn(wm.x, vm.x), __fmul_rn(ws.x, vs.x), acc.x);
-        acc.x = __fmaf_rn(__fadd_rn(wm.y, vm.y), -__fmul_rn(ws.y, vs.y), acc.x);
-        acc.y = __fmaf_rn(__fadd_rn(wm.y, vm.x), __fmul_rn(ws.y, vs.x), acc.y);
-        acc.y = __fmaf_rn(__fadd_rn(vm.y, wm.x), __fmul_rn(vs.y, ws.x), acc.y);
+    // acc += w (x) v, Eq. 6: re += w_r(x)v_r - w_i(x)v_i, im += w_i(x)v_r + v_i(x)w_r.
+    // Each a (x) b with a the twiddle component and b the data component is
+    // fma(sgn a, fma(sgn b, |a|, b), acc): the inner fma is sgn(b)(|a| + |b|)
+    // rounded once (round to nearest is symmetric; 0 when b = 0), the outer
+    // scales it exactly by sgn a (0 when a = 0) and rounds the sum once, so the
+    // result is fl(acc + a (x) b) with a (x) b rounded once (Eq. 1): two
+    // instructions per real (x).  wm, ws: |w|, sgn w; vv, vs: v, sgn v.
+    __device__ static void mac(Acc &acc, const Mag &wm, const Sgn &ws, const Mag &vv, const Sgn &vs) {
+        acc.x = __fmaf_rn(ws.x, __fmaf_rn(vs.x, wm.x, vv.x), acc.x);
+        acc.x = __fmaf_rn(-ws.y, __fmaf_rn(vs.y, wm.y, vv.y), acc.x);
+        acc.y = __fmaf_rn(ws.y, __fmaf_rn(vs.x, wm.y, vv.x), acc.y);
+        acc.y = __fmaf_rn(ws.x, __fmaf_rn(vs.y, wm.x, vv.y), acc.y);
     }
     __device__ static float2 out(const Acc &a) { return a; }
     using Out = float2;
@@ -84,6 +94,7 @@ struct PrecQ14 {
         s = make_uint4(v.x < 0 ? 0xffffffffu : 0u, v.y < 0 ? 0xffffffffu : 0u, v.x ? 0xffffffffu : 0u,
                        v.y ? 0xffffffffu : 0u);
     }
+    __device__ static void ready_data(V v, Mag &m, Sgn &s) { ready(v, m, s); }
     __device__ static Acc acc0() { return make_uint2(0u, 0u); }
     __device__ static uint32_t ox(int am, uint32_t as, uint32_t az, int bm, uint32_t bs, uint32_t bz) {
         const uint32_t m = (uint32_t)(am + bm);
@@ -138,7 +149,7 @@ struct CafSrc {
 };
 
 struct Smem {
-    // [KC][BP + 2] magnitudes and [KC][BP + 1] sign/zero words, twiddles then data.
+    // [KC][BP + 2] magnitudes (fp32 data: values) and [KC][BP + 1] sign/zero words, twiddles then data.
     static constexpr int kMagStride = BP + 2;
     static constexpr int kSgnStride = BP + 1;
     __host__ __device__ static constexpr size_t bytes(size_t mag_size, size_t sgn_size) {
@@ -225,7 +236,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
             typename P::V v = (n < n_end && col0 + c < ncols) ? src(col0 + c, n) : P::zero();
             Mag mg;
             Sgn sg;
-            P::ready(v, mg, sg);
+            P::ready_data(v, mg, sg);
             vM[dk * Smem::kMagStride + c] = mg;
             vS[dk * Smem::kSgnStride + c] = sg;
         }

@@ -138,7 +138,7 @@ __device__ __forceinline__ float sgnf(float v) {
 
 // sgn(v) in two instructions: 1.0f where v != 0 (set.ne), with v's sign bit
 // copied in; a zero v gives a zero of v's sign.  cox_ready only multiplies it
-// by a twiddle magnitude and adds v back, and its outer fma's +0 addend turns
+// by a twiddle magnitude and adds v back, and its outer fmas' +0 addends turn
 // every zero into +0, so the result has the same bits as with sgnf.
 __device__ __forceinline__ float sgn_mul(float v) {
     float nz;
@@ -147,18 +147,23 @@ __device__ __forceinline__ float sgn_mul(float v) {
 }
 
 // Eq. 6 with the twiddle in "ready" form (|Re|, |Im|, sgn Re, sgn Im).  Each
-// real a (x) b = sgn(a) sgn(b) (|a| + |b|) is formed as
-// fma(sgn a, fma(sgn b, |a|, b), +0): the inner fma rounds sgn(b)(|a| + |b|)
-// once (round to nearest is symmetric), the outer one scales it exactly by
-// sgn a, and the +0 addend turns every zero product into +0, as the
-// definition's 0 for a zero operand.  Same bits as cox_f32.
+// real a (x) b = sgn(a) sgn(b) (|a| + |b|) starts as the inner
+// fma(sgn b, |a|, b) = sgn(b)(|a| + |b|), rounded once (round to nearest is
+// symmetric); scaling it by sgn a (+-1 or 0) is exact, so the difference and
+// the sum of Eq. 6 each take one more fma: Re = fma(sgn Wr, i1, -(Wi (x) Oi))
+// with -(Wi (x) Oi) = fma(-sgn Wi, i2, +0), one rounding as in t1 - t2, and
+// the +0 addend makes every zero come out +0, as the definition's 0 for a zero
+// operand.  Same bits as cox_f32, signed zeros, subnormals, exact
+// cancellations and the axis twiddles included.
 __device__ __forceinline__ float2 cox_ready(float4 w, float2 o) {
     const float sx = sgn_mul(o.x), sy = sgn_mul(o.y);
-    const float t1 = __fmaf_rn(w.z, __fmaf_rn(sx, w.x, o.x), 0.f);  // Wr (x) Or
-    const float t2 = __fmaf_rn(w.w, __fmaf_rn(sy, w.y, o.y), 0.f);  // Wi (x) Oi
-    const float t3 = __fmaf_rn(w.w, __fmaf_rn(sx, w.y, o.x), 0.f);  // Wi (x) Or
-    const float t4 = __fmaf_rn(w.z, __fmaf_rn(sy, w.x, o.y), 0.f);  // Oi (x) Wr
-    return make_float2(__fsub_rn(t1, t2), __fadd_rn(t3, t4));
+    const float i1 = __fmaf_rn(sx, w.x, o.x);  // sgn Or (|Wr| + |Or|)
+    const float i2 = __fmaf_rn(sy, w.y, o.y);  // sgn Oi (|Wi| + |Oi|)
+    const float i3 = __fmaf_rn(sx, w.y, o.x);  // sgn Or (|Wi| + |Or|)
+    const float i4 = __fmaf_rn(sy, w.x, o.y);  // sgn Oi (|Wr| + |Oi|)
+    const float n2 = __fmaf_rn(-w.w, i2, 0.f);  // -(Wi (x) Oi)
+    const float t4 = __fmaf_rn(w.z, i4, 0.f);   // Oi (x) Wr
+    return make_float2(__fmaf_rn(w.z, i1, n2), __fmaf_rn(w.w, i3, t4));
 }
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
