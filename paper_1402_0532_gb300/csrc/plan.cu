@@ -71,6 +71,9 @@ void free_plan(Plan &p) {
         for (int i = 0; i < 2 * p.tcap; ++i) cudaEventDestroy(p.tev[i]);
         delete[] p.tev;
     }
+    if (p.ev_fork) cudaEventDestroy(p.ev_fork);
+    if (p.ev_join) cudaEventDestroy(p.ev_join);
+    if (p.side) cudaStreamDestroy(p.side);
 }
 
 template <class T>
@@ -383,6 +386,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
     } else if (key == 4) {
         if (value > 1) return NDFT_E_INVALID;
         plan->p.test_starve = value;
+    } else if (key == 5) {
+        if (value > (1 << 20) || (value > 1 && value % 256)) return NDFT_E_INVALID;
+        plan->p.tune_parts = value;
     } else {
         return NDFT_E_INVALID;
     }

@@ -1251,25 +1251,31 @@ __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__rest
     }
 }
 
-// One problem: block (x, y) packs columns [32 x, 32 x + 32) of K blocks
-// [8 y, 8 y + 8), one 16-byte entry per thread and K block, no division.
+// One problem: tile (x, y) = b mod gx, b / gx packs columns [32 x, 32 x + 32)
+// of K blocks [8 y, 8 y + 8), one 16-byte entry per thread and K block.  Block
+// b0 takes tiles b0, b0 + gridDim.x, ...: one tile per block on a full grid, or
+// a bounded grid that leaves room on every SM for a contraction CTA.
 constexpr int kPackKb = 8;
 __global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags, bool caf,
                                                      const float2 *__restrict__ a_base,
-                                                     const float2 *__restrict__ r_base, uint4 *__restrict__ B) {
+                                                     const float2 *__restrict__ r_base, uint4 *__restrict__ B,
+                                                     int gx, int64_t ntiles) {
     const int t = threadIdx.x & 7;
-    const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
-    if (col >= P.ncols) return;
     const float2 *a = a_base + P.a_off;
     const float2 *r = r_base + P.r_off;
-    const int kb0 = blockIdx.y * kPackKb;
-    const int kb1 = min(kb0 + kPackKb, P.kblocks);
+    for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int bx = (int)(b % gx), by = (int)(b / gx);
+        const int col = bx * 32 + (threadIdx.x >> 3);
+        if (col >= P.ncols) continue;
+        const int kb0 = by * kPackKb;
+        const int kb1 = min(kb0 + kPackKb, P.kblocks);
 #pragma unroll 2
-    for (int kb = kb0; kb < kb1; ++kb) {
-        const int64_t i = (int64_t)kb * 8 + t;
-        float2 v = make_float2(0.f, 0.f);
-        if (i < P.N) v = caf ? lag_product(P, a, r, col, i, flags) : a[(int64_t)col * P.ldx + i];
-        B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
+        for (int kb = kb0; kb < kb1; ++kb) {
+            const int64_t i = (int64_t)kb * 8 + t;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < P.N) v = caf ? lag_product(P, a, r, col, i, flags) : a[(int64_t)col * P.ldx + i];
+            B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
+        }
     }
 }
 
@@ -1419,14 +1425,20 @@ int choose_split(int64_t tiles, int kblocks, int sm, int tune, int64_t cap_units
     return std::max(1, std::min(s, std::max(1, kblocks / 4)));
 }
 
+// max_blocks > 0 bounds the single-problem grid (blocks then loop over tiles).
 cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob, const PackProb &single,
                         int64_t rows, uint32_t flags, bool caf, const void *a_base, const void *r_base, void *B, int sm,
-                        cudaStream_t s) {
+                        cudaStream_t s, int max_blocks = 0) {
     const int threads = 256;
-    if (!probs && (single.kblocks + kPackKb - 1) / kPackKb <= 65535) {
-        const dim3 grid((single.ncols + 31) / 32, (single.kblocks + kPackKb - 1) / kPackKb);
-        k_pack_single<<<grid, threads, 0, s>>>(single, flags, caf, static_cast<const float2 *>(a_base),
-                                               static_cast<const float2 *>(r_base), static_cast<uint4 *>(B));
+    if (!probs) {
+        const int gx = (single.ncols + 31) / 32;
+        const int64_t ntiles = (int64_t)gx * ((single.kblocks + kPackKb - 1) / kPackKb);
+        int64_t blocks = ntiles;
+        if (max_blocks > 0) blocks = std::min<int64_t>(blocks, max_blocks);
+        blocks = std::min<int64_t>(blocks, INT32_MAX);
+        k_pack_single<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, s>>>(
+            single, flags, caf, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base),
+            static_cast<uint4 *>(B), gx, ntiles);
         return cudaGetLastError();
     }
     const int64_t want = (rows * 8 + threads - 1) / threads;
@@ -1564,37 +1576,58 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
         return e;
     p.tmap_host2 = std::aligned_alloc(64, sizeof(CUtensorMap));  // 128-row box for the pair tile
     if (!p.tmap_host2) return cudaErrorMemoryAllocation;
-    return make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host2), TN / 2);
+    if ((e = make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host2), TN / 2)) !=
+        cudaSuccess)
+        return e;
+    // side stream and fork / join events of the two-part contraction; the packing
+    // kernel asks for the largest shared-memory carveout, so that an SM running
+    // its blocks is configured to take a contraction CTA beside them
+    if ((e = cudaFuncSetAttribute(k_pack_single, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    return cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming);
 }
 
-static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, const void *a_base,
-                              const void *r_base, void *out, cudaStream_t s, int *launches) {
+// Packs columns [c0, c0 + nc) of a single problem into the B rows from b_row0
+// on (laid out as a problem of nc columns).
+static cudaError_t pack_cols(Plan &p, PackProb pp, bool caf, int c0, int nc, int64_t b_row0, const void *a_base,
+                             const void *r_base, cudaStream_t s, int max_blocks) {
+    if (caf) pp.lag0 += c0;  // the lag window fits in int32 (checked at the boundary)
+    else pp.a_off += (int64_t)c0 * pp.ldx;
+    pp.ncols = nc;
+    pp.row0 = b_row0;
+    return launch_pack(nullptr, nullptr, 0, pp, (int64_t)pp.kblocks * nc, p.d.flags, caf, a_base, r_base, p.ws,
+                       p.sm_count, s, max_blocks);
+}
+
+// Contraction of nc packed columns (B rows from b_row0 on) into out
+// ([nc][nbins] complex), with the ordered split-K sum when the sample axis is
+// split.
+static cudaError_t gemm_cols(Plan &p, int nc, int64_t b_row0, void *out, cudaStream_t s, int *launches) {
     const int N = p.d.n, nb = p.d.nbins;
     const TernLayout L = layout_for(p.d, p.sm_count);
-    cudaError_t e = launch_pack(nullptr, nullptr, 0, pp, (int64_t)L.kblocks * ncols, p.d.flags, caf, a_base, r_base,
-                                p.ws, p.sm_count, s);
-    if (e != cudaSuccess) return e;
-    *launches += 1;
     Problem P{};
     P.N = N;
     P.p0 = p.d.p0;
     P.nbins = nb;
-    P.ncols = ncols;
+    P.ncols = nc;
     P.kblocks = L.kblocks;
     const bool pair = tile_pair(p);
     const int MH = tile_halves(p);
     const int rows = 128 * MH;
     P.mtiles = (2 * nb + rows - 1) / rows;
-    P.ntiles = (ncols + TN - 1) / TN;
+    P.ntiles = (nc + TN - 1) / TN;
     // scheduled units per split and the slots that run them (a 2-SM pair per unit
     // with the pair tile)
     const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
     const int slots = pair ? p.sm_count / 2 : p.sm_count;
     const int64_t cap_units = (int64_t)(L.part_bytes / ((size_t)rows * TN * sizeof(float)));
     P.nsplit = choose_split(tiles, L.kblocks, slots, p.tune_split, cap_units);
-    P.b_row0 = 0;
+    P.b_row0 = b_row0;
     P.ld = 2LL * nb;
-    P.split_stride = (int64_t)ncols * 2 * nb;
+    P.split_stride = (int64_t)nc * 2 * nb;
     P.ang = p.ang;
     P.nth = nth_for(N);
     P.out_off = 0;
@@ -1604,8 +1637,9 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     // bulk tensor stores / adds for the epilogue when the rows are 16-byte multiples
     alignas(64) CUtensorMap omap;
     const bool tma_out = (nb % 2 == 0) && p.tune_drain == 0 &&
-                         make_out_map(out_base, nb, ncols, P.nsplit, &omap) == cudaSuccess;
+                         make_out_map(out_base, nb, nc, P.nsplit, &omap) == cudaSuccess;
     const CUtensorMap *om = tma_out ? &omap : nullptr;
+    cudaError_t e;
     if (pair) e = launch_gemm_pair(p, P, nunits, out_base, om, s);
     else if (MH == 2) e = launch_gemm<2>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     else e = launch_gemm<1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
@@ -1613,9 +1647,53 @@ static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, 
     *launches += 1;
     if (P.nsplit > 1) {
         *launches += 1;
-        return launch_reduce_splits(part, P.nsplit, (int64_t)ncols * 2 * nb, static_cast<float *>(out), s);
+        return launch_reduce_splits(part, P.nsplit, (int64_t)nc * 2 * nb, static_cast<float *>(out), s);
     }
     return cudaSuccess;
+}
+
+// Columns of the first part when a problem runs in two column parts: the
+// tuning value (a multiple of TN), 1 for one part, or by default half the
+// columns rounded down to TN once there are at least 2 TN.
+static int first_part_cols(const Plan &p, int ncols) {
+    if (!p.side || p.tune_parts == 1) return 0;
+    const int h0 = p.tune_parts > 1 ? p.tune_parts : std::max(TN, (ncols / 2) / TN * TN);
+    return (ncols >= 2 * TN && h0 < ncols) ? h0 : 0;
+}
+
+// Grid of the second part's packing: two blocks of 256 threads per SM, which
+// fit beside one contraction CTA (448 threads, under 48 K registers, the shared
+// memory untouched), so the packing runs under the first part's contraction.
+constexpr int kPackBlocksPerSm = 2;
+
+static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, const void *a_base,
+                              const void *r_base, void *out, cudaStream_t s, int *launches) {
+    const int h0 = first_part_cols(p, ncols);
+    cudaError_t e;
+    if (h0 == 0) {
+        if ((e = pack_cols(p, pp, caf, 0, ncols, 0, a_base, r_base, s, 0)) != cudaSuccess) return e;
+        *launches += 1;
+        return gemm_cols(p, ncols, 0, out, s, launches);
+    }
+    // Two column parts.  Part 0 is packed on s; part 1 is packed on the plan's
+    // side stream once part 0's packing is done (and with it everything before
+    // on s, such as the last call's contraction reading B), during part 0's
+    // contraction; part 1's contraction waits for it.  B rows: part 0 first.
+    const int h1 = ncols - h0;
+    const int64_t row1 = (int64_t)pp.kblocks * h0;
+    if ((e = pack_cols(p, pp, caf, 0, h0, 0, a_base, r_base, s, 0)) != cudaSuccess) return e;
+    *launches += 1;
+    if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess) return e;
+    if ((e = gemm_cols(p, h0, 0, out, s, launches)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = pack_cols(p, pp, caf, h0, h1, row1, a_base, r_base, p.side, kPackBlocksPerSm * p.sm_count)) !=
+        cudaSuccess)
+        return e;
+    *launches += 1;
+    if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
+    float *out1 = static_cast<float *>(out) + (int64_t)h0 * 2 * p.d.nbins;
+    return gemm_cols(p, h1, row1, out1, s, launches);
 }
 
 cudaError_t launch_ternary_ndft(Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s, int *launches) {

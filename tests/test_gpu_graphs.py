@@ -65,6 +65,34 @@ def test_caf_in_a_graph(api, form, prec, tile):
     plan.query_error()
 
 
+@pytest.mark.parametrize("tile", [0, 258])
+def test_two_part_caf_in_a_graph(api, tile):
+    """A tensor-core call of 600 lags runs as two column parts, the second part's
+    packing on the plan's side stream (forked from and joined back into the
+    capturing stream): the captured call replays the eager result bit for bit."""
+    N, nlags, nbins = 8192, 600, 64
+    plan = api.Plan(N, p0=-32, nbins=nbins, max_lags=nlags, form="ternary", prec="bf16x2")
+    if tile:
+        plan.set_tuning(1, tile)
+
+    def inputs(seed):
+        sc = scenes.radar_scene(N=N, nlags=nlags, nbins=nbins, seed=seed)
+        return torch.from_numpy(sc.s_surv).cuda(), torch.from_numpy(sc.s_ref).cuda()
+    ss, sr = inputs(110)
+    A = torch.empty((nlags, nbins), dtype=torch.complex64, device="cuda")
+    g = capture(lambda: plan.caf(ss, sr, -5, nlags, out=A))
+    for seed in (111, 112):
+        s2, r2 = inputs(seed)
+        ss.copy_(s2)
+        sr.copy_(r2)
+        g.replay()
+        torch.cuda.synchronize()
+        want = plan.caf(s2, r2, -5, nlags).cpu().numpy()
+        assert np.array_equal(A.cpu().numpy(), want)
+    assert plan.last_launches() == 6  # two parts: packing, contraction, ordered split-K sum each
+    plan.query_error()
+
+
 @pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2")])
 def test_backward_in_a_graph(api, form, prec):
     N, nlags, nbins = 4096, 64, 64

@@ -116,6 +116,33 @@ def test_ternary_caf_split_k_sampled(api):
     assert np.max(np.abs(Ad - got)) / peak < 2 * TOL
 
 
+@pytest.mark.parametrize("parts", [0, 1, 512])
+def test_ternary_two_column_parts(api, parts):
+    """Calls of at least 512 lags run by default as two column parts (the second
+    part packed under the first part's contraction on the plan's side stream);
+    one part (key 5 = 1) and an explicit first part of 512 lags give the same
+    surface within the bar, ragged in lags, bins and samples."""
+    sc = scenes.radar_scene(N=9000, nlags=700, nbins=200, seed=47)
+    rng = np.random.default_rng(48)
+    lags = np.concatenate([[0, 255, 256, 511, 512, 699], rng.integers(0, 700, 40)])
+    bins = np.concatenate([[0, 5, -12, 99, -100, 40], rng.integers(-100, 100, 40)])
+    ref = oracle.caf_cells(sc.s_surv, sc.s_ref, np.asarray(lags) - 4, bins, z32=True)
+    p = api.Plan(sc.N, p0=sc.p0, nbins=200, max_lags=700, form="ternary", prec="bf16x2")
+    p.set_tuning(5, parts)
+    A = p.caf(dev(sc.s_surv), dev(sc.s_ref), -4, 700).cpu().numpy()
+    p.query_error()
+    assert p.last_launches() == (3 if parts == 1 else 6)
+    peak = np.max(np.abs(A))
+    assert np.max(np.abs(A[lags, bins - sc.p0] - ref)) / peak < TOL
+    # the NDFT of 700 vectors the same way
+    x = scenes.cn(np.random.default_rng(49), (700, 300)).astype(np.complex64)
+    q = api.Plan(300, p0=-7, nbins=77, max_batch=700, form="ternary", prec="bf16x2")
+    q.set_tuning(5, parts)
+    got = q.ndft(dev(x)).cpu().numpy()
+    want = oracle.ndft(x.astype(np.complex128), p0=-7, nbins=77)
+    assert relerr(got, want) < TOL
+
+
 @pytest.mark.parametrize("tile", [256, 128, 258])
 @pytest.mark.parametrize("chunk", [64, 16])
 def test_ternary_tile_variants(api, tile, chunk):
