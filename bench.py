@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile/split settings (no autotuner)")
     ap.add_argument("--tile", type=int, default=0,
                     help="tensor-core tile (tuning key 1: 256, 128, 258 = 2-SM pair); implies --no-tune")
+    ap.add_argument("--parts", type=int, default=-1,
+                    help="tensor-core column parts (tuning key 5: 0 two parts, 1 one part); implies --no-tune")
     ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft", "adjoint"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
@@ -442,14 +444,14 @@ class ClockSampler:
 
 
 def gemm_traffic(per_step: int):
-    """dram bytes per launch of the contraction kernel from the committed ncu summary,
-    or None when the kernel source or the launches per step changed since the capture."""
+    """dram bytes per launch of the contraction kernel from the committed ncu summary
+    (a line `traffic_bytes_per_launch[launches_per_step=K]: X` per captured layout),
+    or None when the kernel source changed since the capture or no line has K = per_step."""
     try:
         txt = open(GEMM_PROFILE).read()
-        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        m = re.search(r"traffic_bytes_per_launch\[launches_per_step=%d\]:\s*([0-9.eE+]+)" % per_step, txt)
         h = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", txt)
-        n = re.search(r"launches_per_step:\s*([0-9]+)", txt)
-        if not m or not h or not n or int(n.group(1)) != per_step:
+        if not m or not h:
             return None
         cur = hashlib.sha1(open(GEMM_SOURCE, "rb").read()).hexdigest()
         return float(m.group(1)) if cur == h.group(1) else None
@@ -548,6 +550,9 @@ def main():
     if args.tile:
         args.no_tune = True
         plan.set_tuning(1, args.tile)
+    if args.parts >= 0:
+        args.no_tune = True
+        plan.set_tuning(5, args.parts)
     tuned = {} if args.no_tune else autotune.tune_caf(plan, ss, sr, 0, NLAGS, out=A)
 
     def step():
