@@ -605,6 +605,9 @@ def main():
                 "issued_frac": issued_flops / gemm_step_s / 1e12 / bf16_peak,
                 "kernel_ms_per_step": gemm_step_s * 1000.0, "launches_per_step": per_step,
                 "kernel_ms_per_launch": gemm_ms / max(gemm_n, 1)}
+    if per_step > 1:
+        roofline["note"] = ("two column parts: the second part's packing runs on the SMs beside the first "
+                            "part's contraction, whose event time includes that interference")
 
     if args.profile:
         if rank == 0:
