@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0,
                     help="tensor-core tile (tuning key 1: 256, 128, 258 = 2-SM pair); implies --no-tune")
     ap.add_argument("--parts", type=int, default=-1,
-                    help="tensor-core column parts (tuning key 5: 0 two parts, 1 one part); implies --no-tune")
+                    help="tensor-core column parts (tuning key 5: 1 one part, the default; 0 two parts); "
+                         "implies --no-tune")
     ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft", "adjoint"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()

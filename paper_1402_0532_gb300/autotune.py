@@ -2,8 +2,7 @@
 
 For a plan and a representative call it tries every candidate setting of the
 knobs exposed by ``ndft_set_tuning`` (split count along the sample axis, tile
-rows of the tensor-core form, tensor-memory accumulation chain length, then
-one or two column parts for tensor-core calls of 512 columns or more), times
+rows of the tensor-core form, tensor-memory accumulation chain length), times
 each with CUDA events on the current stream, keeps the fastest and records it
 in a JSON cache keyed by GPU name and problem shape, so later plans of the
 same shape reuse the choice without timing.
@@ -22,7 +21,7 @@ import threading
 _lock = threading.Lock()
 
 SPLIT, ROWS, CHUNK, DRAIN = 0, 1, 2, 3
-PARTS = 5  # tensor-core calls of >= 512 columns: 0 two column parts (packing overlapped), 1 one part
+PARTS = 5  # tensor-core calls of >= 512 columns: 1 one part (default), 0 two parts (not tuned: see tune_caf)
 
 TERNARY_SPACE = {ROWS: [256, 128, 258], CHUNK: [64, 32], SPLIT: [0, 8, 16, 19, 24, 32]}
 DIRECT_SPACE = {SPLIT: [0, 2, 4, 6, 8, 12, 16]}
@@ -135,9 +134,6 @@ def tune_caf(plan, s_surv, s_ref, lag0: int, nlags: int, out=None, **kw) -> dict
     out = out if out is not None else torch.empty(
         (nlags,) + plan._row_shape(plan.nbins), dtype=plan._out_dtype, device=s_surv.device)
     name = torch.cuda.get_device_name(s_surv.device)
-    run = lambda: plan.caf(s_surv, s_ref, lag0, nlags, out=out)  # noqa: E731
-    best = tune(plan, run, key, space, name, **kw)
-    if plan.form == "ternary" and nlags >= 512:
-        # then one or two column parts, with the other settings fixed
-        best = {**best, **tune(plan, run, f"{key}|parts", {PARTS: [0, 1]}, name, **kw)}
-    return best
+    # (column parts are not tuned: two parts win the short timings here but lose
+    # about 3 % in long runs at the power limit)
+    return tune(plan, lambda: plan.caf(s_surv, s_ref, lag0, nlags, out=out), key, space, name, **kw)

@@ -68,7 +68,7 @@ struct Plan {
     int tune_chunk = 0;          // ternary form: K blocks per TMEM accumulation chain
     int tune_drain = 0;          // ternary form: 0 bulk tensor stores/adds, 1 per-element adds
     int test_starve = 0;         // ternary form, tests only: issue no operand loads (waits run out)
-    int tune_parts = 0;          // ternary form: columns of the first of two parts (0 auto, 1 one part)
+    int tune_parts = 1;          // ternary form: 1 one part (default); 0 two parts, half each; else part 0's columns
     // ternary form: side stream and events of the two-part contraction (the
     // second part's packing runs under the first part's contraction)
     cudaStream_t side = nullptr;

@@ -67,11 +67,12 @@ def test_caf_in_a_graph(api, form, prec, tile):
 
 @pytest.mark.parametrize("tile", [0, 258])
 def test_two_part_caf_in_a_graph(api, tile):
-    """A tensor-core call of 600 lags runs as two column parts, the second part's
-    packing on the plan's side stream (forked from and joined back into the
-    capturing stream): the captured call replays the eager result bit for bit."""
+    """A tensor-core call of 600 lags as two column parts (key 5 = 0), the second
+    part's packing on the plan's side stream (forked from and joined back into
+    the capturing stream): the captured call replays the eager result bit for bit."""
     N, nlags, nbins = 8192, 600, 64
     plan = api.Plan(N, p0=-32, nbins=nbins, max_lags=nlags, form="ternary", prec="bf16x2")
+    plan.set_tuning(5, 0)
     if tile:
         plan.set_tuning(1, tile)
 

@@ -118,10 +118,10 @@ def test_ternary_caf_split_k_sampled(api):
 
 @pytest.mark.parametrize("parts", [0, 1, 512])
 def test_ternary_two_column_parts(api, parts):
-    """Calls of at least 512 lags run by default as two column parts (the second
+    """Key 5 = 0 runs calls of at least 512 lags as two column parts (the second
     part packed under the first part's contraction on the plan's side stream);
-    one part (key 5 = 1) and an explicit first part of 512 lags give the same
-    surface within the bar, ragged in lags, bins and samples."""
+    one part (key 5 = 1, the default) and an explicit first part of 512 lags
+    give the same surface within the bar, ragged in lags, bins and samples."""
     sc = scenes.radar_scene(N=9000, nlags=700, nbins=200, seed=47)
     rng = np.random.default_rng(48)
     lags = np.concatenate([[0, 255, 256, 511, 512, 699], rng.integers(0, 700, 40)])
