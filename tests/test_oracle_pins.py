@@ -630,3 +630,28 @@ def test_adjoint_sampled_matches_full(oracle):
                               full_s[idx])
         assert np.array_equal(oracle.caf_adjoint_at(ss, sr, lag0, nlags, p0, nbins, gA, "ref", idx, flags),
                               full_r[idx])
+
+
+def test_lags_at_the_int32_limits(oracle):
+    """Lags are taken as int64 by the oracle: windows ending at 2^31 - 1 or
+    starting at -2^31 meet no sample (exact zeros, adjoints included), and with
+    the circular flag they reduce modulo N, so they equal the reduced window."""
+    rng = np.random.default_rng(92)
+    N, nlags, p0, nbins = 40, 3, -5, 9
+    ss = scenes.cn(rng, (N,))
+    sr = scenes.cn(rng, (N,))
+    gA = scenes.cn(rng, (nlags, nbins))
+    circ = oracle.F_CIRCULAR_LAG
+    for lag0 in (2**31 - nlags, -2**31):
+        assert np.all(oracle.caf(ss, sr, lag0, nlags, p0, nbins) == 0)
+        assert np.all(oracle.caf_adjoint(ss, sr, lag0, nlags, p0, nbins, gA) == 0)
+        assert np.all(oracle.caf_adjoint_ref(ss, sr, lag0, nlags, p0, nbins, gA) == 0)
+        red = lag0 % N
+        assert red + nlags <= N  # no wrap inside the reduced window
+        np.testing.assert_array_equal(oracle.caf(ss, sr, lag0, nlags, p0, nbins, flags=circ),
+                                      oracle.caf(ss, sr, red, nlags, p0, nbins, flags=circ))
+        np.testing.assert_array_equal(oracle.caf_adjoint(ss, sr, lag0, nlags, p0, nbins, gA, flags=circ),
+                                      oracle.caf_adjoint(ss, sr, red, nlags, p0, nbins, gA, flags=circ))
+        np.testing.assert_array_equal(oracle.caf_adjoint_ref(ss, sr, lag0, nlags, p0, nbins, gA, flags=circ),
+                                      oracle.caf_adjoint_ref(ss, sr, red, nlags, p0, nbins, gA, flags=circ))
+        assert np.any(oracle.caf(ss, sr, lag0, nlags, p0, nbins, flags=circ) != 0)
