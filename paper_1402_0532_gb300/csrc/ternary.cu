@@ -1251,22 +1251,21 @@ __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__rest
     }
 }
 
-// One problem: tile (x, y) = b mod gx, b / gx packs columns [32 x, 32 x + 32)
-// of K blocks [8 y, 8 y + 8), one 16-byte entry per thread and K block.  Block
-// b0 takes tiles b0, b0 + gridDim.x, ...: one tile per block on a full grid, or
-// a bounded grid that leaves room on every SM for a contraction CTA.
+// One problem: block (x, y) packs columns [32 x, 32 x + 32) of K blocks
+// [8 y', 8 y' + 8) for y' = y, y + gridDim.y, ... < gy, one 16-byte entry per
+// thread and K block, no division: one tile per block on a full grid, or a
+// grid bounded in y that leaves room on every SM for a contraction CTA.
 constexpr int kPackKb = 8;
 __global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags, bool caf,
                                                      const float2 *__restrict__ a_base,
                                                      const float2 *__restrict__ r_base, uint4 *__restrict__ B,
-                                                     int gx, int64_t ntiles) {
+                                                     int gy) {
     const int t = threadIdx.x & 7;
+    const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
+    if (col >= P.ncols) return;
     const float2 *a = a_base + P.a_off;
     const float2 *r = r_base + P.r_off;
-    for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
-        const int bx = (int)(b % gx), by = (int)(b / gx);
-        const int col = bx * 32 + (threadIdx.x >> 3);
-        if (col >= P.ncols) continue;
+    for (int by = blockIdx.y; by < gy; by += gridDim.y) {
         const int kb0 = by * kPackKb;
         const int kb1 = min(kb0 + kPackKb, P.kblocks);
 #pragma unroll 2
@@ -1425,20 +1424,20 @@ int choose_split(int64_t tiles, int kblocks, int sm, int tune, int64_t cap_units
     return std::max(1, std::min(s, std::max(1, kblocks / 4)));
 }
 
-// max_blocks > 0 bounds the single-problem grid (blocks then loop over tiles).
+// max_blocks > 0 bounds the single-problem grid to about that many blocks (its
+// y extent shrinks and the blocks loop over the K-block tiles).
 cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob, const PackProb &single,
                         int64_t rows, uint32_t flags, bool caf, const void *a_base, const void *r_base, void *B, int sm,
                         cudaStream_t s, int max_blocks = 0) {
     const int threads = 256;
     if (!probs) {
         const int gx = (single.ncols + 31) / 32;
-        const int64_t ntiles = (int64_t)gx * ((single.kblocks + kPackKb - 1) / kPackKb);
-        int64_t blocks = ntiles;
-        if (max_blocks > 0) blocks = std::min<int64_t>(blocks, max_blocks);
-        blocks = std::min<int64_t>(blocks, INT32_MAX);
-        k_pack_single<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, s>>>(
-            single, flags, caf, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base),
-            static_cast<uint4 *>(B), gx, ntiles);
+        const int gy = (single.kblocks + kPackKb - 1) / kPackKb;
+        int grid_y = std::min(gy, 65535);
+        if (max_blocks > 0) grid_y = std::max(1, std::min(grid_y, max_blocks / gx));
+        k_pack_single<<<dim3(gx, grid_y), threads, 0, s>>>(single, flags, caf, static_cast<const float2 *>(a_base),
+                                                           static_cast<const float2 *>(r_base),
+                                                           static_cast<uint4 *>(B), gy);
         return cudaGetLastError();
     }
     const int64_t want = (rows * 8 + threads - 1) / threads;
