@@ -15,7 +15,7 @@
  * The identity a (x) b = sgn(b) a + sgn(a) b is deliberately NOT used here;
  * the tests use it only as an independent cross-check.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   twiddles  W^m = exp(-j 2 pi m / N) with the angle reduced to a quadrant
  *             in integer arithmetic, so values on the axes are exact
  *             (cos = 0 exactly at m = N/4, 3N/4; sin = 0 at m = 0, N/2).
