@@ -43,7 +43,7 @@ extern "C" {
 typedef enum {
     NDFT_OK = 0,
     NDFT_E_INVALID = 1,      /* bad argument: null/misaligned pointer, size, combination */
-    NDFT_E_UNSUPPORTED = 2,  /* valid request this build does not provide */
+    NDFT_E_UNSUPPORTED = 2,  /* valid request the library does not provide */
     NDFT_E_CUDA = 3,         /* a CUDA runtime call or launch failed */
     NDFT_E_NOMEM = 4,        /* device allocation at plan time failed */
     NDFT_E_TIMEOUT = 5,      /* a bounded device-side wait ran out (see ndft_query_error) */

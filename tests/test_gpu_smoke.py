@@ -1,4 +1,4 @@
-"""The driver's smoke check (one small invocation of every form against the
+"""The smoke check (one small invocation of every form against the
 oracle) as part of the GPU suite, so it cannot break unnoticed."""
 import pytest
 
