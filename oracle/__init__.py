@@ -79,6 +79,7 @@ def _load():
             lib.oracle_nfft_f32.argtypes = [P, i64, i64, P]
             lib.oracle_nfft_dif.argtypes = [P, i64, i64, P]
             lib.oracle_nfft_dif_f32.argtypes = [P, i64, i64, P]
+            lib.oracle_nfft_bound.argtypes = [P, i64, i64, i32, P, P, P]
             lib.oracle_lagprod.argtypes = [P, P, i64, i64, u32, P]
             lib.oracle_lagprod_f32.argtypes = [P, P, i64, i64, u32, P]
             lib.oracle_caf.argtypes = [P, P, i64, i64, i64, i64, i64, u32, i32, P]
@@ -90,7 +91,7 @@ def _load():
             lib.oracle_caf_adjoint_at.argtypes = [P, P, i64, i64, i64, i64, i64, u32, P, i32, P, i64, P]
             lib.oracle_num_threads.restype = i32
             for name in ("oracle_ndft", "oracle_nfft", "oracle_nfft_f32", "oracle_nfft_dif",
-                         "oracle_nfft_dif_f32", "oracle_lagprod",
+                         "oracle_nfft_dif_f32", "oracle_nfft_bound", "oracle_lagprod",
                          "oracle_lagprod_f32", "oracle_caf", "oracle_caf_cells", "oracle_ndft_q14",
                          "oracle_caf_q14", "oracle_caf_adjoint", "oracle_caf_adjoint_ref",
                          "oracle_caf_adjoint_at"):
@@ -202,6 +203,33 @@ def nfft_f32(x, dif: bool = False) -> np.ndarray:
     fn = _load().oracle_nfft_dif_f32 if dif else _load().oracle_nfft_f32
     _check(fn(_ptr(x), B, N, _ptr(X)), "nfft_f32")
     return X
+
+
+def nfft_bound(x, dif: bool = False):
+    """Sec. 3 recursion in fp64 with a running error bound for an fp32
+    evaluation of the same recursion: returns (X, bound, stable).  X equals
+    ``nfft(x, dif)``; bound[b, k] holds the bounds of the Re and Im parts as
+    the real and imaginary parts of one complex number; stable[b] is True when
+    every data operand of every (x) of vector b keeps its fp64 sign in fp32,
+    in which case |Re/Im (X32 - X)| <= Re/Im bound.  x must be representable
+    in fp32 (complex64 values)."""
+    x = np.ascontiguousarray(x, np.complex64).astype(np.complex128)
+    if x.ndim == 1:
+        X, b, s = nfft_bound(x[None], dif)
+        return X[0], b[0], s[0]
+    B, N = x.shape
+    X = np.zeros((B, N), np.complex128)
+    bound = np.zeros((B, N), np.complex128)
+    stable = np.zeros(B, np.int32)
+    _check(_load().oracle_nfft_bound(_ptr(x), B, N, 1 if dif else 0, _ptr(X), _ptr(bound), _ptr(stable)),
+           "nfft_bound")
+    return X, bound, stable.astype(bool)
+
+
+def within_bound(got, want, bound) -> np.ndarray:
+    """Elementwise |Re/Im (got - want)| <= Re/Im bound."""
+    d = np.asarray(got, np.complex128) - want
+    return (np.abs(d.real) <= bound.real) & (np.abs(d.imag) <= bound.imag)
 
 
 def dft(x, p0: int = 0, nbins: int | None = None) -> np.ndarray:

@@ -405,6 +405,155 @@ int oracle_nfft_dif_f32(const float *x, int64_t batch, int64_t N, float *X) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Conditioning of the NFFT (Sec. 3, either order) in fp32.  (x) jumps where */
+/* an operand crosses zero, so an fp32 evaluation of the recursion stays     */
+/* close to the fp64 one only while every data operand of every (x) keeps    */
+/* its fp64 sign.  This evaluates the fp64 recursion (the same values as     */
+/* oracle_nfft / oracle_nfft_dif) and beside each value a bound on how far   */
+/* an fp32 evaluation of it (fp32 twiddles, one rounding per (x) and per     */
+/* addition) can be from it, by running error analysis: with u = 2^-24,      */
+/*   input (fp32 data)                     e = 0                            */
+/*   twiddle component w                   e = u |w|                        */
+/*   real a (x) b, both signs kept         e = (e_a + e_b)(1 + u) + u' |r|   */
+/*   c = a +- b                            e = (e_a + e_b)(1 + u) + u' |c|   */
+/* (u' = u + 2^-52 also covers the rounding of the fp64 value itself).  A    */
+/* data operand v keeps its sign in fp32 if |v| > e_v, or v = 0 with e_v = 0;*/
+/* stable[b] = 1 if that holds for every (x) of vector b, and then           */
+/* |X32 - X64| <= bound elementwise (per component).                         */
+/* ------------------------------------------------------------------------ */
+#define U32 5.9604644775390625e-08 /* 2^-24 */
+#define U32P (5.9604644775390625e-08 + 2.220446049250313e-16)
+
+static int keeps_sign(double v, double e) { return fabs(v) > e || (v == 0.0 && e == 0.0); }
+
+/* real (x) with the twiddle component w (sign exact in fp32) and the data
+ * operand v: value and bound; clears *ok when v may change sign */
+static double ox_bound(double w, double v, double ev, double *e, int *ok) {
+    if (!keeps_sign(v, ev)) *ok = 0;
+    double r = oracle_otimes(w, v);
+    /* an exact zero on either side gives exactly 0 in fp32 as well */
+    *e = (w == 0.0 || (v == 0.0 && ev == 0.0)) ? 0.0 : (U32 * fabs(w) + ev) * (1.0 + U32) + U32P * fabs(r);
+    return r;
+}
+
+/* complex W (x) v with bounds, Eq. 6 in the operand order of cot64 */
+static void cot_bound(double wr, double wi, double vr, double vi, double evr, double evi, double *cr,
+                      double *ci, double *ecr, double *eci, int *ok) {
+    double e1, e2, e3, e4;
+    double t1 = ox_bound(wr, vr, evr, &e1, ok);
+    double t2 = ox_bound(wi, vi, evi, &e2, ok);
+    double t3 = ox_bound(wi, vr, evr, &e3, ok);
+    double t4 = ox_bound(wr, vi, evi, &e4, ok); /* vi (x) wr: (x) commutes exactly */
+    *cr = t1 - t2;
+    *ci = t3 + t4;
+    *ecr = (e1 + e2) * (1.0 + U32) + U32P * fabs(*cr);
+    *eci = (e3 + e4) * (1.0 + U32) + U32P * fabs(*ci);
+}
+
+static double add_bound(double c, double ea, double eb) { return (ea + eb) * (1.0 + U32) + U32P * fabs(c); }
+
+/* values v[2n] and bounds e[2n] (Re, Im interleaved in both) */
+static void nfft_bnd_dit(const double *x, const double *ex, int64_t n, int64_t stride, const double *W,
+                         int64_t Nfull, double *out, double *eout, double *scr, int *ok) {
+    if (n == 1) {
+        out[0] = x[0];
+        out[1] = x[1];
+        eout[0] = ex[0];
+        eout[1] = ex[1];
+        return;
+    }
+    int64_t h = n / 2;
+    double *E = scr, *O = scr + 2 * h, *eE = scr + 2 * n, *eO = eE + 2 * h, *sub = scr + 4 * n;
+    nfft_bnd_dit(x, ex, h, 2 * stride, W, Nfull, E, eE, sub, ok);
+    nfft_bnd_dit(x + 2 * stride, ex + 2 * stride, h, 2 * stride, W, Nfull, O, eO, sub, ok);
+    int64_t step = Nfull / n;
+    for (int64_t k = 0; k < h; ++k) {
+        double tr, ti, etr, eti;
+        cot_bound(W[2 * k * step], W[2 * k * step + 1], O[2 * k], O[2 * k + 1], eO[2 * k], eO[2 * k + 1], &tr,
+                  &ti, &etr, &eti, ok);
+        out[2 * k] = E[2 * k] + tr;
+        out[2 * k + 1] = E[2 * k + 1] + ti;
+        out[2 * (k + h)] = E[2 * k] - tr;
+        out[2 * (k + h) + 1] = E[2 * k + 1] - ti;
+        eout[2 * k] = add_bound(out[2 * k], eE[2 * k], etr);
+        eout[2 * k + 1] = add_bound(out[2 * k + 1], eE[2 * k + 1], eti);
+        eout[2 * (k + h)] = add_bound(out[2 * (k + h)], eE[2 * k], etr);
+        eout[2 * (k + h) + 1] = add_bound(out[2 * (k + h) + 1], eE[2 * k + 1], eti);
+    }
+}
+
+static void nfft_bnd_dif(const double *x, const double *ex, int64_t n, const double *W, int64_t Nfull,
+                         double *out, double *eout, double *scr, int *ok) {
+    if (n == 1) {
+        out[0] = x[0];
+        out[1] = x[1];
+        eout[0] = ex[0];
+        eout[1] = ex[1];
+        return;
+    }
+    int64_t h = n / 2, step = Nfull / n;
+    double *Y = scr, *Z = scr + 2 * h, *YY = scr + 2 * n, *ZZ = YY + 2 * h;
+    double *eY = scr + 4 * n, *eZ = eY + 2 * h, *eYY = scr + 6 * n, *eZZ = eYY + 2 * h, *sub = scr + 8 * n;
+    for (int64_t m = 0; m < h; ++m) {
+        double ar = x[2 * m], ai = x[2 * m + 1], br = x[2 * (m + h)], bi = x[2 * (m + h) + 1];
+        Y[2 * m] = ar + br;
+        Y[2 * m + 1] = ai + bi;
+        eY[2 * m] = add_bound(Y[2 * m], ex[2 * m], ex[2 * (m + h)]);
+        eY[2 * m + 1] = add_bound(Y[2 * m + 1], ex[2 * m + 1], ex[2 * (m + h) + 1]);
+        double dr = ar - br, di = ai - bi;
+        double edr = add_bound(dr, ex[2 * m], ex[2 * (m + h)]);
+        double edi = add_bound(di, ex[2 * m + 1], ex[2 * (m + h) + 1]);
+        cot_bound(W[2 * m * step], W[2 * m * step + 1], dr, di, edr, edi, &Z[2 * m], &Z[2 * m + 1], &eZ[2 * m],
+                  &eZ[2 * m + 1], ok);
+    }
+    nfft_bnd_dif(Y, eY, h, W, Nfull, YY, eYY, sub, ok);
+    nfft_bnd_dif(Z, eZ, h, W, Nfull, ZZ, eZZ, sub, ok);
+    for (int64_t k = 0; k < h; ++k) {
+        out[4 * k] = YY[2 * k];
+        out[4 * k + 1] = YY[2 * k + 1];
+        out[4 * k + 2] = ZZ[2 * k];
+        out[4 * k + 3] = ZZ[2 * k + 1];
+        eout[4 * k] = eYY[2 * k];
+        eout[4 * k + 1] = eYY[2 * k + 1];
+        eout[4 * k + 2] = eZZ[2 * k];
+        eout[4 * k + 3] = eZZ[2 * k + 1];
+    }
+}
+
+/* x: [batch][N] complex (values representable in fp32); X and bound: [batch][N]
+ * complex-interleaved; stable: [batch] */
+int oracle_nfft_bound(const double *x, int64_t batch, int64_t N, int dif, double *X, double *bound,
+                      int32_t *stable) {
+    if (!is_pow2(N) || batch < 0) return 1;
+    double *W = twiddle_table64(N);
+    if (!W) return 2;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *scr = (double *)malloc(sizeof(double) * (20 * (size_t)N + 64));
+        double *ex = (double *)calloc(2 * (size_t)N, sizeof(double));
+        if (!scr || !ex) {
+#pragma omp atomic write
+            err = 2;
+        } else {
+#pragma omp for schedule(dynamic)
+            for (int64_t b = 0; b < batch; ++b) {
+                int ok = 1;
+                if (dif)
+                    nfft_bnd_dif(x + 2 * b * N, ex, N, W, N, X + 2 * b * N, bound + 2 * b * N, scr, &ok);
+                else
+                    nfft_bnd_dit(x + 2 * b * N, ex, N, 1, W, N, X + 2 * b * N, bound + 2 * b * N, scr, &ok);
+                stable[b] = ok;
+            }
+        }
+        free(scr);
+        free(ex);
+    }
+    free(W);
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Lag product of Eq. 12a: z_l[i] = s_surv[i] (x) conj(s_ref[i - l]).        */
 /* ------------------------------------------------------------------------ */
 static int64_t ref_index(int64_t i, int64_t l, int64_t N, uint32_t flags) {

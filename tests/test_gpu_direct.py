@@ -31,6 +31,19 @@ def relerr(got, ref):
     return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
 
 
+def check_nfft_vs_fp64(got, x, dif):
+    """The NFFT gate against fp64: every sign-stable vector within the running
+    error bound of the fp64 recursion and within TOL of its max |X|; returns
+    the number of vectors left out as ill-conditioned (and prints it)."""
+    X, bound, stable = oracle.nfft_bound(x, dif=dif)
+    amax = np.maximum(np.abs(X).max(axis=1), 1e-30)
+    if stable.any():
+        assert oracle.within_bound(got[stable], X[stable], bound[stable]).all()
+        assert (np.abs(got - X).max(axis=1) / amax)[stable].max() < TOL
+    print(f"NFFT N={x.shape[1]} dif={dif}: {int((~stable).sum())} of {len(stable)} vectors ill-conditioned")
+    return int((~stable).sum())
+
+
 # --------------------------------------------------------------------------------
 # tables
 # --------------------------------------------------------------------------------
@@ -124,11 +137,13 @@ def test_nfft_bit_exact(api, N, batch):
     t = dev(x)
     p.nfft(t, out=t)
     assert np.array_equal(t.cpu().numpy().view(np.uint32), want.view(np.uint32))
-    # and within fp32 rounding of the fp64 recursion on well-conditioned rows
-    if N <= 1024:
-        ref = oracle.nfft(x.astype(np.complex128))
-        rows = [2] + list(range(5, batch)) if batch > 4 else list(range(2, batch))
-        assert relerr(got[rows], ref[rows]) < 1e-3
+    # against the fp64 recursion: on the vectors whose every (x) data operand
+    # provably keeps its fp64 sign in fp32 (the oracle's running error bound),
+    # within that bound and within the 1e-5 bar; the others are counted and
+    # reported, not failed ((x) jumps at zero, so there fp32 and fp64 may
+    # legitimately part)
+    if N <= 4096:
+        check_nfft_vs_fp64(got, x, dif=False)
 
 
 def test_nfft_hand_cases(api):

@@ -61,6 +61,13 @@ def test_nfft_dif_bit_exact(api, N, batch):
     t = dev(x)
     p.nfft(t, out=t)  # in place
     assert same_bits(t.cpu().numpy(), want)
+    # against the fp64 DIF recursion on sign-stable vectors (running error bound)
+    if N <= 4096:
+        X, bound, stable = oracle.nfft_bound(x, dif=True)
+        if stable.any():
+            assert oracle.within_bound(got[stable], X[stable], bound[stable]).all()
+            amax = np.maximum(np.abs(X).max(axis=1), 1e-30)
+            assert (np.abs(got - X).max(axis=1) / amax)[stable].max() < 1e-5
 
 
 @pytest.mark.parametrize("N,lag0,nlags,p0,nbins", [(8, -3, 12, 0, 0), (1024, -5, 33, -512, 1024),

@@ -42,6 +42,15 @@ def test_nfft_full_batch_bit_exact(api, batch):
     p.query_error()
     want = oracle.nfft_f32(batch)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    # every vector whose (x) operands provably keep their fp64 signs in fp32:
+    # within the running error bound of the fp64 recursion and within 1e-5 of
+    # its max |X|; the rest are counted as ill-conditioned
+    X, bound, stable = oracle.nfft_bound(batch)
+    assert stable.mean() > 0.9
+    assert oracle.within_bound(got[stable], X[stable], bound[stable]).all()
+    amax = np.abs(X).max(axis=1)
+    assert (np.abs(got - X).max(axis=1) / amax)[stable].max() < TOL
+    print(f"NFFT 65536 x 1024: {int((~stable).sum())} vectors ill-conditioned")
 
 
 @pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2")])

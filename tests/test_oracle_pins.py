@@ -403,6 +403,45 @@ def test_nfft_dif_literal_and_impulse(oracle):
     np.testing.assert_array_equal(oracle.nfft_f32(xi, dif=True), oracle.nfft(xi, dif=True).astype(np.complex64))
 
 
+def test_nfft_f32_both_orders_exact_at_n4(oracle):
+    """N = 4: the twiddles are W^0 = 1 and W^1 = -j, so with small-integer data
+    every intermediate of either order is an exact small integer and the fp32
+    evaluation must equal the fp64 one bit for bit.  This reaches the DIF
+    difference branch through a non-trivial twiddle and the even/odd output
+    interleave, which N = 2 cannot."""
+    rng = np.random.default_rng(29)
+    x = (rng.integers(-20, 21, (64, 4)) + 1j * rng.integers(-20, 21, (64, 4))).astype(np.complex64)
+    x[0] = 0
+    x[1, 1::2] = 0
+    for dif in (False, True):
+        np.testing.assert_array_equal(oracle.nfft_f32(x, dif=dif),
+                                      oracle.nfft(x.astype(complex), dif=dif).astype(np.complex64))
+    # the two orders are different transforms already at N = 4
+    assert not np.array_equal(oracle.nfft(x[2:], dif=True), oracle.nfft(x[2:]))
+
+
+@pytest.mark.parametrize("N", [8, 256, 1024])
+@pytest.mark.parametrize("dif", [False, True])
+def test_nfft_f32_within_running_error_bound(oracle, N, dif):
+    """The fp32 recursion (either order) against the fp64 one, which the
+    literal recursion pins for N <= 16.  (x) jumps at zero, so fp32 can only
+    track fp64 while every data operand keeps its sign; the oracle's running
+    error analysis marks those vectors (stable) and bounds |X32 - X64| per
+    component.  A wrong twiddle index, a swapped difference or a wrong output
+    interleave in either recursion moves bins by O(1) and fails the bound."""
+    rng = np.random.default_rng(31 + N)
+    x = scenes.cn(rng, (200, N)).astype(np.complex64)
+    X, bound, stable = oracle.nfft_bound(x, dif=dif)
+    np.testing.assert_array_equal(X, oracle.nfft(x.astype(complex), dif=dif))  # same fp64 values
+    assert stable.mean() >= 0.9
+    X32 = oracle.nfft_f32(x, dif=dif)
+    assert oracle.within_bound(X32[stable], X[stable], bound[stable]).all()
+    rel = np.abs(X32 - X).max(axis=1) / np.abs(X).max(axis=1)
+    assert rel[stable].max() < 1e-5
+    # the bound is tight enough to mean something: well under 1e-3 of max|X|
+    assert np.median(np.maximum(bound.real, bound.imag).max(axis=1) / np.abs(X).max(axis=1)) < 1e-4
+
+
 def test_caf_12b_literal_and_parseval(oracle):
     """Eq. 12b: the literal DFT sum of the literal (x) lag product; Parseval
     (sum_p |A[l,p]|^2 = N sum_i |z_l[i]|^2 over all N bins) on a larger case; and
