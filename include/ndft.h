@@ -261,8 +261,26 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * call's stream, so stream order and CUDA-graph capture are unaffected); a
  * multiple of 256 = two parts, the first of that many columns.  Two parts
  * shorten short bursts of calls by about 1 % but lengthen long runs at the
- * power limit by about 3 % (measured on the 65536-sample, 1024 x 1024 surface). */
+ * power limit by about 3 % (measured on the 65536-sample, 1024 x 1024 surface).
+ * Key 6 = ternary-GEMM conjugate pairing: 0 (default) contracts bins +c and -c
+ * together wherever that takes fewer tensor-core steps (W^(-c i) =
+ * conj(W^(c i)), Eq. 8, so both bins come from one pair of real contractions
+ * U = S_r v + F_r sigma(v), V = S_i v + F_i sigma(v): X[+c] = U + jV,
+ * X[-c] = U - jV, half the multiply-adds per bin; bin 0 is summed by the
+ * packing kernel); 1 = never; 2 = wherever the window allows it.  Pairing is
+ * used with the default tile and one column part only.  Same bar, different
+ * fp32 rounding. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
+
+/* Read-only facts about a plan and its last exec call, into *value:
+ * key 0 = S, the largest frequency min(p, N - p) of the bin window (ternary
+ *         plans; the paired contraction has rows for frequencies 1 .. S);
+ * key 1 = the contraction variant of the last exec call: 0 none or not a
+ *         tensor-core call, 1 one row pair per bin, 2 conjugate-paired rows;
+ * key 2 = the sample-axis split count of the last exec call's contraction
+ *         (0 if none).
+ * NDFT_E_INVALID for another key or a NULL argument. */
+ndft_status ndft_plan_query(ndft_plan_t plan, int32_t key, int64_t *value);
 
 /* Device timing of the plan's main contraction kernel (the tensor-core GEMM,
  * the direct tile kernel, the NFFT or the adjoint kernel).  ndft_timer_start

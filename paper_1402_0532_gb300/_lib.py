@@ -20,7 +20,7 @@ F_NO_CONJ_REF, F_CIRCULAR_LAG, F_NFFT_DIF = 0x1, 0x2, 0x4
 EXPORTS = ("ndft_plan", "ndft_plan_batched", "ndft_plan_destroy", "ndft_exec", "nfft_exec", "caf_exec",
            "caf_exec_batched", "caf_backward", "caf_backward_inputs", "ndft_argmax", "ndft_query_error", "ndft_get_twiddles",
            "ndft_plan_bytes", "ndft_last_launches", "ndft_set_tuning", "ndft_timer_start", "ndft_timer_read",
-           "ndft_status_string", "ndft_version", "ndft_last_cuda_error", "caf_exec_noalloc")
+           "ndft_status_string", "ndft_version", "ndft_last_cuda_error", "caf_exec_noalloc", "ndft_plan_query")
 
 
 class NdftDesc(ctypes.Structure):
@@ -73,6 +73,7 @@ def load() -> ctypes.CDLL:
         "ndft_plan_bytes": (i32, [P, ctypes.POINTER(i64)]),
         "ndft_last_launches": (i32, [P, ctypes.POINTER(i32)]),
         "ndft_set_tuning": (i32, [P, i32, i32]),
+        "ndft_plan_query": (i32, [P, i32, ctypes.POINTER(i64)]),
         "ndft_timer_start": (i32, [P, i32]),
         "ndft_timer_read": (i32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]),
         "ndft_status_string": (ctypes.c_char_p, [i32]),

@@ -102,6 +102,14 @@ class Plan:
         L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
         self._tuning[int(key)] = int(value)
 
+    def query(self, key: int) -> int:
+        """ndft_plan_query: 0 = paired frequencies S of the window, 1 = last call's
+        contraction variant (0 none, 1 unpaired rows, 2 conjugate-paired rows),
+        2 = last call's sample-axis split count."""
+        v = ctypes.c_int64()
+        L.check(self.lib.ndft_plan_query(self.handle, int(key), ctypes.byref(v)), "ndft_plan_query")
+        return v.value
+
     def twin(self) -> "Plan":
         """A second plan with this plan's descriptor and tuning settings and its own
         tables and workspace: same results bit for bit, and the two can run at once on

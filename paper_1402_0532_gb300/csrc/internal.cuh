@@ -69,11 +69,16 @@ struct Plan {
     int tune_drain = 0;          // ternary form: 0 bulk tensor stores/adds, 1 per-element adds
     int test_starve = 0;         // ternary form, tests only: issue no operand loads (waits run out)
     int tune_parts = 1;          // ternary form: 1 one part (default); 0 two parts, half each; else part 0's columns
+    int tune_pair = 0;           // ternary form: 0 conjugate-paired rows where they save work (default), 1 never
+    int pair_slots = 0;          // ternary form: frequencies 1 .. pair_slots cover the bin window (0: none)
+    size_t dc_bytes = 0;         // ternary form: per-tile DC sums of the paired packing
     // ternary form: side stream and events of the two-part contraction (the
     // second part's packing runs under the first part's contraction)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int last_launches = 0;
+    int last_variant = 0;        // contraction of the last exec call: 0 none, 1 unpaired rows, 2 paired rows
+    int last_nsplit = 0;         // its sample-axis split count
     // optional timing of the main contraction kernel (event pairs, see ndft_timer_start)
     mutable cudaEvent_t *tev = nullptr;
     mutable int tcap = 0;

@@ -300,6 +300,20 @@ __device__ __forceinline__ void gen_pair_w(uint32_t u, uint32_t N, float2 W, uin
     im = make_uint4(si, sr, wi, wr);
 }
 
+// Conjugate-paired form: the K entries of one (frequency c, sample i) for the
+// R row ([S_r, S_r, F_hi_r, F_lo_r]) and the I row ([S_i, S_i, F_hi_i,
+// F_lo_i]), as two 32-bit words each (signs, then the bf16 hi + lo of F).
+__device__ __forceinline__ void gen_conj_words(uint32_t u, uint32_t N, float2 W, uint32_t &sr, uint32_t &si,
+                                               uint32_t &wr, uint32_t &wi) {
+    sign_bits(u, N, sr, si);
+    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(W.x, W.y);
+    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(W.x - __low2float(hi2), W.y - __high2float(hi2));
+    const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi2);
+    const uint32_t ul = *reinterpret_cast<const uint32_t *>(&lo2);
+    wr = __byte_perm(uh, ul, 0x5410);  // [F_hi_r, F_lo_r]
+    wi = __byte_perm(uh, ul, 0x7632);  // [F_hi_i, F_lo_i]
+}
+
 // W <- W * R (fp32 complex product)
 __device__ __forceinline__ float2 cmul_f2(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
@@ -354,12 +368,13 @@ struct Tile {
 // ADJ selects the adjoint contractions (rows = samples, columns = lags, K =
 // bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
 // forward epilogue on a [lags][2N] fp32 output).
-template <int MH, bool BT, int ADJ>
+template <int MH, bool BT, int ADJ, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
                    int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
     static_assert(ADJ == 0 || (MH == 2 && !BT), "the adjoint runs on the 256-row tile");
+    static_assert(!PAIR || (MH == 2 && !BT && ADJ == 0), "the conjugate-paired form runs on the 256-row tile");
     using T = Tile<MH>;
     constexpr int STG = T::kStages;
     constexpr int NB = T::kBufs;
@@ -548,6 +563,73 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ub[j] += dd[j];
                         if (ub[j] >= 4u * N) ub[j] -= 4u * N;
                     }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[stage]);
+                    if (++stage == STG) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        } else if constexpr (PAIR) {
+            // Conjugate-paired rows: slot k of the unit is the frequency
+            // c = p0 + k (p0 = the first paired frequency); its R row (2 k) and
+            // I row (2 k + 1) hold, per sample, [S_r, S_r, F_hi_r, F_lo_r] and
+            // [S_i, S_i, F_hi_i, F_lo_i] of F = W^(c i).  A K block is 16
+            // samples; thread (pg, t) makes slots pg + 32 j, samples 2 t and
+            // 2 t + 1 of it, each twiddle advanced by W^(16 c) per K block and
+            // re-seeded from the table every kReseed blocks.
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
+                gen_bar();  // every producer is done with the previous table
+                for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
+                    const float2 v = w.P.ang[e];
+                    if (e < w.P.nth) s_thi[e] = v;
+                    else s_tlo[e - w.P.nth] = v;
+                }
+                gen_bar();
+                if (!ok) continue;
+                const uint32_t N = (uint32_t)w.P.N;
+                const uint32_t thi = smem_u32(s_thi), tlo = smem_u32(s_tlo);
+                uint32_t ua[4], ub[4], dd[4];
+                float2 wa[4], wb[4], rot[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = w.mt * 128 + pg + 32 * j;  // slot
+                    int64_t c = ((int64_t)w.P.p0 + k) % (int64_t)N;
+                    if (c < 0) c += N;
+                    const int64_t i0 = (int64_t)w.kb0 * 16 + 2 * t;
+                    ua[j] = 4u * (uint32_t)((c * (i0 % (int64_t)N)) % (int64_t)N);
+                    ub[j] = 4u * (uint32_t)((c * ((i0 + 1) % (int64_t)N)) % (int64_t)N);
+                    dd[j] = 4u * (uint32_t)((16 * c) % (int64_t)N);
+                    rot[j] = tw_table(dd[j], N, thi, tlo);  // W^(16 c)
+                }
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                    const uint32_t a_st = a_base + stage * T::kABytes;
+                    const bool seed = ((kb - w.kb0) % kReseed) == 0;
+                    uint4 vre[4], vim[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (seed) {
+                            wa[j] = tw_table(ua[j], N, thi, tlo);
+                            wb[j] = tw_table(ub[j], N, thi, tlo);
+                        }
+                        uint32_t sra, sia, wra, wia, srb, sib, wrb, wib;
+                        gen_conj_words(ua[j], N, wa[j], sra, sia, wra, wia);
+                        gen_conj_words(ub[j], N, wb[j], srb, sib, wrb, wib);
+                        vre[j] = make_uint4(sra, wra, srb, wrb);
+                        vim[j] = make_uint4(sia, wia, sib, wib);
+                        wa[j] = cmul_f2(wa[j], rot[j]);
+                        wb[j] = cmul_f2(wb[j], rot[j]);
+                        ua[j] += dd[j];
+                        if (ua[j] >= 4u * N) ua[j] -= 4u * N;
+                        ub[j] += dd[j];
+                        if (ub[j] >= 4u * N) ub[j] -= 4u * N;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) store_pair(a_st, pg + 32 * j, t, vre[j], vim[j]);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&full[stage]);
@@ -1340,6 +1422,134 @@ __global__ void __launch_bounds__(256) k_pack_adjoint(const float2 *__restrict__
     }
 }
 
+// ---- conjugate-paired form: packing and fold --------------------------------------
+// With F[-p][i] = conj(F[p][i]) and sigma(conj w) = conj(sigma(w)) (Eq. 8 and
+// the sign cases of Eq. 2), bins +c and -c share U = S_r v + F_r sigma(v) and
+// V = S_i v + F_i sigma(v) (real matrices times the complex v):
+//     X[+c] = U + j V,   X[-c] = U - j V.
+// As one real GEMM: row R of frequency c pairs [S_r, S_r, F_hi_r, F_lo_r] and
+// row I [S_i, S_i, F_hi_i, F_lo_i] per sample with two B columns per input
+// column, (col, r) = [v_hi_r, v_lo_r, s_r, s_r] and (col, i) = [v_hi_i,
+// v_lo_i, s_i, s_i]; the four results per (c, col) are
+//     a = R.(col, r) = Re U,  d = R.(col, i) = Im U,
+//     e = I.(col, r) = Re V,  b = I.(col, i) = Im V,
+// so X[+c] = (a - b) + j (d + e) and X[-c] = (a + b) + j (d - e).  Half the
+// multiply-adds of the unpaired rows per output bin.  c = 0 (W = 1) needs
+// no GEMM row: X[0] = sum_i (v + sigma(v)) is summed by the packing kernel.
+//
+// B row (kb, 2 col + comp) holds samples 16 kb .. 16 kb + 15 of component comp
+// of column col, 4 bf16 each.  Thread t of a column's 8 packs samples 2 t and
+// 2 t + 1 of each K block into both rows and adds v + sigma(v) of them to the
+// column's DC sum; the 8 partial sums of a column are combined in a fixed
+// order and written per K-block tile (dc[tile][col]).
+constexpr int kPairPackKb = 16;  // K blocks (16 samples each) per packing tile
+
+__device__ __forceinline__ uint32_t bf16_hilo(float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+}
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+__device__ __forceinline__ uint32_t sign2(float v) {
+    return v > 0.f ? 0x3F803F80u : (v < 0.f ? 0xBF80BF80u : 0u);
+}
+
+__global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, bool caf,
+                                                   const float2 *__restrict__ a_base,
+                                                   const float2 *__restrict__ r_base, uint4 *__restrict__ B,
+                                                   float2 *__restrict__ dc, int gy) {
+    const int t = threadIdx.x & 7;
+    const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
+    const bool live = col < P.ncols;  // whole 8-lane groups are live or not
+    const float2 *a = a_base + P.a_off;
+    const float2 *r = r_base + P.r_off;
+    const int64_t ncols2 = 2LL * P.ncols;
+    for (int by = blockIdx.y; by < gy; by += gridDim.y) {
+        const int kb0 = by * kPairPackKb;
+        const int kb1 = min(kb0 + kPairPackKb, P.kblocks);
+        float sr = 0.f, si = 0.f;
+        if (live) {
+            for (int kb = kb0; kb < kb1; ++kb) {
+                const int64_t i = (int64_t)kb * 16 + 2 * t;
+                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+                if (caf) {
+                    if (i < P.N) v0 = lag_product(P, a, r, col, i, flags);
+                    if (i + 1 < P.N) v1 = lag_product(P, a, r, col, i + 1, flags);
+                } else {
+                    const float2 *x = a + (int64_t)col * P.ldx;
+                    if (i < P.N) v0 = x[i];
+                    if (i + 1 < P.N) v1 = x[i + 1];
+                }
+                const int64_t row = P.row0 + (int64_t)kb * ncols2 + 2LL * col;
+                B[row * 8 + t] = make_uint4(bf16_hilo(v0.x), sign2(v0.x), bf16_hilo(v1.x), sign2(v1.x));
+                B[(row + 1) * 8 + t] = make_uint4(bf16_hilo(v0.y), sign2(v0.y), bf16_hilo(v1.y), sign2(v1.y));
+                sr += (v0.x + sgnf(v0.x)) + (v1.x + sgnf(v1.x));
+                si += (v0.y + sgnf(v0.y)) + (v1.y + sgnf(v1.y));
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (live && t == 0 && dc) dc[(int64_t)by * P.ncols + col] = make_float2(sr, si);
+    }
+}
+
+// Split-K sum and pair fold into the output [cols][nbins]: block x = output
+// column, its threads over the bins.  Bin p0 + k of the window is frequency
+// c = min(p, N - p), p = (p0 + k) mod N: c = 0 from the DC tiles; else slot
+// c - 1 of the partials [split][2 cols][2 S] (rows 2 s, 2 s + 1 = R, I;
+// columns 2 col, 2 col + 1 = r, i), each of a, b, d, e summed over the
+// splits in order, then combined for the sign of the bin.  Deterministic.
+__global__ void __launch_bounds__(256) k_pair_fold(const float *__restrict__ part, int nsplit, int64_t split_stride,
+                                                   int S, int N, int p0, int nbins, const float2 *__restrict__ dc,
+                                                   int gy, int ncols, float2 *__restrict__ out) {
+    const int col = blockIdx.x;
+    const int64_t S2 = 2LL * S;
+    const float *pr = part + (int64_t)(2 * col) * S2;      // column (col, r)
+    const float *pi = part + (int64_t)(2 * col + 1) * S2;  // column (col, i)
+    float2 *o = out + (int64_t)col * nbins;
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) {
+        int64_t p = ((int64_t)p0 + k) % N;
+        if (p < 0) p += N;
+        const int64_t c = p <= N - p ? p : N - p;
+        if (c == 0) continue;
+        const int64_t s = c - 1;
+        float2 ae = *reinterpret_cast<const float2 *>(pr + 2 * s);  // (a, e)
+        float2 db = *reinterpret_cast<const float2 *>(pi + 2 * s);  // (d, b)
+        for (int sp = 1; sp < nsplit; ++sp) {
+            const float2 u = *reinterpret_cast<const float2 *>(pr + sp * split_stride + 2 * s);
+            const float2 v = *reinterpret_cast<const float2 *>(pi + sp * split_stride + 2 * s);
+            ae.x = __fadd_rn(ae.x, u.x);
+            ae.y = __fadd_rn(ae.y, u.y);
+            db.x = __fadd_rn(db.x, v.x);
+            db.y = __fadd_rn(db.y, v.y);
+        }
+        o[k] = p == c ? make_float2(__fsub_rn(ae.x, db.y), __fadd_rn(db.x, ae.y))
+                      : make_float2(__fadd_rn(ae.x, db.y), __fsub_rn(db.x, ae.y));
+    }
+    // bin 0 (if in the window): the DC tiles in a fixed order, warp 0
+    if (threadIdx.x < 32) {
+        int64_t k0 = (-(int64_t)p0) % N;
+        if (k0 < 0) k0 += N;
+        if (k0 < nbins) {
+            float sr = 0.f, si = 0.f;
+            for (int g = threadIdx.x; g < gy; g += 32) {
+                const float2 v = dc[(int64_t)g * ncols + col];
+                sr = __fadd_rn(sr, v.x);
+                si = __fadd_rn(si, v.y);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                sr = __fadd_rn(sr, __shfl_xor_sync(0xffffffffu, sr, off));
+                si = __fadd_rn(si, __shfl_xor_sync(0xffffffffu, si, off));
+            }
+            if (threadIdx.x == 0) o[k0] = make_float2(sr, si);
+        }
+    }
+}
+
 // Two-level angle table: entry j < nth is (cos, sin)((pi/2) 256 j / N), entry
 // nth + j (j < 256) is (cos, sin)((pi/2) j / N); fp64, rounded to fp32.
 __global__ void k_angles(int N, int nth, float2 *__restrict__ ang) {
@@ -1448,11 +1658,11 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH, bool BT = false, int ADJ = 0>
+template <int MH, bool BT = false, int ADJ = 0, bool PAIR = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = Tile<MH>::kSmemTotal;
-    auto kern = k_ternary_gemm<MH, BT, ADJ>;
+    auto kern = k_ternary_gemm<MH, BT, ADJ, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
@@ -1512,16 +1722,35 @@ struct TernLayout {
     int64_t b_rows;
     size_t b_bytes;
     size_t part_bytes;
+    size_t dc_bytes;  // paired form: DC sums per packing tile and column
 };
+
+int pair_kblocks(int N) { return (N + 15) / 16; }
+int pair_pack_tiles(int N) { return (pair_kblocks(N) + kPairPackKb - 1) / kPairPackKb; }
 
 TernLayout layout_for(const ndft_desc &d, int sm) {
     TernLayout L;
     L.kblocks = (d.n + 7) / 8;
     const int cols = max_cols(d);
-    L.b_rows = (int64_t)L.kblocks * cols;
+    // the unpaired layout (8 samples x 8 entries per row, one row per column)
+    // or the paired one (16 samples x 4 entries, two rows per column)
+    L.b_rows = std::max<int64_t>((int64_t)L.kblocks * cols, (int64_t)pair_kblocks(d.n) * 2 * cols);
     L.b_bytes = (size_t)L.b_rows * 128;
     L.part_bytes = (size_t)4 * sm * 256 * TN * sizeof(float);  // 4 waves of 256 x 256 partial tiles
+    L.dc_bytes = ((size_t)pair_pack_tiles(d.n) * cols * sizeof(float2) + 255) / 256 * 256;
     return L;
+}
+
+// Frequencies 1 .. S that the bin window p0 .. p0 + nbins - 1 (mod N) folds
+// onto, c(p) = min(p, N - p); S = max c over the window.
+int pair_slots_for(int N, int p0, int nbins) {
+    int64_t cmax = 0;
+    for (int k = 0; k < nbins; ++k) {
+        int64_t p = ((int64_t)p0 + k) % N;
+        if (p < 0) p += N;
+        cmax = std::max<int64_t>(cmax, std::min<int64_t>(p, N - p));
+    }
+    return (int)cmax;
 }
 
 // Device-side description of a batched plan (one allocation, laid out by
@@ -1553,7 +1782,7 @@ bool ternary_supported(const ndft_desc &d) {
 size_t ternary_ws_bytes(const ndft_desc &d, int sm) {
     if (!ternary_supported(d)) return 0;
     const TernLayout L = layout_for(d, sm);
-    return L.b_bytes + L.part_bytes;
+    return L.b_bytes + L.part_bytes + L.dc_bytes;
 }
 
 cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
@@ -1568,6 +1797,8 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
     const TernLayout L = layout_for(p.d, p.sm_count);
     p.b_bytes = L.b_bytes;
     p.part_bytes = L.part_bytes;
+    p.dc_bytes = L.dc_bytes;
+    p.pair_slots = pair_slots_for(N, p.d.p0, p.d.nbins);
     p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));  // CUtensorMap wants 64-byte alignment
     if (!p.tmap_host) return cudaErrorMemoryAllocation;
     if ((e = make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
@@ -1644,6 +1875,8 @@ static cudaError_t gemm_cols(Plan &p, int nc, int64_t b_row0, void *out, cudaStr
     else e = launch_gemm<1>(p, P, nullptr, nullptr, nunits, out_base, om, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
+    p.last_variant = 1;
+    p.last_nsplit = P.nsplit;
     if (P.nsplit > 1) {
         *launches += 1;
         return launch_reduce_splits(part, P.nsplit, (int64_t)nc * 2 * nb, static_cast<float *>(out), s);
@@ -1665,8 +1898,80 @@ static int first_part_cols(const Plan &p, int ncols) {
 // memory untouched), so the packing runs under the first part's contraction.
 constexpr int kPackBlocksPerSm = 2;
 
+// Conjugate-paired contraction of ncols columns: rows = the R / I rows of
+// frequencies 1 .. S, columns = (col, r/i), K = 16 samples per block; the
+// split partials always go to the workspace, and the fold writes the output
+// (bin 0 from the packing kernel's DC sums).
+static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, const void *a_base,
+                             const void *r_base, void *out, cudaStream_t s, int *launches) {
+    const int N = p.d.n, S = p.pair_slots;
+    const int kblocks = pair_kblocks(N);
+    const int gy = pair_pack_tiles(N);
+    float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + p.b_bytes);
+    float2 *dc = reinterpret_cast<float2 *>(static_cast<unsigned char *>(p.ws) + p.b_bytes + p.part_bytes);
+    PackProb pp = pp0;
+    pp.kblocks = kblocks;
+    pp.ncols = ncols;
+    pp.row0 = 0;
+    {
+        const int gx = (ncols + 31) / 32;
+        k_pack_pair<<<dim3(gx, std::min(gy, 65535)), 256, 0, s>>>(
+            pp, p.d.flags, caf, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base),
+            static_cast<uint4 *>(p.ws), dc, gy);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        *launches += 1;
+    }
+    Problem P{};
+    P.N = N;
+    P.p0 = 1;
+    P.nbins = S;
+    P.ncols = 2 * ncols;
+    P.kblocks = kblocks;
+    P.mtiles = (2 * S + 255) / 256;
+    P.ntiles = (P.ncols + TN - 1) / TN;
+    const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+    const int64_t cap_units = (int64_t)(p.part_bytes / ((size_t)256 * TN * sizeof(float)));
+    P.nsplit = choose_split(tiles, kblocks, p.sm_count, p.tune_split, cap_units);
+    P.b_row0 = 0;
+    P.ld = 2LL * S;
+    P.split_stride = (int64_t)P.ncols * 2 * S;
+    P.ang = p.ang;
+    P.nth = nth_for(N);
+    P.out_off = 0;
+    alignas(64) CUtensorMap omap;
+    const bool tma_out = (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap) == cudaSuccess;
+    cudaError_t e = launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
+                                                   tma_out ? &omap : nullptr, s);
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    p.last_variant = 2;
+    p.last_nsplit = P.nsplit;
+    k_pair_fold<<<ncols, 256, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc, gy, ncols,
+                                      static_cast<float2 *>(out));
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+// Whether a call of ncols columns runs conjugate-paired: the plan's window
+// folds onto frequencies 1 .. S, the default tile and one part are in use,
+// the partials of one split fit, and the paired contraction issues fewer
+// K-block steps than the unpaired one.
+static bool use_pair(const Plan &p, int ncols) {
+    if (p.tune_pair == 1 || p.pair_slots < 1 || tile_pair(p) || tile_halves(p) != 2 || first_part_cols(p, ncols))
+        return false;
+    const int64_t S = p.pair_slots, nb = p.d.nbins, N = p.d.n;
+    if ((size_t)2 * ncols * 2 * S * sizeof(float) > p.part_bytes) return false;
+    if ((size_t)pair_pack_tiles((int)N) * ncols * sizeof(float2) > p.dc_bytes) return false;
+    if (p.tune_pair == 2) return true;
+    const int64_t paired = ((2 * S + 255) / 256) * ((2LL * ncols + TN - 1) / TN) * (int64_t)pair_kblocks((int)N);
+    const int64_t plain = ((2 * nb + 255) / 256) * (((int64_t)ncols + TN - 1) / TN) * ((N + 7) / 8);
+    return paired < plain;
+}
+
 static cudaError_t run_single(Plan &p, const PackProb &pp, bool caf, int ncols, const void *a_base,
                               const void *r_base, void *out, cudaStream_t s, int *launches) {
+    if (use_pair(p, ncols)) return pair_cols(p, pp, caf, ncols, a_base, r_base, out, s, launches);
     const int h0 = first_part_cols(p, ncols);
     cudaError_t e;
     if (h0 == 0) {

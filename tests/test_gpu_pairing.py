@@ -1,0 +1,153 @@
+"""GPU parity of the conjugate-paired tensor-core contraction.
+
+W^(-c i) = conj(W^(c i)) (Eq. 8) and sigma(conj w) = conj(sigma(w)) (Eq. 2),
+so bins +c and -c of the NDFT come from one pair of real contractions,
+U = S_r v + F_r sigma(v) and V = S_i v + F_i sigma(v): X[+c] = U + jV,
+X[-c] = U - jV; bin 0 is the packing kernel's sum of v + sigma(v).  Every case
+is checked against the fp64 oracle at the fp32 bar (1e-5 of max |X|), with the
+paired path forced (tuning key 6 = 2) and cross-checked against the unpaired
+rows (key 6 = 1) on the same inputs: centred and full windows, windows that
+wrap past bin 0, contain N/2 or give an odd number of paired frequencies (the
+element-wise fold-out), ragged N, both CAF flags and several sample-axis
+splits."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0532_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_0532_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
+
+
+def slots(N, p0, nbins):
+    p = (p0 + np.arange(nbins)) % N
+    return int(np.max(np.minimum(p, N - p)))
+
+
+@pytest.mark.parametrize("N,batch,p0,nbins", [
+    (64, 300, 0, 0),          # full window, N/2 self-conjugate
+    (1024, 600, 0, 0),
+    (1000, 77, -500, 1000),   # centred, even N
+    (999, 40, -499, 999),     # centred, odd N (no N/2 bin)
+    (100, 130, -7, 77),       # asymmetric: N/2 inside, most bins unpaired
+    (4133, 9, 4128, 20),      # wraps past bin 0
+    (300, 33, -15, 31),       # odd slot count: element-wise fold-out
+    (4, 5, 0, 0), (2, 3, 0, 0), (3, 7, 0, 0),
+])
+def test_paired_ndft(api, N, batch, p0, nbins):
+    rng = np.random.default_rng(60 + N)
+    x = scenes.cn(rng, (batch, N)).astype(np.complex64)
+    x[:, ::7] = 0
+    if batch > 2:
+        x[1, :] = 0
+    nb = nbins or N
+    ref = oracle.ndft(x.astype(np.complex128), p0=p0, nbins=nb)
+    outs = {}
+    for key in (2, 1):
+        p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="ternary", prec="bf16x2")
+        assert p.query(0) == slots(N, p0, nb)
+        p.set_tuning(6, key)
+        got = p.ndft(dev(x)).cpu().numpy()
+        p.query_error()
+        assert p.query(1) == (2 if key == 2 else 1)
+        assert relerr(got, ref) < TOL, key
+        outs[key] = got
+    assert np.max(np.abs(outs[2] - outs[1])) / np.max(np.abs(ref)) < 2 * TOL
+
+
+@pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
+    (4133, -3, 100, -48, 96, 0),
+    (700, 650, 40, -16, 33, 1),
+    (700, 650, 40, -16, 33, 2),
+    (2048, 0, 300, -1024, 2048, 0),   # every bin of N, lags in two n-tiles
+    (513, -600, 3, 250, 20, 0),       # lags entirely before the samples: exact zeros
+])
+def test_paired_caf(api, N, lag0, nlags, p0, nbins, flags):
+    sc = scenes.radar_scene(N=N, nlags=min(nlags, 64), nbins=min(nbins, 64), seed=61 + N % 97)
+    ref = oracle.caf(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, flags=flags, z32=True)
+    outs = {}
+    for key in (2, 1):
+        p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="ternary", prec="bf16x2")
+        p.set_tuning(6, key)
+        got = p.caf(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags).cpu().numpy()
+        p.query_error()
+        assert p.query(1) == (2 if key == 2 else 1)
+        if np.max(np.abs(ref)) == 0:
+            assert np.max(np.abs(got)) == 0
+        else:
+            assert relerr(got, ref) < TOL, key
+        outs[key] = got
+
+
+@pytest.mark.parametrize("split", [0, 1, 3, 19])
+def test_paired_caf_splits_sampled(api, split):
+    """The headline layout at N = 16384: 1024 lags x bins -512..511 (512 paired
+    frequencies, bin 0 from the DC sums), every sample-axis split count giving
+    the same cells within the bar; the default choice pairs."""
+    sc = scenes.radar_scene(N=16384, nlags=1024, nbins=1024, seed=62)
+    p = api.Plan(sc.N, p0=-512, nbins=1024, max_lags=1024, form="ternary", prec="bf16x2")
+    assert p.query(0) == 512
+    p.set_tuning(0, split)
+    A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 1024)
+    idx, _ = api.argmax(A.reshape(1, -1))
+    got = A.cpu().numpy()
+    p.query_error()
+    assert p.query(1) == 2
+    if split:
+        assert p.query(2) == split
+    rng = np.random.default_rng(63)
+    lags = np.concatenate([[0, 0, 0, 37, 120, 301, 1023, 255, 256, 511, 512], rng.integers(0, 1024, 40)])
+    bins = np.concatenate([[0, -512, 511, 5, -12, 40, -1, 1, -511, 255, -256], rng.integers(-512, 512, 40)])
+    ref = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
+    peak = np.max(np.abs(got))
+    assert np.max(np.abs(got[lags, bins + 512] - ref)) / peak < TOL
+    assert int(idx[0]) == 512  # the direct path at lag 0, bin 0
+
+
+def test_paired_deterministic_and_graph(api):
+    """Two calls give the same bits, and a CUDA-graph replay of the paired call
+    on new inputs equals an eager call on them."""
+    sc = scenes.radar_scene(N=8192, nlags=256, nbins=512, seed=64)
+    p = api.Plan(sc.N, p0=-256, nbins=512, max_lags=256, form="ternary", prec="bf16x2")
+    ss, sr = dev(sc.s_surv), dev(sc.s_ref)
+    a1 = p.caf(ss, sr, 0, 256).cpu().numpy()
+    a2 = p.caf(ss, sr, 0, 256).cpu().numpy()
+    assert p.query(1) == 2
+    assert np.array_equal(a1.view(np.uint32), a2.view(np.uint32))
+    out = torch.empty((256, 512), dtype=torch.complex64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.caf(ss, sr, 0, 256, out=out)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        p.caf(ss, sr, 0, 256, out=out)
+    sc2 = scenes.radar_scene(N=8192, nlags=256, nbins=512, seed=65)
+    ss.copy_(dev(sc2.s_surv))
+    sr.copy_(dev(sc2.s_ref))
+    g.replay()
+    torch.cuda.synchronize()
+    want = p.caf(ss, sr, 0, 256).cpu().numpy()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want.view(np.uint32))
