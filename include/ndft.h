@@ -245,8 +245,9 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * two accumulators used in turn; 258: the 256-row tile on a 2-SM pair, M = 256
  * MMAs with each CTA holding half of A and of B and two tensor-memory
  * accumulators used in turn); key 2 = ternary-GEMM K blocks
- * (8 samples each) per tensor-memory accumulation chain before it is folded
- * into the fp32 result (0 = 64); key 3 = ternary-GEMM fold path (0: bulk
+ * per tensor-memory accumulation chain before it is folded into the fp32
+ * result (0 = the default: 64 blocks of 8 samples, or 256 blocks of 16
+ * samples in the conjugate-paired contraction of key 6); key 3 = ternary-GEMM fold path (0: bulk
  * tensor stores/adds, 1: per-element adds).  Used by the autotuner; affects
  * speed and fp32 rounding only.  Key 4 (test only) = 1: the ternary GEMM's
  * operand loader issues no loads, so every bounded wait of the kernel runs out

@@ -7,8 +7,10 @@ each with CUDA events on the current stream, keeps the fastest and records it
 in a JSON cache keyed by GPU name and problem shape, so later plans of the
 same shape reuse the choice without timing.
 
-Only settings that keep the accuracy bar are offered: chains of at most 64
-K blocks (measured error <= 3.3e-6 of max|A| on the 65536-sample surface).
+Only settings that keep the accuracy bar are offered: the default chain
+length of each contraction variant (0: 256 blocks of 16 samples in the
+conjugate-paired one, 1.9e-6 of max|A| on the 65536-sample surface; 64 blocks
+of 8 samples in the unpaired one, 3.3e-6) or shorter ones.
 The cache lives at ``$NDFT_AUTOTUNE_CACHE`` or ``~/.cache/ndft_gb300/autotune.json``.
 """
 from __future__ import annotations
@@ -23,7 +25,7 @@ _lock = threading.Lock()
 SPLIT, ROWS, CHUNK, DRAIN = 0, 1, 2, 3
 PARTS = 5  # tensor-core calls of >= 512 columns: 1 one part (default), 0 two parts (not tuned: see tune_caf)
 
-TERNARY_SPACE = {ROWS: [256, 128, 258], CHUNK: [64, 32], SPLIT: [0, 8, 16, 19, 24, 32]}
+TERNARY_SPACE = {ROWS: [256, 128, 258], CHUNK: [0, 64, 32], SPLIT: [0, 8, 16, 19, 24, 32]}
 DIRECT_SPACE = {SPLIT: [0, 2, 4, 6, 8, 12, 16]}
 # batched tensor-core plans: one persistent contraction over all CPIs, no split;
 # the knobs are the chain length and the fold-out path

@@ -52,8 +52,18 @@ constexpr int kMaxThi = kMaxN / R_LO + 2;
 constexpr int kGenWarps = 8;
 constexpr int kEpiWarp0 = 2 + kGenWarps;  // warps 10..13 -> TMEM lane quarters 2, 3, 0, 1
 constexpr int kThreads = (2 + kGenWarps + 4) * 32;
+// the conjugate-paired contraction generates twice the twiddles per MMA of the
+// unpaired one and runs twice the A-producer warps (4 per SM sub-partition) to
+// hide their latency
+constexpr int kGenWarpsPair = 16;
+__host__ __device__ constexpr int gemm_gen_warps(bool pair) { return pair ? kGenWarpsPair : kGenWarps; }
+__host__ __device__ constexpr int gemm_threads(bool pair) { return (2 + gemm_gen_warps(pair) + 4) * 32; }
 constexpr int kMaxSplit = 32;
 constexpr int kChunk = 64;  // K blocks per TMEM accumulation chain (512 samples)
+// paired form: 256 K blocks of 16 samples (4096 samples) per chain; measured on
+// the 65536-sample surface, chains of 64 / 128 / 256 blocks give 4.7e-7 /
+// 9.3e-7 / 1.9e-6 of max|A| against the fp64 oracle
+constexpr int kChunkPair = 256;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 
@@ -188,6 +198,8 @@ __device__ __forceinline__ void red_add_f32(float *addr, float v) {
 }
 
 __device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory"); }
+template <int GW>
+__device__ __forceinline__ void gen_bar_n() { asm volatile("bar.sync 1, %0;" ::"n"(GW * 32) : "memory"); }
 
 // Bulk tensor copies of a staged [32 columns][128 rows] fp32 block to the
 // output map at {row, column, split}: plain store, or element-wise add in L2.
@@ -300,18 +312,40 @@ __device__ __forceinline__ void gen_pair_w(uint32_t u, uint32_t N, float2 W, uin
     im = make_uint4(si, sr, wi, wr);
 }
 
-// Conjugate-paired form: the K entries of one (frequency c, sample i) for the
-// R row ([S_r, S_r, F_hi_r, F_lo_r]) and the I row ([S_i, S_i, F_hi_i,
-// F_lo_i]), as two 32-bit words each (signs, then the bf16 hi + lo of F).
-__device__ __forceinline__ void gen_conj_words(uint32_t u, uint32_t N, float2 W, uint32_t &sr, uint32_t &si,
-                                               uint32_t &wr, uint32_t &wi) {
-    sign_bits(u, N, sr, si);
-    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(W.x, W.y);
-    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(W.x - __low2float(hi2), W.y - __high2float(hi2));
-    const uint32_t uh = *reinterpret_cast<const uint32_t *>(&hi2);
-    const uint32_t ul = *reinterpret_cast<const uint32_t *>(&lo2);
-    wr = __byte_perm(uh, ul, 0x5410);  // [F_hi_r, F_lo_r]
-    wi = __byte_perm(uh, ul, 0x7632);  // [F_hi_i, F_lo_i]
+// Conjugate-paired form, one 16-byte chunk of a row = samples a and a + 1 of
+// the K block, in the K order [S(a), S(a+1), S(a), S(a+1), F_hi(a), F_hi(a+1),
+// F_lo(a), F_lo(a+1)] (the packed B chunk pairs [v_hi, v_lo, sigma, sigma] in
+// the same order), so every word is one bf16x2 conversion of two samples.
+// The twiddle index is carried as an exact integer-valued float uf = 4 ((c i)
+// mod N) < 2^20, and the exact signs come from it by range arithmetic:
+//     sgn Re W = sgn((uf - N)(uf - 3N)),   sgn Im W = sgn(uf (uf - 2N)),
+// both factors exact integers, so the product is 0 exactly on the axes and
+// otherwise at least 1 in magnitude: clamping it to [-1, 1] gives the sign.
+__device__ __forceinline__ float sgn_clamp(float x) { return fminf(fmaxf(x, -1.f), 1.f); }
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// hi and lo words of the bf16 split of two values
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    hi = bf2(x0, x1);
+    lo = bf2(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xFFFF0000u));
+}
+
+// The R and I chunks of one frequency for samples a and a + 1 (twiddles Wa, Wb
+// at indices ua, ub).
+__device__ __forceinline__ void gen_conj_chunk(float ua, float ub, float2 Wa, float2 Wb, float fN, uint4 &re,
+                                               uint4 &im) {
+    const float sra = sgn_clamp((ua - fN) * (ua - 3.f * fN)), srb = sgn_clamp((ub - fN) * (ub - 3.f * fN));
+    const float sia = sgn_clamp(ua * (ua - 2.f * fN)), sib = sgn_clamp(ub * (ub - 2.f * fN));
+    const uint32_t SR = bf2(sra, srb), SI = bf2(sia, sib);
+    uint32_t hr, lr, hi, li;
+    split2(Wa.x, Wb.x, hr, lr);
+    split2(Wa.y, Wb.y, hi, li);
+    re = make_uint4(SR, SR, hr, lr);
+    im = make_uint4(SI, SI, hi, li);
 }
 
 // W <- W * R (fp32 complex product)
@@ -369,12 +403,14 @@ struct Tile {
 // bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
 // forward epilogue on a [lags][2N] fp32 output).
 template <int MH, bool BT, int ADJ, bool PAIR = false>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(gemm_threads(PAIR), 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
                    int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
     static_assert(ADJ == 0 || (MH == 2 && !BT), "the adjoint runs on the 256-row tile");
     static_assert(!PAIR || (MH == 2 && !BT && ADJ == 0), "the conjugate-paired form runs on the 256-row tile");
+    constexpr int GW = gemm_gen_warps(PAIR);  // A-producer warps: warps 2 .. 2 + GW - 1
+    constexpr int EPI0 = 2 + GW;              // epilogue warps EPI0 .. EPI0 + 3 -> TMEM lane quarters warp % 4
     using T = Tile<MH>;
     constexpr int STG = T::kStages;
     constexpr int NB = T::kBufs;
@@ -399,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STG; ++s) {
-            mbar_init(&full[s], 1 + kGenWarps);
+            mbar_init(&full[s], 1 + GW);
             mbar_init(&empty[s], 1);  // one MMA commit
         }
         for (int b = 0; b < NB; ++b) {
@@ -524,10 +560,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
-    } else if (warp < kEpiWarp0) {
+    } else if (warp < EPI0) {
         // ---------------- A producers ----------------
         constexpr int PPT = 2 * MH;      // (bin, sample) pairs per thread per K block
-        const int g = threadIdx.x - 64;  // 0..255
+        const int g = threadIdx.x - 64;  // 0 .. 32 GW - 1
         const int t = g & 7, pg = g >> 3;
         int stage = 0;
         uint32_t phase = 0;
@@ -575,61 +611,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else if constexpr (PAIR) {
             // Conjugate-paired rows: slot k of the unit is the frequency
             // c = p0 + k (p0 = the first paired frequency); its R row (2 k) and
-            // I row (2 k + 1) hold, per sample, [S_r, S_r, F_hi_r, F_lo_r] and
-            // [S_i, S_i, F_hi_i, F_lo_i] of F = W^(c i).  A K block is 16
-            // samples; thread (pg, t) makes slots pg + 32 j, samples 2 t and
-            // 2 t + 1 of it, each twiddle advanced by W^(16 c) per K block and
-            // re-seeded from the table every kReseed blocks.
+            // I row (2 k + 1) hold the signs and bf16 hi + lo parts of Re and
+            // Im F, F = W^(c i), in the chunk order of gen_conj_chunk.  A K
+            // block is 16 samples; thread (pg, t) makes slots pg + 4 GW j,
+            // samples 2 t and 2 t + 1 of it, each twiddle advanced by
+            // W^(16 c) per K block and re-seeded from the table every kReseed
+            // blocks; the index advances in exact float arithmetic.
+            constexpr int SPT = 32 / GW;  // slots per thread: pg + 4 GW j
             for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
                 const Work w = decode(u, single, probs, units);
-                gen_bar();  // every producer is done with the previous table
-                for (int e = g; e < w.P.nth + R_LO; e += kGenWarps * 32) {
+                gen_bar_n<GW>();  // every producer is done with the previous table
+                for (int e = g; e < w.P.nth + R_LO; e += GW * 32) {
                     const float2 v = w.P.ang[e];
                     if (e < w.P.nth) s_thi[e] = v;
                     else s_tlo[e - w.P.nth] = v;
                 }
-                gen_bar();
+                gen_bar_n<GW>();
                 if (!ok) continue;
                 const uint32_t N = (uint32_t)w.P.N;
+                const float fN = (float)N, f4N = 4.f * fN;
                 const uint32_t thi = smem_u32(s_thi), tlo = smem_u32(s_tlo);
-                uint32_t ua[4], ub[4], dd[4];
-                float2 wa[4], wb[4], rot[4];
+                float ua[SPT], ub[SPT], dd[SPT];  // exact integers < 2^20
+                float2 wa[SPT], wb[SPT], rot[SPT];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int k = w.mt * 128 + pg + 32 * j;  // slot
+                for (int j = 0; j < SPT; ++j) {
+                    const int k = w.mt * 128 + pg + 4 * GW * j;  // slot
                     int64_t c = ((int64_t)w.P.p0 + k) % (int64_t)N;
                     if (c < 0) c += N;
                     const int64_t i0 = (int64_t)w.kb0 * 16 + 2 * t;
-                    ua[j] = 4u * (uint32_t)((c * (i0 % (int64_t)N)) % (int64_t)N);
-                    ub[j] = 4u * (uint32_t)((c * ((i0 + 1) % (int64_t)N)) % (int64_t)N);
-                    dd[j] = 4u * (uint32_t)((16 * c) % (int64_t)N);
-                    rot[j] = tw_table(dd[j], N, thi, tlo);  // W^(16 c)
+                    const uint32_t d4 = 4u * (uint32_t)((16 * c) % (int64_t)N);
+                    ua[j] = (float)(4u * (uint32_t)((c * (i0 % (int64_t)N)) % (int64_t)N));
+                    ub[j] = (float)(4u * (uint32_t)((c * ((i0 + 1) % (int64_t)N)) % (int64_t)N));
+                    dd[j] = (float)d4;
+                    rot[j] = tw_table(d4, N, thi, tlo);  // W^(16 c)
                 }
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     const uint32_t a_st = a_base + stage * T::kABytes;
                     const bool seed = ((kb - w.kb0) % kReseed) == 0;
-                    uint4 vre[4], vim[4];
+                    uint4 vre[SPT], vim[SPT];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < SPT; ++j) {
                         if (seed) {
-                            wa[j] = tw_table(ua[j], N, thi, tlo);
-                            wb[j] = tw_table(ub[j], N, thi, tlo);
+                            wa[j] = tw_table((uint32_t)ua[j], N, thi, tlo);
+                            wb[j] = tw_table((uint32_t)ub[j], N, thi, tlo);
                         }
-                        uint32_t sra, sia, wra, wia, srb, sib, wrb, wib;
-                        gen_conj_words(ua[j], N, wa[j], sra, sia, wra, wia);
-                        gen_conj_words(ub[j], N, wb[j], srb, sib, wrb, wib);
-                        vre[j] = make_uint4(sra, wra, srb, wrb);
-                        vim[j] = make_uint4(sia, wia, sib, wib);
+                        gen_conj_chunk(ua[j], ub[j], wa[j], wb[j], fN, vre[j], vim[j]);
                         wa[j] = cmul_f2(wa[j], rot[j]);
                         wb[j] = cmul_f2(wb[j], rot[j]);
                         ua[j] += dd[j];
-                        if (ua[j] >= 4u * N) ua[j] -= 4u * N;
+                        if (ua[j] >= f4N) ua[j] -= f4N;
                         ub[j] += dd[j];
-                        if (ub[j] >= 4u * N) ub[j] -= 4u * N;
+                        if (ub[j] >= f4N) ub[j] -= f4N;
                     }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) store_pair(a_st, pg + 32 * j, t, vre[j], vim[j]);
+                    for (int j = 0; j < SPT; ++j) store_pair(a_st, pg + 4 * GW * j, t, vre[j], vim[j]);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&full[stage]);
@@ -1438,21 +1474,16 @@ __global__ void __launch_bounds__(256) k_pack_adjoint(const float2 *__restrict__
 // no GEMM row: X[0] = sum_i (v + sigma(v)) is summed by the packing kernel.
 //
 // B row (kb, 2 col + comp) holds samples 16 kb .. 16 kb + 15 of component comp
-// of column col, 4 bf16 each.  Thread t of a column's 8 packs samples 2 t and
+// of column col, 4 bf16 each: chunk t (16 bytes) = samples a = 16 kb + 2 t and
+// a + 1 as [v_hi(a), v_hi(a+1), v_lo(a), v_lo(a+1), sigma(a), sigma(a+1),
+// sigma(a), sigma(a+1)] against the A rows' [S, S, F_hi, F_lo] in the same
+// order.  Thread t of a column's 8 packs samples 2 t and
 // 2 t + 1 of each K block into both rows and adds v + sigma(v) of them to the
 // column's DC sum; the 8 partial sums of a column are combined in a fixed
 // order and written per K-block tile (dc[tile][col]).
 constexpr int kPairPackKb = 16;  // K blocks (16 samples each) per packing tile
 
-__device__ __forceinline__ uint32_t bf16_hilo(float v) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
-}
 __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
-__device__ __forceinline__ uint32_t sign2(float v) {
-    return v > 0.f ? 0x3F803F80u : (v < 0.f ? 0xBF80BF80u : 0u);
-}
 
 __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, bool caf,
                                                    const float2 *__restrict__ a_base,
@@ -1481,8 +1512,12 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
                     if (i + 1 < P.N) v1 = x[i + 1];
                 }
                 const int64_t row = P.row0 + (int64_t)kb * ncols2 + 2LL * col;
-                B[row * 8 + t] = make_uint4(bf16_hilo(v0.x), sign2(v0.x), bf16_hilo(v1.x), sign2(v1.x));
-                B[(row + 1) * 8 + t] = make_uint4(bf16_hilo(v0.y), sign2(v0.y), bf16_hilo(v1.y), sign2(v1.y));
+                uint32_t hr, lr, hi, li;
+                split2(v0.x, v1.x, hr, lr);
+                split2(v0.y, v1.y, hi, li);
+                const uint32_t sr2 = bf2(sgnf(v0.x), sgnf(v1.x)), si2 = bf2(sgnf(v0.y), sgnf(v1.y));
+                B[row * 8 + t] = make_uint4(hr, lr, sr2, sr2);
+                B[(row + 1) * 8 + t] = make_uint4(hi, li, si2, si2);
                 sr += (v0.x + sgnf(v0.x)) + (v1.x + sgnf(v1.x));
                 si += (v0.y + sgnf(v0.y)) + (v1.y + sgnf(v1.y));
             }
@@ -1666,14 +1701,14 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
-    const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
+    const int chunk = p.tune_chunk > 0 ? p.tune_chunk : (PAIR ? kChunkPair : kChunk);
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
     const CUtensorMap &om = omap ? *omap : none;
     const int out_tma = omap ? 1 : 0;
     timer_begin(p, s);
     const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
-    kern<<<grid, kThreads, smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
+    kern<<<grid, gemm_threads(PAIR), smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
                                       out_base, p.err);
     e = cudaGetLastError();
     timer_end(p, s);
