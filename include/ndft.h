@@ -246,8 +246,8 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * MMAs with each CTA holding half of A and of B and two tensor-memory
  * accumulators used in turn); key 2 = ternary-GEMM K blocks
  * per tensor-memory accumulation chain before it is folded into the fp32
- * result (0 = the default: 64 blocks of 8 samples, or 256 blocks of 16
- * samples in the conjugate-paired contraction of key 6); key 3 = ternary-GEMM fold path (0: bulk
+ * result (0 = the default: 64 blocks of 8 samples, or of 16 samples in the
+ * conjugate-paired contraction of key 6); key 3 = ternary-GEMM fold path (0: bulk
  * tensor stores/adds, 1: per-element adds).  Used by the autotuner; affects
  * speed and fp32 rounding only.  Key 4 (test only) = 1: the ternary GEMM's
  * operand loader issues no loads, so every bounded wait of the kernel runs out

@@ -8,9 +8,10 @@ in a JSON cache keyed by GPU name and problem shape, so later plans of the
 same shape reuse the choice without timing.
 
 Only settings that keep the accuracy bar are offered: the default chain
-length of each contraction variant (0: 256 blocks of 16 samples in the
-conjugate-paired one, 1.9e-6 of max|A| on the 65536-sample surface; 64 blocks
-of 8 samples in the unpaired one, 3.3e-6) or shorter ones.
+length of each contraction variant (0: 256 MMA K steps per chain, 64 blocks of
+16 samples in the conjugate-paired one or of 8 samples in the unpaired one;
+4.0e-6 / 4.9e-6 of max|X| on the worst case measured, the N = 2^18 NDFT of
+CN(0,1) vectors) or shorter ones.
 The cache lives at ``$NDFT_AUTOTUNE_CACHE`` or ``~/.cache/ndft_gb300/autotune.json``.
 """
 from __future__ import annotations

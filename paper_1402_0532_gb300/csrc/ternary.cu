@@ -60,10 +60,13 @@ __host__ __device__ constexpr int gemm_gen_warps(bool pair) { return pair ? kGen
 __host__ __device__ constexpr int gemm_threads(bool pair) { return (2 + gemm_gen_warps(pair) + 4) * 32; }
 constexpr int kMaxSplit = 32;
 constexpr int kChunk = 64;  // K blocks per TMEM accumulation chain (512 samples)
-// paired form: 256 K blocks of 16 samples (4096 samples) per chain; measured on
-// the 65536-sample surface, chains of 64 / 128 / 256 blocks give 4.7e-7 /
-// 9.3e-7 / 1.9e-6 of max|A| against the fp64 oracle
-constexpr int kChunkPair = 256;
+// paired form: 64 K blocks of 16 samples (1024 samples, the same 256 MMA K
+// steps per chain as the unpaired default).  The tensor core's truncating fp32
+// accumulation makes the error grow with the K steps of a chain: measured on
+// the N = 2^18 NDFT of CN(0,1) vectors (the worst case found), chains of 32 /
+// 64 / 128 / 256 paired blocks give 2.5e-6 / 4.0e-6 / 8.2e-6 / 1.6e-5 of max|X|
+// (the unpaired form 2.6e-6 / 4.9e-6 / 8.4e-6 / 1.7e-5 at the same K steps)
+constexpr int kChunkPair = 64;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 
