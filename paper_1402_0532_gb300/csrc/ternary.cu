@@ -285,6 +285,18 @@ __device__ __forceinline__ float2 tw_table(uint32_t u, uint32_t N, uint32_t thi,
                                                                             : make_float2(s, c);
 }
 
+// The same from the table in global memory (cached in L1).
+__device__ __forceinline__ float2 tw_table_g(uint32_t u, uint32_t N, const float2 *__restrict__ ang, int nth) {
+    const uint32_t q = (u >= N) + (u >= 2 * N) + (u >= 3 * N);
+    const uint32_t r = u - q * N;
+    const float2 h = __ldg(ang + (r >> 8));
+    const float2 l = __ldg(ang + nth + (r & (R_LO - 1)));
+    const float c = fmaf(h.x, l.x, -(h.y * l.y));
+    const float s = fmaf(h.y, l.x, h.x * l.y);
+    return q == 0u ? make_float2(c, -s) : q == 1u ? make_float2(-s, -c) : q == 2u ? make_float2(-c, s)
+                                                                            : make_float2(s, c);
+}
+
 // sigma(W) at u = 4 ((p i) mod N) in [0, 4N) as bf16 pairs, exact: Re W = cos
 // is < 0 for N < u < 3N and 0 at u = N, 3N; Im W = -sin is < 0 for 0 < u < 2N
 // and 0 at u = 0, 2N (the integer quadrant rule written as range tests).
@@ -402,6 +414,33 @@ struct Tile {
     static constexpr size_t kSmemTotal = kSmemBar + 160 + 1024;  // barriers, flags, alignment slack
 };
 
+// The conjugate-paired contraction: the 256-row tile without the twiddle table
+// in shared memory (its producers read the table through L1, a re-seed every
+// 16 K blocks) and with 4 KB fold-out buffers, two per epilogue warp, so that
+// each bulk copy moves 32 columns.
+struct TileP {
+    static constexpr int kRows = 256;
+    static constexpr int kABytes = kRows * 128;
+    static constexpr int kStages = 3;
+    static constexpr int kBufs = 1;
+    static constexpr size_t kSmemA = 0;
+    static constexpr size_t kSmemB = kSmemA + (size_t)kStages * kABytes;
+    static constexpr size_t kSmemStage = kSmemB + (size_t)kStages * B_BYTES;
+    static constexpr size_t kSmemTab = kSmemStage;  // unused
+    static constexpr size_t kSmemBar = kSmemStage + 4 * 8192;  // per epilogue warp 2 x [32 cols][32 rows] fp32
+    static constexpr size_t kSmemTotal = kSmemBar + 160 + 1024;
+};
+static_assert(TileP::kSmemTotal <= 232448, "shared memory of one CTA");
+
+template <bool PAIR, int MH>
+struct TileOf {
+    using type = Tile<MH>;
+};
+template <int MH>
+struct TileOf<true, MH> {
+    using type = TileP;
+};
+
 // ADJ selects the adjoint contractions (rows = samples, columns = lags, K =
 // bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
 // forward epilogue on a [lags][2N] fp32 output).
@@ -414,7 +453,7 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
     static_assert(!PAIR || (MH == 2 && !BT && ADJ == 0), "the conjugate-paired form runs on the 256-row tile");
     constexpr int GW = gemm_gen_warps(PAIR);  // A-producer warps: warps 2 .. 2 + GW - 1
     constexpr int EPI0 = 2 + GW;              // epilogue warps EPI0 .. EPI0 + 3 -> TMEM lane quarters warp % 4
-    using T = Tile<MH>;
+    using T = typename TileOf<PAIR, MH>::type;
     constexpr int STG = T::kStages;
     constexpr int NB = T::kBufs;
     extern __shared__ unsigned char smem_raw[];
@@ -623,17 +662,11 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
             constexpr int SPT = 32 / GW;  // slots per thread: pg + 4 GW j
             for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
                 const Work w = decode(u, single, probs, units);
-                gen_bar_n<GW>();  // every producer is done with the previous table
-                for (int e = g; e < w.P.nth + R_LO; e += GW * 32) {
-                    const float2 v = w.P.ang[e];
-                    if (e < w.P.nth) s_thi[e] = v;
-                    else s_tlo[e - w.P.nth] = v;
-                }
-                gen_bar_n<GW>();
-                if (!ok) continue;
+                if (!ok) break;
                 const uint32_t N = (uint32_t)w.P.N;
                 const float fN = (float)N, f4N = 4.f * fN;
-                const uint32_t thi = smem_u32(s_thi), tlo = smem_u32(s_tlo);
+                const float2 *ang = w.P.ang;
+                const int nth = w.P.nth;
                 float ua[SPT], ub[SPT], dd[SPT];  // exact integers < 2^20
                 float2 wa[SPT], wb[SPT], rot[SPT];
 #pragma unroll
@@ -646,7 +679,7 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                     ua[j] = (float)(4u * (uint32_t)((c * (i0 % (int64_t)N)) % (int64_t)N));
                     ub[j] = (float)(4u * (uint32_t)((c * ((i0 + 1) % (int64_t)N)) % (int64_t)N));
                     dd[j] = (float)d4;
-                    rot[j] = tw_table(d4, N, thi, tlo);  // W^(16 c)
+                    rot[j] = tw_table_g(d4, N, ang, nth);  // W^(16 c)
                 }
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
@@ -656,8 +689,8 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
 #pragma unroll
                     for (int j = 0; j < SPT; ++j) {
                         if (seed) {
-                            wa[j] = tw_table((uint32_t)ua[j], N, thi, tlo);
-                            wb[j] = tw_table((uint32_t)ub[j], N, thi, tlo);
+                            wa[j] = tw_table_g((uint32_t)ua[j], N, ang, nth);
+                            wb[j] = tw_table_g((uint32_t)ub[j], N, ang, nth);
                         }
                         gen_conj_chunk(ua[j], ub[j], wa[j], wb[j], fN, vre[j], vim[j]);
                         wa[j] = cmul_f2(wa[j], rot[j]);
@@ -832,6 +865,63 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                 // written by one thread only, in chain order, so the sum is
                 // deterministic.
                 const bool first = (c0 == w.kb0);
+                if (PAIR && out_tma) {
+                    // Paired tile: 32-column groups, each two tcgen05.ld of 16
+                    // columns -> one of two 4 KB staging buffers [32 cols][32 rows]
+                    // -> one bulk tensor store / add (box 32 x 32) by lane 0.  As
+                    // below, lane 0 waits for all of the previous chain's copies
+                    // before the chain's first copy (adds land in chain order) and,
+                    // before refilling a buffer, for the copy issued two groups
+                    // earlier to have read it.
+                    const uint32_t wst = smem_u32(smem + T::kSmemStage) + (uint32_t)quarter * 8192u;
+                    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+                    const int mrow0 = w.mt * T::kRows + 32 * quarter;
+                    constexpr int GPH = TN / 32;  // groups per row half
+                    constexpr int NG = MH * GPH;
+#pragma unroll 1
+                    for (int g = 0; g < NG; ++g) {
+                        const uint32_t tc = (uint32_t)((buf + g / GPH) * TN + (g % GPH) * 32);
+                        uint32_t ra[16], rb[16];
+                        tmem_ld16(trow + tc, ra);
+                        tmem_ld16(trow + tc + 16, rb);
+                        tmem_wait_ld();
+                        if (MH == 2 && g + 1 == GPH) {  // every load of half 0 has completed
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(tmem_half0);
+                        }
+                        if (g + 1 == NG) {  // the whole accumulator has been read
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+                        }
+                        const uint32_t sb = wst + (uint32_t)(g & 1) * 4096u;
+                        if (lane == 0) {
+                            if (g == 0) bulk_wait_all();
+                            else if (g > 1) bulk_wait_read1();
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(sb + (uint32_t)(j * 32 + lane) * 4u), "r"(ra[j])
+                                         : "memory");
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(sb + (uint32_t)((16 + j) * 32 + lane) * 4u),
+                                         "r"(rb[j])
+                                         : "memory");
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) {
+                            const int mrow = mrow0 + 128 * (g / GPH);
+                            const int col = w.nt * TN + (g % GPH) * 32;
+                            if (first) tma_store_out(&omap, sb, mrow, col, w.split);
+                            else tma_reduce_out(&omap, sb, mrow, col, w.split);
+                            bulk_commit();
+                        }
+                    }
+                    continue;
+                }
                 if (out_tma) {
                     // Each epilogue warp drains its own 32 TMEM lanes (rows) on its own:
                     // 16-column groups go TMEM -> registers -> one of two 2 KB staging
@@ -1627,13 +1717,13 @@ cudaError_t make_tmap(void *base, int64_t rows, CUtensorMap *map, int box_rows =
 // Output (or split partials) as a 3-D fp32 tensor {2 nbins rows, ncols, nsplit},
 // box 32 rows x 16 columns x 1 split, no swizzle: the epilogue warps' bulk
 // stores / adds (one warp's 32 TMEM lanes, a 16-column group).  Needs 2 nbins * 4 bytes to be a multiple of 16 (nbins even).
-cudaError_t make_out_map(void *base, int nbins, int ncols, int nsplit, CUtensorMap *map) {
+cudaError_t make_out_map(void *base, int nbins, int ncols, int nsplit, CUtensorMap *map, int box_cols = 16) {
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t rows = 2ull * nbins;
     cuuint64_t dims[3] = {rows, (cuuint64_t)ncols, (cuuint64_t)nsplit};
     cuuint64_t strides[2] = {rows * 4, rows * 4 * (cuuint64_t)ncols};
-    cuuint32_t box[3] = {32, 16, 1};  // one epilogue warp's 32 rows x 16 columns
+    cuuint32_t box[3] = {32, (cuuint32_t)box_cols, 1};  // one epilogue warp's 32 rows x 16 (paired: 32) columns
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1699,7 +1789,7 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
 template <int MH, bool BT = false, int ADJ = 0, bool PAIR = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
-    constexpr size_t smem = Tile<MH>::kSmemTotal;
+    constexpr size_t smem = TileOf<PAIR, MH>::type::kSmemTotal;
     auto kern = k_ternary_gemm<MH, BT, ADJ, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1978,7 +2068,8 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     P.nth = nth_for(N);
     P.out_off = 0;
     alignas(64) CUtensorMap omap;
-    const bool tma_out = (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap) == cudaSuccess;
+    const bool tma_out =
+        (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap, 32) == cudaSuccess;
     cudaError_t e = launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
                                                    tma_out ? &omap : nullptr, s);
     if (e != cudaSuccess) return e;
