@@ -698,9 +698,13 @@ def main():
     base = None
     if rank == 0:
         import oracle
-        rng = np.random.default_rng(11)
-        lags = np.concatenate([[0, 37, 120, 301], rng.integers(0, NLAGS, 60)])
-        bins = np.concatenate([[0, 5, -12, 40], rng.integers(P0, P0 + NBINS, 60)])
+        # every bin of 38 lag rows: the direct path and the echoes, the first and
+        # last lag and both sides of every 64- and 128-lag tile boundary
+        row_lags = np.array(sorted({0, 1, 37, 63, 64, 120, 127, 128, 129, 191, 192, 255, 256, 301, 320, 383, 384,
+                                    447, 448, 511, 512, 575, 576, 639, 640, 703, 704, 767, 768, 831, 832, 895,
+                                    896, 959, 960, 1000, 1022, 1023}))
+        Lg, Bg = np.meshgrid(row_lags, np.arange(P0, P0 + NBINS), indexing="ij")
+        lags, bins = Lg.ravel(), Bg.ravel()
         ref = oracle.caf_cells(scene.s_surv, scene.s_ref, lags, bins)
         ref32 = oracle.caf_cells(scene.s_surv, scene.s_ref, lags, bins, z32=True)
         At, Adn = A.cpu().numpy(), Ad.cpu().numpy()
@@ -709,7 +713,8 @@ def main():
         err = {"ternary": float(np.max(np.abs(gt - ref)) / amax), "direct": float(np.max(np.abs(gd - ref)) / amax),
                "ternary_vs_fp32_lagproduct": float(np.max(np.abs(gt - ref32)) / amax),
                "direct_vs_fp32_lagproduct": float(np.max(np.abs(gd - ref32)) / amax),
-               "normalised_by": "max |A| of the surface", "cells": int(lags.size)}
+               "normalised_by": "max |A| of the surface", "cells": int(lags.size),
+               "sample": "all 1024 bins of 38 lag rows"}
         if not args.no_cpu_baseline and world == 1:
             base = cpu_baseline(scene, budget_cells=16 * NBINS)
 

@@ -205,8 +205,11 @@ ndft_status caf_backward_inputs(ndft_plan_t plan, const void *s_surv, const void
  * the library keeps until exit.  Limits: 1 <= n <= 2^20, 1 <= nbins <= n,
  * 1 <= nlags <= 2^20; beyond them NDFT_E_INVALID and nothing is launched.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make it before any stream capture.  Calls share the
- * array: calls that overlap on the GPU race and must be serialised.
+ * (cudaGetSymbolAddress) and loads every kernel the call can launch; make it
+ * before any stream capture.  After a reset of the device's context
+ * (cudaDeviceReset) the next call repeats that set-up, so it too belongs
+ * before any capture.  Calls share the array: calls that overlap on the GPU
+ * race and must be serialised.
  * s_surv, s_ref: [n] complex64; A: [nlags][nbins] complex64; device pointers. */
 ndft_status caf_exec_noalloc(int32_t n, int32_t p0, int32_t nbins, const void *s_surv, const void *s_ref,
                              int32_t lag0, int32_t nlags, uint32_t flags, void *A, cudaStream_t stream);

@@ -401,6 +401,14 @@ cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t ba
     return cudaGetLastError();
 }
 
+cudaError_t direct_caf_preload() {
+    auto k = k_direct<PrecF32, CafSrc<PrecF32>>;
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+    return prep_kernel(k, Smem::bytes_for<PrecF32>());
+}
+
 cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
                               void *A, cudaStream_t s, int *launches) {
     const int N = p.d.n, nb = p.d.nbins ? p.d.nbins : N;

@@ -96,6 +96,11 @@ int grid_for(int64_t n, int threads) {
 
 }  // namespace
 
+cudaError_t reduce_preload() {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_reduce_f32);
+}
+
 cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s) {
     k_reduce_f32<<<grid_for(count / 4 + 1, 256), 256, 0, s>>>(ws, nsplit, count, out);
     return cudaGetLastError();

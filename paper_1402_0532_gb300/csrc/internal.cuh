@@ -156,6 +156,7 @@ inline void timer_end(const Plan &p, cudaStream_t s) {
 
 // tables.cu
 cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, cudaStream_t s);
+cudaError_t tables_preload();  // loads the module of the table kernel (no launch)
 
 // direct.cu
 cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
@@ -165,6 +166,7 @@ cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_r
 cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *ref, void *out,
                                   cudaStream_t s, int *launches);
 size_t direct_ws_bytes(const ndft_desc &d, int sm_count);
+cudaError_t direct_caf_preload();  // loads the fp32 CAF kernel's module and sets its attributes (no launch)
 int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune);
 
 // nfft.cu
@@ -184,6 +186,7 @@ cudaError_t launch_fft_caf(const Plan &p, const void *s_surv, const void *s_ref,
 
 // epilogue.cu
 cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s);
+cudaError_t reduce_preload();  // loads the fp32 split-sum kernel's module (no launch)
 cudaError_t launch_reduce_splits_i32(const uint32_t *ws, int nsplit, int64_t count, uint32_t *out,
                                      cudaStream_t s);
 cudaError_t launch_argmax(const float2 *X, int64_t rows, int64_t cols, int64_t *idx, float *val,

@@ -15,11 +15,18 @@
 // process exits.  Host code cannot use the array's name as a device address
 // (it names a host-side stand-in), so the first call on each device, with that
 // device current, looks the address up with cudaGetSymbolAddress and caches
-// it; make that first call before any stream capture.  All calls share the
-// array and each call rewrites everything it reads (table first, then the
-// partials), so nothing needs clearing; calls that overlap on the GPU (other
-// streams, other host threads) race on it and must be serialised by the caller.
+// it together with the device's current context; the same set-up also loads
+// every kernel the call can launch (the table kernel, the direct CAF kernel
+// and the split sum), so that later calls load no module.  Make that first
+// call before any stream capture.  A device whose context was reset
+// (cudaDeviceReset) gets a new context, and the next call repeats the set-up:
+// make it before any capture as well.  All calls share the array and each
+// call rewrites everything it reads (table first, then the partials), so
+// nothing needs clearing; calls that overlap on the GPU (other streams, other
+// host threads) race on it and must be serialised by the caller.
 #include "internal.cuh"
+
+#include <cuda.h>
 
 #include <mutex>
 
@@ -33,18 +40,42 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices];
+CUcontext g_scratch_ctx[kMaxDevices];
 std::mutex g_scratch_mu;
+
+// The calling thread's current context, through the runtime's driver entry
+// point (the library does not link the driver library itself).
+cudaError_t current_context(CUcontext *ctx) {
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return cudaErrorNotSupported;
+        fn = reinterpret_cast<Fn>(p);
+    }
+    return fn(ctx) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 cudaError_t scratch_address(void **out, int *sm_count) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    CUcontext ctx = nullptr;  // NULL before the runtime has set up a context on this thread
+    if ((e = current_context(&ctx)) != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!ctx || !g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         if ((e = cudaGetSymbolAddress(&p, g_scratch)) != cudaSuccess) return e;
+        if ((e = tables_preload()) != cudaSuccess) return e;
+        if ((e = direct_caf_preload()) != cudaSuccess) return e;
+        if ((e = reduce_preload()) != cudaSuccess) return e;
+        if ((e = current_context(&ctx)) != cudaSuccess) return e;  // set up by the lookup if it was not
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     if ((e = cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -30,6 +30,11 @@ __global__ void k_tables(int N, float2 *__restrict__ tw32, short2 *__restrict__ 
     }
 }
 
+cudaError_t tables_preload() {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_tables);
+}
+
 cudaError_t launch_tables(int N, float2 *tw32, short2 *twq, cudaStream_t s) {
     const int64_t count = N;
     const int threads = 256;

@@ -134,16 +134,19 @@ def test_full_256_cpi_batch_sampled(api, cpi256, form, prec):
     bp.query_error()
     got = out.cpu().numpy()
     rng = np.random.default_rng(60)
-    for c in list(rng.choice(256, 12, replace=False)) + [int(np.argmax([s.N for s in scs]))]:
+    # every CPI: its four corner cells (first / last lag x first / last bin), the
+    # direct path and 4 random cells
+    for c in range(256):
         sc, cp = scs[c], cpis[c]
-        lags = np.concatenate([[0, min(37, sc.nlags - 1)], rng.integers(0, sc.nlags, 14)])
-        bins = np.concatenate([[0, 5], rng.integers(sc.p0, sc.p0 + sc.nbins, 14)])
+        last_l, last_b = sc.nlags - 1, sc.p0 + sc.nbins - 1
+        lags = np.concatenate([[0, 0, last_l, last_l, 0], rng.integers(0, sc.nlags, 4)])
+        bins = np.concatenate([[sc.p0, last_b, sc.p0, last_b, 0], rng.integers(sc.p0, sc.p0 + sc.nbins, 4)])
         idx = cp["off_out"] + lags * sc.nbins + (bins - sc.p0)
         if q14:
             qs, qr = scenes.quantize_q14(sc.s_surv, 0.25), scenes.quantize_q14(sc.s_ref, 0.25)
             for l, b, i in zip(lags, bins, idx):
                 want, _ = oracle.caf_q14(qs, qr, int(l), 1, int(b), 1)
-                assert np.array_equal(got[i], want[0, 0])
+                assert np.array_equal(got[i], want[0, 0]), (c, l, b)
         else:
             want = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
             peak = abs(oracle.caf_cells(sc.s_surv, sc.s_ref, [0], [0], z32=True)[0])

@@ -1,7 +1,8 @@
 """The 2-SM pair tile of the tensor-core form (tcgen05 cta_group::2, tuning key
-1 = 258): the same units, chains and fold order as the one-CTA 256-row tile,
-so with the same split of the sample axis the surface is bit-identical to it;
-and within the fp32 bar of the oracle."""
+1 = 258): the same units, chains and fold order as the one-CTA 256-row tile
+with one row pair per bin (tuning key 6 = 1), so with the same split of the
+sample axis the surface is bit-identical to it; and within the fp32 bar of the
+oracle."""
 import numpy as np
 import pytest
 
@@ -41,6 +42,7 @@ def test_pair_tile_bit_identical_caf(api, N, nlags, nbins, split):
         p = api.Plan(N, p0=sc.p0, nbins=nbins, max_lags=nlags, form="ternary", prec="bf16x2")
         p.set_tuning(0, split)
         p.set_tuning(1, tile)
+        p.set_tuning(6, 1)  # one row pair per bin on both tiles: the pair tile has no conjugate pairing
         out.append(p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, nlags).cpu().numpy())
         p.query_error()
     assert np.array_equal(out[0], out[1])
