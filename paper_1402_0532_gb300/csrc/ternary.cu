@@ -1578,6 +1578,21 @@ constexpr int kPairPackKb = 16;  // K blocks (16 samples each) per packing tile
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
+// Real a (x) b = sgn(a) (sgn(b) |a| + b): the fma rounds sgn(b)(|a| + |b|)
+// once (round to nearest is sign-symmetric) and the outer sign is exact, so
+// this is |a| + |b| rounded once with the sign of Eq. 2; a zero operand gives
+// a zero (of either sign, which no later step distinguishes).
+__device__ __forceinline__ float ox_fma(float a, float sa, float b, float sb) { return sa * fmaf(sb, fabsf(a), b); }
+
+// Eq. 6 for the lag product s (x) c, c = conj(r) (or r with NDFT_F_NO_CONJ_REF).
+__device__ __forceinline__ float2 lag_ox(float2 s, float2 r, bool conj) {
+    const float cr = r.x, ci = conj ? -r.y : r.y;
+    const float ss_r = sgnf(s.x), ss_i = sgnf(s.y), sc_r = sgnf(cr), sc_i = sgnf(ci);
+    const float t1 = ox_fma(s.x, ss_r, cr, sc_r), t2 = ox_fma(s.y, ss_i, ci, sc_i);
+    const float t3 = ox_fma(s.y, ss_i, cr, sc_r), t4 = ox_fma(ci, sc_i, s.x, ss_r);
+    return make_float2(__fsub_rn(t1, t2), __fadd_rn(t3, t4));
+}
+
 __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, bool caf,
                                                    const float2 *__restrict__ a_base,
                                                    const float2 *__restrict__ r_base, uint4 *__restrict__ B,
@@ -1585,34 +1600,53 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
     const int t = threadIdx.x & 7;
     const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
     const bool live = col < P.ncols;  // whole 8-lane groups are live or not
-    const float2 *a = a_base + P.a_off;
+    const float2 *a = a_base + P.a_off + (caf ? 0 : (int64_t)col * P.ldx);
     const float2 *r = r_base + P.r_off;
     const int64_t ncols2 = 2LL * P.ncols;
+    const bool conj = !(flags & NDFT_F_NO_CONJ_REF), circ = (flags & NDFT_F_CIRCULAR_LAG) != 0;
+    const int N = P.N;
+    const int64_t lag = (int64_t)P.lag0 + col;
+    const bool vec = (reinterpret_cast<uintptr_t>(a) & 15u) == 0;  // rows of odd length start at 8 bytes
     for (int by = blockIdx.y; by < gy; by += gridDim.y) {
         const int kb0 = by * kPairPackKb;
         const int kb1 = min(kb0 + kPairPackKb, P.kblocks);
         float sr = 0.f, si = 0.f;
         if (live) {
             for (int kb = kb0; kb < kb1; ++kb) {
-                const int64_t i = (int64_t)kb * 16 + 2 * t;
+                const int i = kb * 16 + 2 * t;  // < 2^18 + 16
                 float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-                if (caf) {
-                    if (i < P.N) v0 = lag_product(P, a, r, col, i, flags);
-                    if (i + 1 < P.N) v1 = lag_product(P, a, r, col, i + 1, flags);
+                if (i + 1 < N && vec) {
+                    const float4 s2 = *reinterpret_cast<const float4 *>(a + i);  // i even, a 16-byte aligned
+                    v0 = make_float2(s2.x, s2.y);
+                    v1 = make_float2(s2.z, s2.w);
                 } else {
-                    const float2 *x = a + (int64_t)col * P.ldx;
-                    if (i < P.N) v0 = x[i];
-                    if (i + 1 < P.N) v1 = x[i + 1];
+                    if (i < N) v0 = a[i];
+                    if (i + 1 < N) v1 = a[i + 1];
+                }
+                if (caf) {
+                    int64_t j = (int64_t)i - lag;
+                    if (circ) {
+                        j %= N;
+                        if (j < 0) j += N;
+                    }
+                    int64_t j1 = j + 1;
+                    if (circ && j1 == N) j1 = 0;
+                    const float2 zero = make_float2(0.f, 0.f);
+                    const float2 r0 = (i < N && j >= 0 && j < N) ? r[j] : zero;
+                    const float2 r1 = (i + 1 < N && j1 >= 0 && j1 < N) ? r[j1] : zero;
+                    v0 = lag_ox(v0, r0, conj);
+                    v1 = lag_ox(v1, r1, conj);
                 }
                 const int64_t row = P.row0 + (int64_t)kb * ncols2 + 2LL * col;
                 uint32_t hr, lr, hi, li;
                 split2(v0.x, v1.x, hr, lr);
                 split2(v0.y, v1.y, hi, li);
-                const uint32_t sr2 = bf2(sgnf(v0.x), sgnf(v1.x)), si2 = bf2(sgnf(v0.y), sgnf(v1.y));
+                const float g0r = sgnf(v0.x), g1r = sgnf(v1.x), g0i = sgnf(v0.y), g1i = sgnf(v1.y);
+                const uint32_t sr2 = bf2(g0r, g1r), si2 = bf2(g0i, g1i);
                 B[row * 8 + t] = make_uint4(hr, lr, sr2, sr2);
                 B[(row + 1) * 8 + t] = make_uint4(hi, li, si2, si2);
-                sr += (v0.x + sgnf(v0.x)) + (v1.x + sgnf(v1.x));
-                si += (v0.y + sgnf(v0.y)) + (v1.y + sgnf(v1.y));
+                sr += (v0.x + g0r) + (v1.x + g1r);
+                si += (v0.y + g0i) + (v1.y + g1i);
             }
         }
 #pragma unroll
@@ -1624,31 +1658,49 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
     }
 }
 
-// Split-K sum and pair fold into the output [cols][nbins]: block x = output
-// column, its threads over the bins.  Bin p0 + k of the window is frequency
-// c = min(p, N - p), p = (p0 + k) mod N: c = 0 from the DC tiles; else slot
-// c - 1 of the partials [split][2 cols][2 S] (rows 2 s, 2 s + 1 = R, I;
-// columns 2 col, 2 col + 1 = r, i), each of a, b, d, e summed over the
-// splits in order, then combined for the sign of the bin.  Deterministic.
-__global__ void __launch_bounds__(256) k_pair_fold(const float *__restrict__ part, int nsplit, int64_t split_stride,
-                                                   int S, int N, int p0, int nbins, const float2 *__restrict__ dc,
-                                                   int gy, int ncols, float2 *__restrict__ out) {
+// Split-K sum and pair fold into the output [cols][nbins]: block (x, y) =
+// output column x, bins 256 y .. 256 y + 255, one bin per thread.  Bin p0 + k
+// of the window is frequency c = min(p, N - p), p = (p0 + k) mod N: c = 0 from
+// the DC tiles; else slot c - 1 of the partials [split][2 cols][2 S] (rows 2 s,
+// 2 s + 1 = R, I; columns 2 col, 2 col + 1 = r, i), each of a, b, d, e summed
+// over the splits in order, then combined for the sign of the bin.  The split
+// loads are issued ahead of the (ordered) additions.  Deterministic.
+constexpr int kFoldBins = 256;
+__global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict__ part, int nsplit,
+                                                         int64_t split_stride, int S, int N, int p0, int nbins,
+                                                         const float2 *__restrict__ dc, int gy, int ncols,
+                                                         float2 *__restrict__ out) {
     const int col = blockIdx.x;
+    const int k = blockIdx.y * kFoldBins + threadIdx.x;
     const int64_t S2 = 2LL * S;
-    const float *pr = part + (int64_t)(2 * col) * S2;      // column (col, r)
-    const float *pi = part + (int64_t)(2 * col + 1) * S2;  // column (col, i)
     float2 *o = out + (int64_t)col * nbins;
-    for (int k = threadIdx.x; k < nbins; k += blockDim.x) {
-        int64_t p = ((int64_t)p0 + k) % N;
-        if (p < 0) p += N;
-        const int64_t c = p <= N - p ? p : N - p;
-        if (c == 0) continue;
+    int64_t p = ((int64_t)p0 + k) % N;
+    if (p < 0) p += N;
+    const int64_t c = p <= N - p ? p : N - p;
+    if (k < nbins && c > 0) {
         const int64_t s = c - 1;
-        float2 ae = *reinterpret_cast<const float2 *>(pr + 2 * s);  // (a, e)
-        float2 db = *reinterpret_cast<const float2 *>(pi + 2 * s);  // (d, b)
-        for (int sp = 1; sp < nsplit; ++sp) {
-            const float2 u = *reinterpret_cast<const float2 *>(pr + sp * split_stride + 2 * s);
-            const float2 v = *reinterpret_cast<const float2 *>(pi + sp * split_stride + 2 * s);
+        const float2 *pr = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col) * S2 + 2 * s);      // (a, e)
+        const float2 *pi = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col + 1) * S2 + 2 * s);  // (d, b)
+        const int64_t st = split_stride / 2;  // float2 elements between splits
+        float2 ae = pr[0], db = pi[0];
+        int sp = 1;
+        for (; sp + 4 <= nsplit; sp += 4) {
+            float2 u[4], v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                u[q] = pr[(sp + q) * st];
+                v[q] = pi[(sp + q) * st];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ae.x = __fadd_rn(ae.x, u[q].x);
+                ae.y = __fadd_rn(ae.y, u[q].y);
+                db.x = __fadd_rn(db.x, v[q].x);
+                db.y = __fadd_rn(db.y, v[q].y);
+            }
+        }
+        for (; sp < nsplit; ++sp) {
+            const float2 u = pr[sp * st], v = pi[sp * st];
             ae.x = __fadd_rn(ae.x, u.x);
             ae.y = __fadd_rn(ae.y, u.y);
             db.x = __fadd_rn(db.x, v.x);
@@ -1657,24 +1709,22 @@ __global__ void __launch_bounds__(256) k_pair_fold(const float *__restrict__ par
         o[k] = p == c ? make_float2(__fsub_rn(ae.x, db.y), __fadd_rn(db.x, ae.y))
                       : make_float2(__fadd_rn(ae.x, db.y), __fsub_rn(db.x, ae.y));
     }
-    // bin 0 (if in the window): the DC tiles in a fixed order, warp 0
-    if (threadIdx.x < 32) {
-        int64_t k0 = (-(int64_t)p0) % N;
-        if (k0 < 0) k0 += N;
-        if (k0 < nbins) {
-            float sr = 0.f, si = 0.f;
-            for (int g = threadIdx.x; g < gy; g += 32) {
-                const float2 v = dc[(int64_t)g * ncols + col];
-                sr = __fadd_rn(sr, v.x);
-                si = __fadd_rn(si, v.y);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                sr = __fadd_rn(sr, __shfl_xor_sync(0xffffffffu, sr, off));
-                si = __fadd_rn(si, __shfl_xor_sync(0xffffffffu, si, off));
-            }
-            if (threadIdx.x == 0) o[k0] = make_float2(sr, si);
+    // bin 0 (if in this block's bins): the DC tiles in a fixed order, warp 0
+    int64_t k0 = (-(int64_t)p0) % N;
+    if (k0 < 0) k0 += N;
+    if (threadIdx.x < 32 && k0 < nbins && k0 / kFoldBins == blockIdx.y) {
+        float sr = 0.f, si = 0.f;
+        for (int g = threadIdx.x; g < gy; g += 32) {
+            const float2 v = dc[(int64_t)g * ncols + col];
+            sr = __fadd_rn(sr, v.x);
+            si = __fadd_rn(si, v.y);
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sr = __fadd_rn(sr, __shfl_xor_sync(0xffffffffu, sr, off));
+            si = __fadd_rn(si, __shfl_xor_sync(0xffffffffu, si, off));
+        }
+        if (threadIdx.x == 0) o[k0] = make_float2(sr, si);
     }
 }
 
@@ -2076,8 +2126,8 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     *launches += 1;
     p.last_variant = 2;
     p.last_nsplit = P.nsplit;
-    k_pair_fold<<<ncols, 256, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc, gy, ncols,
-                                      static_cast<float2 *>(out));
+    k_pair_fold<<<dim3(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins), kFoldBins, 0, s>>>(
+        part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc, gy, ncols, static_cast<float2 *>(out));
     *launches += 1;
     return cudaGetLastError();
 }
