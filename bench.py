@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--parts", type=int, default=-1,
                     help="tensor-core column parts (tuning key 5: 1 one part, the default; 0 two parts); "
                          "implies --no-tune")
-    ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "nfft", "adjoint"],
+    ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "direct-q14", "nfft", "adjoint"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
 
@@ -80,6 +80,16 @@ def profile_other(args, api, scenes, dev):
         step = lambda: plan.caf(ss, sr, 0, NLAGS, out=out)  # noqa: E731
         units = NLAGS * NBINS
         what = f"direct-form CAF, N={N}, {NLAGS} lags x {NBINS} bins"
+    elif args.profile_form == "direct-q14":
+        # the plain form in Q1.14 on the workload's scene (inputs quantised at 2^-2)
+        scene = scenes.radar_scene(N=N)
+        ss = torch.from_numpy(scenes.quantize_q14(scene.s_surv, 0.25)).to(dev)
+        sr = torch.from_numpy(scenes.quantize_q14(scene.s_ref, 0.25)).to(dev)
+        plan = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="direct", prec="q14", device=dev)
+        out = torch.empty(NLAGS, NBINS, 2, dtype=torch.int32, device=dev)
+        step = lambda: plan.caf(ss, sr, 0, NLAGS, out=out)  # noqa: E731
+        units = NLAGS * NBINS
+        what = f"direct-form CAF in Q1.14, N={N}, {NLAGS} lags x {NBINS} bins"
     elif args.profile_form == "adjoint":
         # both gradients of the workload's surface on the tensor cores (the
         # G-storing adjoint contraction and the fold)

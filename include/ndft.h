@@ -47,7 +47,7 @@ typedef enum {
     NDFT_E_CUDA = 3,         /* a CUDA runtime call or launch failed */
     NDFT_E_NOMEM = 4,        /* device allocation at plan time failed */
     NDFT_E_TIMEOUT = 5,      /* a bounded device-side wait ran out (see ndft_query_error) */
-    NDFT_E_OVERFLOW = 6      /* reserved: fixed-point range report */
+    NDFT_E_OVERFLOW = 6      /* a Q1.14 sum left int32 (plans with NDFT_F_Q14_RANGE; see ndft_query_error) */
 } ndft_status;
 
 typedef enum {
@@ -76,6 +76,17 @@ typedef enum {
 #define NDFT_F_NFFT_DIF 0x4u     /* NFFT by decimation in frequency (Sec. 3 names both
                                     FFT orders; the (x) butterflies make them differ):
                                     nfft_exec, and ndft_exec / caf_exec on NFFT plans */
+#define NDFT_F_ABS_OUT 0x10u     /* caf_exec writes the magnitude surface |A| (fp32,
+                                    [nlags][nbins]; |A| = sqrt(re^2 + im^2), each step
+                                    rounded once) from the epilogue instead of A, on
+                                    DIRECT fp32 and TERNARY_GEMM plans (single-CPI);
+                                    ndft_exec returns NDFT_E_UNSUPPORTED on such plans */
+#define NDFT_F_Q14_RANGE 0x8u    /* Q1.14 plans only: keep every output cell's sum exact
+                                    (int64) besides the int32 result modulo 2^32, and
+                                    report a cell whose sum left the int32 range through
+                                    ndft_query_error (NDFT_E_OVERFLOW).  The output is
+                                    the same either way; the sample axis of caf_exec
+                                    is not split on such plans */
 
 /* Plan descriptor.  Output bins are k = p0 .. p0 + nbins - 1 (signed, taken
  * modulo N); nbins = 0 means N bins starting at p0. */
@@ -226,7 +237,11 @@ ndft_status ndft_argmax(const void *X, int64_t rows, int64_t cols, int64_t *idx,
 /* ---- diagnostics ------------------------------------------------------------- */
 
 /* Synchronises `stream`, returns the plan's device error word as a status
- * (NDFT_OK if none) and clears it. */
+ * (NDFT_OK if none) and clears it: NDFT_E_TIMEOUT (a bounded wait ran out),
+ * NDFT_E_OVERFLOW (a Q1.14 output cell's exact sum left int32, on plans with
+ * NDFT_F_Q14_RANGE; the cell holds the sum modulo 2^32), NDFT_E_CUDA
+ * (another device-side check).  The first error recorded since the last
+ * query wins. */
 ndft_status ndft_query_error(ndft_plan_t plan, cudaStream_t stream);
 
 /* Copies one of the plan's tables to caller memory: which = 0 -> fp32

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_PKG, "libndft.so")
 OK, E_INVALID, E_UNSUPPORTED, E_CUDA, E_NOMEM, E_TIMEOUT, E_OVERFLOW = range(7)
 FORM_DIRECT, FORM_TERNARY_GEMM, FORM_NFFT, FORM_FFT = 0, 1, 2, 3
 PREC_FP32, PREC_BF16X2, PREC_Q14 = 0, 1, 2
-F_NO_CONJ_REF, F_CIRCULAR_LAG, F_NFFT_DIF = 0x1, 0x2, 0x4
+F_NO_CONJ_REF, F_CIRCULAR_LAG, F_NFFT_DIF, F_Q14_RANGE, F_ABS_OUT = 0x1, 0x2, 0x4, 0x8, 0x10
 
 # every symbol include/ndft.h declares
 EXPORTS = ("ndft_plan", "ndft_plan_batched", "ndft_plan_destroy", "ndft_exec", "nfft_exec", "caf_exec",

@@ -12,7 +12,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from ._lib import F_CIRCULAR_LAG, F_NFFT_DIF, F_NO_CONJ_REF  # noqa: F401  (plan flags)
+from ._lib import F_ABS_OUT, F_CIRCULAR_LAG, F_NFFT_DIF, F_NO_CONJ_REF, F_Q14_RANGE  # noqa: F401  (plan flags)
 
 _FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM, "nfft": L.FORM_NFFT, "fft": L.FORM_FFT}
 _PRECS = {"fp32": L.PREC_FP32, "bf16x2": L.PREC_BF16X2, "q14": L.PREC_Q14}
@@ -168,12 +168,14 @@ class Plan:
 
     def caf(self, s_surv: torch.Tensor, s_ref: torch.Tensor, lag0: int, nlags: int,
             out: torch.Tensor | None = None) -> torch.Tensor:
-        """Eq. 12a surface [nlags, nbins] (complex64, or [nlags, nbins, 2] int32 for q14)."""
+        """Eq. 12a surface [nlags, nbins] (complex64, [nlags, nbins, 2] int32 for q14, or the
+        magnitudes [nlags, nbins] float32 on plans with F_ABS_OUT)."""
         _need(s_surv, self._in_dtype, "s_surv")
         _need(s_ref, self._in_dtype, "s_ref")
+        odt = torch.float32 if self.flags & F_ABS_OUT else self._out_dtype
         if out is None:
-            out = torch.empty((nlags,) + self._row_shape(self.nbins), dtype=self._out_dtype, device=s_surv.device)
-        _need(out, self._out_dtype, "out")
+            out = torch.empty((nlags,) + self._row_shape(self.nbins), dtype=odt, device=s_surv.device)
+        _need(out, odt, "out")
         L.check(self.lib.caf_exec(self.handle, _ptr(s_surv), _ptr(s_ref), int(lag0), int(nlags), _ptr(out),
                                   _stream(s_surv.device)), "caf_exec")
         return out

@@ -15,9 +15,16 @@
 // fma(sgn a, fma(sgn b, |a|, b), acc) = acc + sgn(a) sgn(b)(|a| + |b|), the
 // inner sum rounded once and the product by sgn a exact, so it rounds exactly
 // as acc + (a (x) b) (Eq. 1-2, the zero case explicit as a zero sign).
-// Q1.14: magnitude, sign mask and nonzero mask; one real (x) is an integer add
-// of magnitudes with the sign applied by XOR and the zero case by AND.  One
-// complex (x) is four real ones (Eq. 6).
+// Q1.14: the same two fmas on exact integers.  A twiddle has |W_r| + |W_i| <=
+// 2^14 sqrt 2 < 23171; a data value (int16, or the integer lag product
+// z = s (x) conj(r), |z_r| + |z_i| <= 2 (|s_r| + |s_i| + |r_r| + |r_i|) <= 2^18)
+// keeps sgn(b)(|a| + |b|) below 2^18 + 2^14, and one sample adds at most
+// 23171 + 2^18 < 285315 to a component's sum: 48 samples (three chunks) stay
+// below 2^24, so every fp32 operation is exact, and every three chunks the sums
+// are converted to integers and added into int32 totals modulo 2^32 -- the
+// integer (x) of Eq. 2 with wrap-around sums, bit for bit.  With NDFT_F_Q14_RANGE the totals are
+// kept exact in int64 (shared memory) and a cell whose sum leaves int32 sets
+// the plan's overflow code.  One complex (x) is four real ones (Eq. 6).
 #include "internal.cuh"
 
 #include <algorithm>
@@ -35,6 +42,7 @@ constexpr int kThreads = 256;
 // ---- precision traits ---------------------------------------------------------
 struct PrecF32 {
     static constexpr bool kTwoLevel = true;  // see direct_tile
+    static constexpr bool kIntFlush = false;
     using In = float2;
     using Tw = float2;
     using V = float2;
@@ -75,13 +83,14 @@ struct PrecF32 {
 };
 
 struct PrecQ14 {
-    static constexpr bool kTwoLevel = false;  // integer sums are exact (modulo 2^32)
+    static constexpr bool kTwoLevel = false;
+    static constexpr bool kIntFlush = true;  // exact fp32 chunk sums -> int32 totals (wrap)
     using In = short2;
     using Tw = short2;
     using V = int2;
-    using Mag = int2;
-    using Sgn = uint4;  // sign masks, nonzero masks
-    using Acc = uint2;  // two's complement wrap
+    using Mag = float2;  // twiddle: |w|; data: the value itself (exact integers)
+    using Sgn = float2;  // signs in {-1, 0, +1}
+    using Acc = float2;  // one chunk's sums, exact integers < 2^24
     __device__ static V load(const In *p, int64_t i) {
         const short2 v = p[i];
         return make_int2(v.x, v.y);
@@ -89,28 +98,24 @@ struct PrecQ14 {
     __device__ static V zero() { return make_int2(0, 0); }
     __device__ static V conj_(V v) { return make_int2(v.x, -v.y); }
     __device__ static V cox(V a, V b) { return cox_i32(a, b); }
+    __device__ static float sgn1(int v) { return v > 0 ? 1.f : (v < 0 ? -1.f : 0.f); }
+    // exact int -> float for |v| < 2^22 on the integer and fp32 pipes: the bits
+    // v + 0x4B400000 are the float 1.5 2^23 + v (the conversion instruction
+    // runs on a quarter-rate pipe)
+    __device__ static float i2f(int v) { return __int_as_float(v + 0x4B400000) - 12582912.0f; }
     __device__ static void ready(V v, Mag &m, Sgn &s) {
-        m = make_int2(abs(v.x), abs(v.y));
-        s = make_uint4(v.x < 0 ? 0xffffffffu : 0u, v.y < 0 ? 0xffffffffu : 0u, v.x ? 0xffffffffu : 0u,
-                       v.y ? 0xffffffffu : 0u);
+        m = make_float2(i2f(abs(v.x)), i2f(abs(v.y)));
+        s = make_float2(sgn1(v.x), sgn1(v.y));
     }
-    __device__ static void ready_data(V v, Mag &m, Sgn &s) { ready(v, m, s); }
-    __device__ static Acc acc0() { return make_uint2(0u, 0u); }
-    __device__ static uint32_t ox(int am, uint32_t as, uint32_t az, int bm, uint32_t bs, uint32_t bz) {
-        const uint32_t m = (uint32_t)(am + bm);
-        const uint32_t sx = as ^ bs;
-        return ((m ^ sx) - sx) & az & bz;
+    __device__ static void ready_data(V v, Mag &m, Sgn &s) {
+        m = make_float2(i2f(v.x), i2f(v.y));
+        s = make_float2(sgn1(v.x), sgn1(v.y));
     }
-    __device__ static void mac(Acc &acc, const Mag &wm, const Sgn &ws, const Mag &vm, const Sgn &vs) {
-        const uint32_t t1 = ox(wm.x, ws.x, ws.z, vm.x, vs.x, vs.z);
-        const uint32_t t2 = ox(wm.y, ws.y, ws.w, vm.y, vs.y, vs.w);
-        const uint32_t t3 = ox(wm.y, ws.y, ws.w, vm.x, vs.x, vs.z);
-        const uint32_t t4 = ox(vm.y, vs.y, vs.w, wm.x, ws.x, ws.z);
-        acc.x += t1 - t2;
-        acc.y += t3 + t4;
+    __device__ static Acc acc0() { return make_float2(0.f, 0.f); }
+    __device__ static void mac(Acc &acc, const Mag &wm, const Sgn &ws, const Mag &vv, const Sgn &vs) {
+        PrecF32::mac(acc, wm, ws, vv, vs);
     }
     using Out = uint2;
-    __device__ static uint2 out(const Acc &a) { return a; }
 };
 
 template <class P>
@@ -157,11 +162,17 @@ struct Smem {
     }
     // fp32: each thread's 16 outer accumulators [cell][thread] after the staging
     static constexpr size_t kOuter = 16 * kThreads * sizeof(float2);
-    template <class P>
+    // Q1.14 with the range check: each thread's 16 exact int64 totals (Re, Im) [2 cell + c][thread]
+    static constexpr size_t kTot64 = 32 * kThreads * sizeof(long long);
+    template <class P, bool CHK = false>
     static constexpr size_t bytes_for() {
-        return bytes(sizeof(typename P::Mag), sizeof(typename P::Sgn)) + (P::kTwoLevel ? kOuter : 0);
+        return bytes(sizeof(typename P::Mag), sizeof(typename P::Sgn)) + (P::kTwoLevel ? kOuter : 0) +
+               (CHK ? kTot64 : 0);
     }
 };
+
+// Q1.14: chunks per exact fp32 partial sum (see the bound above)
+constexpr int kIntFlushChunks = 3;
 
 // fp32 sums run in two levels: the register accumulators take kFlushChunks
 // chunks (1024 samples) and are then added into per-thread outer sums in
@@ -172,11 +183,12 @@ constexpr int kFlushChunks = 64;
 
 // One 64 x 64 tile over samples [n_begin, n_end).  out points at the tile's
 // [col][bin] destination with row stride ldo.
-template <class P, class Src>
+template <class P, class Src, bool CHK = false>
 __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename P::Tw *__restrict__ tw, int N,
                                             int p0, int nbins, int ncols, int bin0, int col0, int64_t n_begin,
                                             int64_t n_end, const Src &src, typename P::Out *__restrict__ out,
-                                            int64_t ldo) {
+                                            int64_t ldo, int32_t *err) {
+    static_assert(!CHK || P::kIntFlush, "the range check is for the integer form");
     using Mag = typename P::Mag;
     Mag *tM = reinterpret_cast<Mag *>(smem);
     using Sgn = typename P::Sgn;
@@ -212,6 +224,19 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
     if constexpr (P::kTwoLevel) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) outer[c * kThreads + tid] = make_float2(0.f, 0.f);
+    }
+    // integer form: int32 totals modulo 2^32, or exact int64 totals in shared memory (CHK)
+    uint2 tot[4][4];
+    long long *tot64 = reinterpret_cast<long long *>(smem + Smem::bytes(sizeof(Mag), sizeof(Sgn)));
+    if constexpr (P::kIntFlush) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tot[i][j] = make_uint2(0u, 0u);
+        if constexpr (CHK) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) tot64[c * kThreads + tid] = 0;
+        }
     }
     int chunk_count = 0;
 
@@ -260,6 +285,27 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
                 for (int j = 0; j < 4; ++j) P::mac(acc[i][j], wm[i], ws[i], vm[j], vs[j]);
         }
         __syncthreads();
+        if constexpr (P::kIntFlush) {
+            // every kIntFlushChunks chunks (and after the last) the exact integer
+            // sums (< 2^24 in magnitude) into the totals
+            if (++chunk_count == kIntFlushChunks || n0 + KC >= n_end) {
+            chunk_count = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int rx = __float2int_rn(acc[i][j].x), ry = __float2int_rn(acc[i][j].y);
+                    if constexpr (CHK) {
+                        tot64[(2 * (i * 4 + j)) * kThreads + tid] += rx;
+                        tot64[(2 * (i * 4 + j) + 1) * kThreads + tid] += ry;
+                    } else {
+                        tot[i][j].x += (uint32_t)rx;
+                        tot[i][j].y += (uint32_t)ry;
+                    }
+                    acc[i][j] = P::acc0();
+                }
+            }
+        }
         if constexpr (P::kTwoLevel) {
             if (++chunk_count == kFlushChunks) {
                 chunk_count = 0;
@@ -284,6 +330,20 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
             }
     }
 
+    if constexpr (CHK) {
+        bool wrapped = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long vx = tot64[(2 * (i * 4 + j)) * kThreads + tid];
+                const long long vy = tot64[(2 * (i * 4 + j) + 1) * kThreads + tid];
+                const bool live = (col0 + tx + 16 * j < ncols) && (bin0 + ty * 4 + i < nbins);
+                wrapped |= live && (vx != (long long)(int32_t)vx || vy != (long long)(int32_t)vy);
+                tot[i][j] = make_uint2((uint32_t)(unsigned long long)vx, (uint32_t)(unsigned long long)vy);
+            }
+        if (wrapped) dev_set_error(err, kDevOverflow);
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int col = col0 + tx + 16 * j;
@@ -291,33 +351,36 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int b = bin0 + ty * 4 + i;
-            if (b < nbins) out[(int64_t)col * ldo + b] = P::out(acc[i][j]);
+            if (b < nbins) {
+                if constexpr (P::kIntFlush) out[(int64_t)col * ldo + b] = tot[i][j];
+                else out[(int64_t)col * ldo + b] = acc[i][j];
+            }
         }
     }
 }
 
-template <class P, class Src>
+template <class P, class Src, bool CHK = false>
 __global__ void __launch_bounds__(kThreads, 2)
     k_direct(const typename P::Tw *__restrict__ tw, int N, int p0, int nbins, int ncols, Src src,
-             int64_t samples_per_split, typename P::Out *__restrict__ out) {
+             int64_t samples_per_split, typename P::Out *__restrict__ out, int32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int bin0 = blockIdx.x * BP;
     const int col0 = blockIdx.y * BC;
     const int64_t n_begin = (int64_t)blockIdx.z * samples_per_split;
     const int64_t n_end = min((int64_t)N, n_begin + samples_per_split);
     typename P::Out *o = out + (int64_t)blockIdx.z * ncols * nbins;
-    direct_tile<P, Src>(smem, tw, N, p0, nbins, ncols, bin0, col0, n_begin, n_end, src, o, nbins);
+    direct_tile<P, Src, CHK>(smem, tw, N, p0, nbins, ncols, bin0, col0, n_begin, n_end, src, o, nbins, err);
 }
 
 // Persistent kernel over the CPI work list of a batched plan.  Unit u of the
 // list encodes (cpi, bin tile, lag tile); units are fetched with an atomic
 // counter, longest CPIs first, and each writes its tile of that CPI's surface.
-template <class P>
+template <class P, bool CHK = false>
 __global__ void __launch_bounds__(kThreads, 2)
     k_direct_batched(const CpiDev *__restrict__ cpis, const int32_t *__restrict__ work, int64_t nwork,
                      int32_t *__restrict__ counter, const unsigned char *__restrict__ tab_arena,
                      const typename P::In *__restrict__ surv, const typename P::In *__restrict__ ref,
-                     typename P::Out *__restrict__ outb, uint32_t flags) {
+                     typename P::Out *__restrict__ outb, uint32_t flags, int32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t s_unit;
     for (;;) {
@@ -330,8 +393,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const CpiDev cp = cpis[c];
         const typename P::Tw *tw = reinterpret_cast<const typename P::Tw *>(tab_arena) + cp.tw_off;
         CafSrc<P> src{surv + cp.off_surv, ref + cp.off_ref, cp.n, cp.lag0, flags};
-        direct_tile<P, CafSrc<P>>(smem, tw, cp.n, cp.p0, cp.nbins, cp.nlags, bt * BP, lt * BC, 0, cp.n, src,
-                                  outb + cp.off_out, cp.nbins);
+        direct_tile<P, CafSrc<P>, CHK>(smem, tw, cp.n, cp.p0, cp.nbins, cp.nlags, bt * BP, lt * BC, 0, cp.n,
+                                       src, outb + cp.off_out, cp.nbins, err);
     }
 }
 
@@ -385,7 +448,16 @@ cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t ba
         timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, (int)batch,
                                      NdftSrc<PrecF32>{static_cast<const float2 *>(x), N}, N,
-                                     static_cast<float2 *>(X));
+                                     static_cast<float2 *>(X), p.err);
+        timer_end(p, s);
+    } else if (p.d.flags & NDFT_F_Q14_RANGE) {
+        const size_t sm = Smem::bytes_for<PrecQ14, true>();
+        auto k = k_direct<PrecQ14, NdftSrc<PrecQ14>, true>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        timer_begin(p, s);
+        k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, (int)batch,
+                                     NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, N,
+                                     static_cast<uint2 *>(X), p.err);
         timer_end(p, s);
     } else {
         const size_t sm = Smem::bytes_for<PrecQ14>();
@@ -394,7 +466,7 @@ cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t ba
         timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, (int)batch,
                                      NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, N,
-                                     static_cast<uint2 *>(X));
+                                     static_cast<uint2 *>(X), p.err);
         timer_end(p, s);
     }
     *launches += 1;
@@ -412,13 +484,16 @@ cudaError_t direct_caf_preload() {
 cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_ref, int lag0, int nlags,
                               void *A, cudaStream_t s, int *launches) {
     const int N = p.d.n, nb = p.d.nbins ? p.d.nbins : N;
-    const int nsplit = direct_caf_splits(N, nlags, nb, p.sm_count, p.tune_split);
+    const bool chk = p.d.prec == NDFT_PREC_Q14 && (p.d.flags & NDFT_F_Q14_RANGE);
+    // the range check needs every cell's whole sum in one block: no split
+    const int nsplit = chk ? 1 : direct_caf_splits(N, nlags, nb, p.sm_count, p.tune_split);
     const int64_t per = ((int64_t)N + nsplit - 1) / nsplit;
     const int64_t per_al = ((per + KC - 1) / KC) * KC;
     const int ns = (int)((N + per_al - 1) / per_al);
     dim3 grid((nb + BP - 1) / BP, (nlags + BC - 1) / BC, ns);
     cudaError_t e;
-    const bool direct_out = (ns == 1);
+    const bool abs_out = (p.d.flags & NDFT_F_ABS_OUT) != 0;
+    const bool direct_out = (ns == 1) && !abs_out;  // |A| is formed by the split sum
     if (p.d.prec == NDFT_PREC_FP32) {
         const size_t sm = Smem::bytes_for<PrecF32>();
         auto k = k_direct<PrecF32, CafSrc<PrecF32>>;
@@ -427,25 +502,37 @@ cudaError_t launch_direct_caf(const Plan &p, const void *s_surv, const void *s_r
         CafSrc<PrecF32> src{static_cast<const float2 *>(s_surv), static_cast<const float2 *>(s_ref), N, lag0,
                             p.d.flags};
         timer_begin(p, s);
-        k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, nlags, src, per_al, dst);
+        k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, nlags, src, per_al, dst, p.err);
         timer_end(p, s);
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (!direct_out) {
             *launches += 1;
+            if (abs_out)
+                return launch_reduce_abs(static_cast<const float2 *>(p.ws), ns, (int64_t)nlags * nb,
+                                         static_cast<float *>(A), s);
             return launch_reduce_splits(static_cast<const float *>(p.ws), ns, (int64_t)nlags * nb * 2,
                                         static_cast<float *>(A), s);
         }
     } else {
-        const size_t sm = Smem::bytes_for<PrecQ14>();
-        auto k = k_direct<PrecQ14, CafSrc<PrecQ14>>;
-        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         uint2 *dst = direct_out ? static_cast<uint2 *>(A) : static_cast<uint2 *>(p.ws);
         CafSrc<PrecQ14> src{static_cast<const short2 *>(s_surv), static_cast<const short2 *>(s_ref), N, lag0,
                             p.d.flags};
-        timer_begin(p, s);
-        k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, nlags, src, per_al, dst);
-        timer_end(p, s);
+        if (chk) {
+            const size_t sm = Smem::bytes_for<PrecQ14, true>();
+            auto k = k_direct<PrecQ14, CafSrc<PrecQ14>, true>;
+            if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+            timer_begin(p, s);
+            k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, nlags, src, per_al, dst, p.err);
+            timer_end(p, s);
+        } else {
+            const size_t sm = Smem::bytes_for<PrecQ14>();
+            auto k = k_direct<PrecQ14, CafSrc<PrecQ14>>;
+            if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+            timer_begin(p, s);
+            k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, nlags, src, per_al, dst, p.err);
+            timer_end(p, s);
+        }
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (!direct_out) {
@@ -470,7 +557,17 @@ cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *r
         k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
                                      static_cast<const unsigned char *>(p.tab_arena),
                                      static_cast<const float2 *>(surv), static_cast<const float2 *>(ref),
-                                     static_cast<float2 *>(out), p.d.flags);
+                                     static_cast<float2 *>(out), p.d.flags, p.err);
+        timer_end(p, s);
+    } else if (p.d.flags & NDFT_F_Q14_RANGE) {
+        const size_t sm = Smem::bytes_for<PrecQ14, true>();
+        auto k = k_direct_batched<PrecQ14, true>;
+        if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        timer_begin(p, s);
+        k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
+                                     static_cast<const unsigned char *>(p.tab_arena),
+                                     static_cast<const short2 *>(surv), static_cast<const short2 *>(ref),
+                                     static_cast<uint2 *>(out), p.d.flags, p.err);
         timer_end(p, s);
     } else {
         const size_t sm = Smem::bytes_for<PrecQ14>();
@@ -480,7 +577,7 @@ cudaError_t launch_direct_batched(const Plan &p, const void *surv, const void *r
         k<<<grid, kThreads, sm, s>>>(p.cpis_dev, p.work_dev, p.nwork, p.counter,
                                      static_cast<const unsigned char *>(p.tab_arena),
                                      static_cast<const short2 *>(surv), static_cast<const short2 *>(ref),
-                                     static_cast<uint2 *>(out), p.d.flags);
+                                     static_cast<uint2 *>(out), p.d.flags, p.err);
         timer_end(p, s);
     }
     *launches += 1;

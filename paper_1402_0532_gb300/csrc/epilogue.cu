@@ -32,6 +32,21 @@ __global__ void k_reduce_f32(const float *__restrict__ ws, int nsplit, int64_t c
     }
 }
 
+// Split-K sum of complex partials [nsplit][count] (float2), in split order,
+// then the magnitude sqrt(re^2 + im^2) with each operation rounded once.
+__global__ void k_reduce_abs(const float2 *__restrict__ ws, int nsplit, int64_t count, float *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        float2 a = ws[i];
+        for (int s = 1; s < nsplit; ++s) {
+            const float2 b = ws[(int64_t)s * count + i];
+            a.x = __fadd_rn(a.x, b.x);
+            a.y = __fadd_rn(a.y, b.y);
+        }
+        out[i] = __fsqrt_rn(__fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y)));
+    }
+}
+
 __global__ void k_reduce_u32(const uint32_t *__restrict__ ws, int nsplit, int64_t count, uint32_t *__restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
@@ -103,6 +118,11 @@ cudaError_t reduce_preload() {
 
 cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s) {
     k_reduce_f32<<<grid_for(count / 4 + 1, 256), 256, 0, s>>>(ws, nsplit, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_abs(const float2 *ws, int nsplit, int64_t count, float *out, cudaStream_t s) {
+    k_reduce_abs<<<grid_for(count, 256), 256, 0, s>>>(ws, nsplit, count, out);
     return cudaGetLastError();
 }
 

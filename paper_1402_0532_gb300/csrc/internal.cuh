@@ -20,7 +20,7 @@ inline bool lag_window_ok(int32_t lag0, int32_t nlags) {
 }
 
 // Device error codes written to the plan's error word (first writer wins).
-enum DevErr : int32_t { kDevOk = 0, kDevTimeout = 5, kDevBadIndex = 7 };
+enum DevErr : int32_t { kDevOk = 0, kDevTimeout = 5, kDevOverflow = 6, kDevBadIndex = 7 };
 
 // One CPI of a batched plan, as the kernels see it (device copy).
 struct CpiDev {
@@ -187,6 +187,8 @@ cudaError_t launch_fft_caf(const Plan &p, const void *s_surv, const void *s_ref,
 // epilogue.cu
 cudaError_t launch_reduce_splits(const float *ws, int nsplit, int64_t count, float *out, cudaStream_t s);
 cudaError_t reduce_preload();  // loads the fp32 split-sum kernel's module (no launch)
+// complex partials [nsplit][count] -> |sum| (fp32) per cell
+cudaError_t launch_reduce_abs(const float2 *ws, int nsplit, int64_t count, float *out, cudaStream_t s);
 cudaError_t launch_reduce_splits_i32(const uint32_t *ws, int nsplit, int64_t count, uint32_t *out,
                                      cudaStream_t s);
 cudaError_t launch_argmax(const float2 *X, int64_t rows, int64_t cols, int64_t *idx, float *val,

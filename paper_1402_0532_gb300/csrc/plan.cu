@@ -5,6 +5,8 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <cstdarg>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -28,6 +30,50 @@ struct Range {
 
 bool aligned16(const void *ptr) { return ptr && ((uintptr_t)ptr & 15u) == 0; }
 
+// NDFT_LOG=1 in the environment: one line on stderr per plan creation and per
+// exec call (what ran and how), read once at the first call.
+bool log_on() {
+    static const bool on = [] {
+        const char *v = std::getenv("NDFT_LOG");
+        return v && *v && std::strcmp(v, "0") != 0;
+    }();
+    return on;
+}
+
+void logf(const char *fmt, ...) {
+    if (!log_on()) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "[ndft] %s\n", buf);
+}
+
+const char *form_name(int f) {
+    switch (f) {
+        case NDFT_FORM_DIRECT: return "direct";
+        case NDFT_FORM_TERNARY_GEMM: return "ternary";
+        case NDFT_FORM_NFFT: return "nfft";
+        case NDFT_FORM_FFT: return "fft";
+    }
+    return "?";
+}
+
+const char *prec_name(int q) {
+    return q == NDFT_PREC_FP32 ? "fp32" : q == NDFT_PREC_BF16X2 ? "bf16x2" : q == NDFT_PREC_Q14 ? "q14" : "?";
+}
+
+const char *variant_name(int v) { return v == 2 ? "paired" : v == 1 ? "unpaired" : "-"; }
+
+ndft_status log_exec(const char *what, const Plan &p, int64_t cols, ndft_status st) {
+    if (log_on())
+        logf("%s N=%d bins=%d@%d cols=%lld form=%s prec=%s variant=%s splits=%d launches=%d status=%d", what, p.d.n,
+             p.d.nbins, p.d.p0, (long long)cols, form_name(p.d.form), prec_name(p.d.prec),
+             variant_name(p.last_variant), p.last_nsplit, p.last_launches, (int)st);
+    return st;
+}
+
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 
 ndft_status from_cuda(cudaError_t e) {
@@ -46,7 +92,8 @@ bool valid_pair(int form, int prec) {
     return false;
 }
 
-constexpr uint32_t kKnownFlags = NDFT_F_NO_CONJ_REF | NDFT_F_CIRCULAR_LAG | NDFT_F_NFFT_DIF;
+constexpr uint32_t kKnownFlags =
+    NDFT_F_NO_CONJ_REF | NDFT_F_CIRCULAR_LAG | NDFT_F_NFFT_DIF | NDFT_F_Q14_RANGE | NDFT_F_ABS_OUT;
 
 bool fft_form(int form) { return form == NDFT_FORM_NFFT || form == NDFT_FORM_FFT; }
 constexpr int32_t kMaxN = 1 << 22;
@@ -129,6 +176,9 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
         const bool known = (d->form >= 0 && d->form <= 3) && (d->prec >= 0 && d->prec <= 2);
         return known ? NDFT_E_UNSUPPORTED : NDFT_E_INVALID;
     }
+    if ((d->flags & NDFT_F_Q14_RANGE) && d->prec != NDFT_PREC_Q14) return NDFT_E_INVALID;
+    if ((d->flags & NDFT_F_ABS_OUT) && d->prec == NDFT_PREC_Q14) return NDFT_E_INVALID;
+    if ((d->flags & NDFT_F_ABS_OUT) && fft_form(d->form)) return NDFT_E_UNSUPPORTED;
     if (fft_form(d->form) && (!pow2(d->n) || d->n > 65536)) return NDFT_E_INVALID;
     if (d->form == NDFT_FORM_TERNARY_GEMM && !ternary_supported(*d)) return NDFT_E_UNSUPPORTED;
     auto *h = new (std::nothrow) ndft_plan_s();
@@ -164,6 +214,9 @@ ndft_status ndft_plan(ndft_plan_t *out, const ndft_desc *d, cudaStream_t stream)
     if ((e = launch_tables(N, p.tw32, p.twq, stream)) != cudaSuccess) goto fail;
     if (tern && (e = ternary_plan_init(p, stream)) != cudaSuccess) goto fail;
     *out = h;
+    logf("ndft_plan N=%d bins=%d@%d max_lags=%d max_batch=%lld form=%s prec=%s flags=0x%x bytes=%zu paired_freqs=%d",
+         p.d.n, p.d.nbins, p.d.p0, p.d.max_lags, (long long)p.d.max_batch, form_name(p.d.form), prec_name(p.d.prec),
+         p.d.flags, p.table_bytes + p.ws_bytes, p.pair_slots);
     return NDFT_OK;
 fail:
     free_plan(p);
@@ -188,6 +241,7 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
     p.last_variant = p.last_nsplit = 0;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X) || x == X) return NDFT_E_INVALID;
+    if (p.d.flags & NDFT_F_ABS_OUT) return NDFT_E_UNSUPPORTED;
     cudaError_t e;
     if (p.d.form == NDFT_FORM_DIRECT) {
         if (batch > 65535LL * 64) return NDFT_E_UNSUPPORTED;
@@ -199,7 +253,7 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
     } else {
         e = launch_ternary_ndft(p, x, X, batch, stream, &p.last_launches);
     }
-    return from_cuda(e);
+    return log_exec("ndft_exec", p, batch, from_cuda(e));
 }
 
 ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, cudaStream_t stream) {
@@ -214,7 +268,7 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
     p.last_variant = p.last_nsplit = 0;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
-    return from_cuda(launch_nfft(p, x, X, batch, stream, &p.last_launches));
+    return log_exec("nfft_exec", p, batch, from_cuda(launch_nfft(p, x, X, batch, stream, &p.last_launches)));
 }
 
 ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags, void *A,
@@ -235,7 +289,7 @@ ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, in
         e = launch_fft_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
     else
         e = launch_ternary_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
-    return from_cuda(e);
+    return log_exec("caf_exec", p, nlags, from_cuda(e));
 }
 
 ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0, int32_t nlags,
@@ -295,6 +349,7 @@ ndft_status ndft_query_error(ndft_plan_t plan, cudaStream_t stream) {
     if (v != 0 && (e = cudaMemset(plan->p.err, 0, sizeof(int32_t))) != cudaSuccess) return NDFT_E_CUDA;
     if (v == 0) return NDFT_OK;
     if (v == kDevTimeout) return NDFT_E_TIMEOUT;
+    if (v == kDevOverflow) return NDFT_E_OVERFLOW;
     return NDFT_E_CUDA;
 }
 
@@ -420,6 +475,8 @@ ndft_status ndft_plan_batched(ndft_plan_t *out, const ndft_cpi *cpis, int32_t nc
                               uint32_t flags, cudaStream_t stream) {
     const Range range("ndft_plan_batched");
     if (!out || !cpis || ncpi < 1 || ncpi > (1 << 20) || (flags & ~kKnownFlags)) return NDFT_E_INVALID;
+    if ((flags & NDFT_F_Q14_RANGE) && prec != NDFT_PREC_Q14) return NDFT_E_INVALID;
+    if (flags & NDFT_F_ABS_OUT) return NDFT_E_UNSUPPORTED;
     *out = nullptr;
     if (!valid_pair(form, prec) || fft_form(form)) return NDFT_E_UNSUPPORTED;
     for (int c = 0; c < ncpi; ++c) {

@@ -1665,15 +1665,21 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
 // 2 s + 1 = R, I; columns 2 col, 2 col + 1 = r, i), each of a, b, d, e summed
 // over the splits in order, then combined for the sign of the bin.  The split
 // loads are issued ahead of the (ordered) additions.  Deterministic.
+// With ABS the magnitude |X| (fp32, each operation rounded once) is written.
 constexpr int kFoldBins = 256;
+__device__ __forceinline__ float cabs_rn(float2 v) {
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)));
+}
+template <bool ABS>
 __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict__ part, int nsplit,
                                                          int64_t split_stride, int S, int N, int p0, int nbins,
                                                          const float2 *__restrict__ dc, int gy, int ncols,
-                                                         float2 *__restrict__ out) {
+                                                         void *__restrict__ out_v) {
     const int col = blockIdx.x;
     const int k = blockIdx.y * kFoldBins + threadIdx.x;
     const int64_t S2 = 2LL * S;
-    float2 *o = out + (int64_t)col * nbins;
+    float2 *o = static_cast<float2 *>(out_v) + (int64_t)col * nbins;
+    float *oa = static_cast<float *>(out_v) + (int64_t)col * nbins;
     int64_t p = ((int64_t)p0 + k) % N;
     if (p < 0) p += N;
     const int64_t c = p <= N - p ? p : N - p;
@@ -1706,8 +1712,10 @@ __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict
             db.x = __fadd_rn(db.x, v.x);
             db.y = __fadd_rn(db.y, v.y);
         }
-        o[k] = p == c ? make_float2(__fsub_rn(ae.x, db.y), __fadd_rn(db.x, ae.y))
-                      : make_float2(__fadd_rn(ae.x, db.y), __fsub_rn(db.x, ae.y));
+        const float2 X = p == c ? make_float2(__fsub_rn(ae.x, db.y), __fadd_rn(db.x, ae.y))
+                                : make_float2(__fadd_rn(ae.x, db.y), __fsub_rn(db.x, ae.y));
+        if constexpr (ABS) oa[k] = cabs_rn(X);
+        else o[k] = X;
     }
     // bin 0 (if in this block's bins): the DC tiles in a fixed order, warp 0
     int64_t k0 = (-(int64_t)p0) % N;
@@ -1724,7 +1732,10 @@ __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict
             sr = __fadd_rn(sr, __shfl_xor_sync(0xffffffffu, sr, off));
             si = __fadd_rn(si, __shfl_xor_sync(0xffffffffu, si, off));
         }
-        if (threadIdx.x == 0) o[k0] = make_float2(sr, si);
+        if (threadIdx.x == 0) {
+            if constexpr (ABS) oa[k0] = cabs_rn(make_float2(sr, si));
+            else o[k0] = make_float2(sr, si);
+        }
     }
 }
 
@@ -2040,7 +2051,8 @@ static cudaError_t gemm_cols(Plan &p, int nc, int64_t b_row0, void *out, cudaStr
     P.nth = nth_for(N);
     P.out_off = 0;
     float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + L.b_bytes);
-    float *out_base = P.nsplit == 1 ? static_cast<float *>(out) : part;
+    const bool abs_out = (p.d.flags & NDFT_F_ABS_OUT) != 0;  // |A| is formed by the split sum
+    float *out_base = (P.nsplit == 1 && !abs_out) ? static_cast<float *>(out) : part;
     const int64_t nunits = tiles * P.nsplit;
     // bulk tensor stores / adds for the epilogue when the rows are 16-byte multiples
     alignas(64) CUtensorMap omap;
@@ -2055,6 +2067,11 @@ static cudaError_t gemm_cols(Plan &p, int nc, int64_t b_row0, void *out, cudaStr
     *launches += 1;
     p.last_variant = 1;
     p.last_nsplit = P.nsplit;
+    if (abs_out) {
+        *launches += 1;
+        return launch_reduce_abs(reinterpret_cast<const float2 *>(part), P.nsplit, (int64_t)nc * nb,
+                                 static_cast<float *>(out), s);
+    }
     if (P.nsplit > 1) {
         *launches += 1;
         return launch_reduce_splits(part, P.nsplit, (int64_t)nc * 2 * nb, static_cast<float *>(out), s);
@@ -2066,7 +2083,7 @@ static cudaError_t gemm_cols(Plan &p, int nc, int64_t b_row0, void *out, cudaStr
 // tuning value (a multiple of TN), 1 for one part, or by default half the
 // columns rounded down to TN once there are at least 2 TN.
 static int first_part_cols(const Plan &p, int ncols) {
-    if (!p.side || p.tune_parts == 1) return 0;
+    if (!p.side || p.tune_parts == 1 || (p.d.flags & NDFT_F_ABS_OUT)) return 0;
     const int h0 = p.tune_parts > 1 ? p.tune_parts : std::max(TN, (ncols / 2) / TN * TN);
     return (ncols >= 2 * TN && h0 < ncols) ? h0 : 0;
 }
@@ -2126,8 +2143,13 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     *launches += 1;
     p.last_variant = 2;
     p.last_nsplit = P.nsplit;
-    k_pair_fold<<<dim3(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins), kFoldBins, 0, s>>>(
-        part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc, gy, ncols, static_cast<float2 *>(out));
+    const dim3 fgrid(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins);
+    if (p.d.flags & NDFT_F_ABS_OUT)
+        k_pair_fold<true><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
+                                                      gy, ncols, out);
+    else
+        k_pair_fold<false><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
+                                                       gy, ncols, out);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -88,6 +88,40 @@ def test_batched_ternary_uniform_bins(api):
         assert np.max(np.abs(g - want)) / np.max(np.abs(want)) < TOL
 
 
+def test_batched_q14_range_check(api):
+    """Batched Q1.14 with NDFT_F_Q14_RANGE: every CPI bit for bit against the
+    oracle as without the flag, no report on in-range data, and NDFT_E_OVERFLOW
+    once one CPI's inputs are at full scale."""
+    from paper_1402_0532_gb300 import _lib as L
+    scs = small_scenes()
+    surv, ref, cpis, total = pack(scs, q14=True)
+    bp = api.BatchedPlan(cpis, form="direct", prec="q14", flags=api.F_Q14_RANGE)
+    out = torch.zeros((total, 2), dtype=torch.int32, device="cuda")
+    bp(dev(surv), dev(ref), out)
+    bp.query_error()
+    got = out.cpu().numpy()
+    for sc, c in zip(scs, cpis):
+        qs, qr = scenes.quantize_q14(sc.s_surv, 0.25), scenes.quantize_q14(sc.s_ref, 0.25)
+        want, novf = oracle.caf_q14(qs, qr, sc.lag0, sc.nlags, sc.p0, sc.nbins)
+        assert novf == 0
+        g = got[c["off_out"]: c["off_out"] + sc.nlags * sc.nbins].reshape(sc.nlags, sc.nbins, 2)
+        assert np.array_equal(g, want)
+    # a full-scale CPI of 65536 samples: its bin-0 sums leave int32
+    n = 65536
+    big = [{"off_surv": 0, "off_ref": 0, "off_out": 0, "n": n, "lag0": 0, "nlags": 2, "p0": -1, "nbins": 3}]
+    fs = np.full((n, 2), 32767, np.int16)
+    fr = np.full((n, 2), -32768, np.int16)
+    want, novf = oracle.caf_q14(fs, fr, 0, 2, -1, 3)
+    assert novf > 0
+    bq = api.BatchedPlan(big, form="direct", prec="q14", flags=api.F_Q14_RANGE)
+    o2 = torch.zeros((6, 2), dtype=torch.int32, device="cuda")
+    bq(dev(fs), dev(fr), o2)
+    assert np.array_equal(o2.cpu().numpy().reshape(2, 3, 2), want)
+    with pytest.raises(L.NdftError) as ex:
+        bq.query_error()
+    assert ex.value.status == L.E_OVERFLOW
+
+
 @pytest.mark.parametrize("form,prec", [("direct", "fp32"), ("ternary", "bf16x2"), ("direct", "q14")])
 def test_batched_graph_replay_equals_eager(api, form, prec):
     q14 = prec == "q14"

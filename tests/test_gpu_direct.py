@@ -193,6 +193,11 @@ def test_caf_direct_q14_bit_exact(api):
 
 
 def test_caf_direct_q14_wraps(api):
+    """Full-scale inputs: the exact sums leave int32 (the oracle counts the
+    cells) and the output holds them modulo 2^32, bit for bit, with or without
+    the range check; with NDFT_F_Q14_RANGE ndft_query_error reports
+    NDFT_E_OVERFLOW, and the plan reports nothing on a call that stays in range."""
+    from paper_1402_0532_gb300 import _lib as L
     N = 16384
     ss = np.full((N, 2), 32767, np.int16)
     sr = np.full((N, 2), -32768, np.int16)
@@ -201,6 +206,45 @@ def test_caf_direct_q14_wraps(api):
     p = api.Plan(N, p0=-1, nbins=3, max_lags=3, prec="q14")
     got = p.caf(dev(ss), dev(sr), 0, 3).cpu().numpy()
     assert np.array_equal(got, want)
+    p.query_error()  # no report without the flag
+    r = api.Plan(N, p0=-1, nbins=3, max_lags=3, prec="q14", flags=api.F_Q14_RANGE)
+    got = r.caf(dev(ss), dev(sr), 0, 3).cpu().numpy()
+    assert np.array_equal(got, want)
+    with pytest.raises(L.NdftError) as ex:
+        r.query_error()
+    assert ex.value.status == L.E_OVERFLOW
+    # the report was cleared; a call whose sums stay in range reports nothing
+    small_s, small_r = ss[:200] // 64, sr[:200] // 64
+    q = api.Plan(200, p0=-1, nbins=3, max_lags=3, prec="q14", flags=api.F_Q14_RANGE)
+    w2, n2 = oracle.caf_q14(small_s, small_r, 0, 3, -1, 3)
+    assert n2 == 0
+    assert np.array_equal(q.caf(dev(small_s), dev(small_r), 0, 3).cpu().numpy(), w2)
+    q.query_error()
+
+
+@pytest.mark.parametrize("N,batch,p0,nbins", [(65536, 3, -2, 5), (4099, 70, 100, 129)])
+def test_ndft_q14_range_check(api, N, batch, p0, nbins):
+    """NDFT in Q1.14 with NDFT_F_Q14_RANGE: the same bits as without it, and
+    NDFT_E_OVERFLOW exactly when the oracle counts a wrapped cell."""
+    from paper_1402_0532_gb300 import _lib as L
+    rng = np.random.default_rng(N)
+    if N == 65536:
+        q = np.full((batch, N, 2), 32767, np.int16)  # full scale: bin 0 sums 65536 x 49151 > 2^31
+        q[1, ::2] = -32768
+    else:
+        q = scenes.quantize_q14(scenes.cn(rng, (batch, N)) * 0.5)
+    want, novf = oracle.ndft_q14(q, p0=p0, nbins=nbins)
+    for flags in (0, api.F_Q14_RANGE):
+        p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, prec="q14", flags=flags)
+        got = p.ndft(dev(q)).cpu().numpy()
+        assert np.array_equal(got, want)
+        if flags and novf > 0:
+            with pytest.raises(L.NdftError) as ex:
+                p.query_error()
+            assert ex.value.status == L.E_OVERFLOW
+        else:
+            p.query_error()
+    assert (novf > 0) == (N == 65536)
 
 
 # --------------------------------------------------------------------------------
