@@ -9,7 +9,11 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libndft.so")
+# NDFT_CHECKED=1 selects the index-checked build (libndft_checked.so), whose
+# kernels test their global indices and report a failed test through the plan's
+# error word
+_CHECKED = os.environ.get("NDFT_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(_PKG, "libndft_checked.so" if _CHECKED else "libndft.so")
 
 OK, E_INVALID, E_UNSUPPORTED, E_CUDA, E_NOMEM, E_TIMEOUT, E_OVERFLOW = range(7)
 FORM_DIRECT, FORM_TERNARY_GEMM, FORM_NFFT, FORM_FFT = 0, 1, 2, 3
@@ -54,7 +58,7 @@ def load() -> ctypes.CDLL:
         return _lib
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: run paper_1402_0532_gb300.build.build() "
-                          "(nvcc, sm_103a) before using the library; there is no CPU fallback")
+                          f"(checked={_CHECKED}; nvcc, sm_103a) before using the library; there is no CPU fallback")
     lib = ctypes.CDLL(LIB_PATH)
     P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
     sig = {

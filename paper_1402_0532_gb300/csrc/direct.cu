@@ -351,7 +351,7 @@ __device__ __forceinline__ void direct_tile(unsigned char *smem, const typename 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int b = bin0 + ty * 4 + i;
-            if (b < nbins) {
+            if (b < nbins && ndft_in(ldo >= nbins, err)) {
                 if constexpr (P::kIntFlush) out[(int64_t)col * ldo + b] = tot[i][j];
                 else out[(int64_t)col * ldo + b] = acc[i][j];
             }

@@ -140,6 +140,21 @@ __device__ __forceinline__ void dev_set_error(int32_t *err, int32_t code) {
     if (err) atomicCAS(err, 0, code);
 }
 
+// Index-checked build (compiled with -DNDFT_CHECKED into libndft_checked.so):
+// the packing, fold, epilogue and direct-tile kernels test each computed
+// global index against the extent their problem implies before the access; a
+// failed test records kDevBadIndex in the plan's error word (ndft_query_error
+// then returns NDFT_E_CUDA) and the access is skipped.  In the normal build the
+// test compiles away.
+#ifdef NDFT_CHECKED
+__device__ __forceinline__ bool ndft_in(bool ok, int32_t *err) {
+    if (!ok) dev_set_error(err, kDevBadIndex);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool ndft_in(bool, int32_t *) { return true; }
+#endif
+
 // Event pair around the main contraction kernel of an exec call (no-ops unless
 // ndft_timer_start armed the plan; recording an event allocates nothing).
 inline void timer_begin(const Plan &p, cudaStream_t s) {

@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                         tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf + h) * TN + cc), r);
                         tmem_wait_ld();
                         const int64_t col0 = (int64_t)w.nt * TN + cc;
-                        if (m < limit_m) {
+                        if (m < limit_m && ndft_in(w.P.ld >= limit_m, err)) {
                             float *dst = out_base + w.out_off + col0 * w.P.ld + m;
                             const int64_t left = w.P.ncols - col0;
                             const int nj = left < 32 ? (int)left : 32;
@@ -1434,7 +1434,7 @@ __device__ __forceinline__ float2 lag_product(const PackProb &P, const float2 *_
 // problem that row falls in (prefix[] holds each problem's first flat row).
 __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__restrict__ prefix, int nprob,
                        PackProb single, int64_t total_rows, uint32_t flags, bool caf, const float2 *__restrict__ a_base,
-                       const float2 *__restrict__ r_base, uint4 *__restrict__ B) {
+                       const float2 *__restrict__ r_base, uint4 *__restrict__ B, int32_t *err) {
     const int64_t total = total_rows * 8;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int t = (int)(e & 7);
@@ -1458,7 +1458,7 @@ __global__ void k_pack(const PackProb *__restrict__ probs, const int64_t *__rest
         float2 v = make_float2(0.f, 0.f);
         const float2 *a = a_base + P.a_off;
         if (i < P.N) v = caf ? lag_product(P, a, r_base + P.r_off, col, i, flags) : a[col * P.ldx + i];
-        B[(P.row0 + local) * 8 + t] = pack_entry(v);
+        if (ndft_in(local < (int64_t)P.kblocks * P.ncols, err)) B[(P.row0 + local) * 8 + t] = pack_entry(v);
     }
 }
 
@@ -1470,7 +1470,7 @@ constexpr int kPackKb = 8;
 __global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags, bool caf,
                                                      const float2 *__restrict__ a_base,
                                                      const float2 *__restrict__ r_base, uint4 *__restrict__ B,
-                                                     int gy) {
+                                                     int gy, int32_t *err) {
     const int t = threadIdx.x & 7;
     const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
     if (col >= P.ncols) return;
@@ -1484,7 +1484,7 @@ __global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags,
             const int64_t i = (int64_t)kb * 8 + t;
             float2 v = make_float2(0.f, 0.f);
             if (i < P.N) v = caf ? lag_product(P, a, r, col, i, flags) : a[(int64_t)col * P.ldx + i];
-            B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
+            if (ndft_in(kb < P.kblocks, err)) B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
         }
     }
 }
@@ -1497,7 +1497,8 @@ __global__ void __launch_bounds__(256) k_pack_single(PackProb P, uint32_t flags,
 __global__ void __launch_bounds__(256) k_pack_tiles(const PackProb *__restrict__ probs,
                                                     const int64_t *__restrict__ tile_prefix, int nprob,
                                                     uint32_t flags, const float2 *__restrict__ a_base,
-                                                    const float2 *__restrict__ r_base, uint4 *__restrict__ B) {
+                                                    const float2 *__restrict__ r_base, uint4 *__restrict__ B,
+                                                    int32_t *err) {
     const int64_t total = tile_prefix[nprob];
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * per;
@@ -1526,7 +1527,7 @@ __global__ void __launch_bounds__(256) k_pack_tiles(const PackProb *__restrict__
             const int64_t i = (int64_t)kb * 8 + t;
             float2 v = make_float2(0.f, 0.f);
             if (i < P.N) v = lag_product(P, a, r, col, i, flags);
-            B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
+            if (ndft_in(kb < P.kblocks, err)) B[(P.row0 + (int64_t)kb * P.ncols + col) * 8 + t] = pack_entry(v);
         }
     }
 }
@@ -1596,10 +1597,11 @@ __device__ __forceinline__ float2 lag_ox(float2 s, float2 r, bool conj) {
 __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, bool caf,
                                                    const float2 *__restrict__ a_base,
                                                    const float2 *__restrict__ r_base, uint4 *__restrict__ B,
-                                                   float2 *__restrict__ dc, int gy) {
+                                                   float2 *__restrict__ dc, int gy, int32_t *err) {
     const int t = threadIdx.x & 7;
     const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
     const bool live = col < P.ncols;  // whole 8-lane groups are live or not
+    const int64_t row_end = P.row0 + (int64_t)P.kblocks * 2 * P.ncols;  // this problem's packed rows
     const float2 *a = a_base + P.a_off + (caf ? 0 : (int64_t)col * P.ldx);
     const float2 *r = r_base + P.r_off;
     const int64_t ncols2 = 2LL * P.ncols;
@@ -1643,8 +1645,10 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
                 split2(v0.y, v1.y, hi, li);
                 const float g0r = sgnf(v0.x), g1r = sgnf(v1.x), g0i = sgnf(v0.y), g1i = sgnf(v1.y);
                 const uint32_t sr2 = bf2(g0r, g1r), si2 = bf2(g0i, g1i);
-                B[row * 8 + t] = make_uint4(hr, lr, sr2, sr2);
-                B[(row + 1) * 8 + t] = make_uint4(hi, li, si2, si2);
+                if (ndft_in(row >= P.row0 && row + 1 < row_end, err)) {
+                    B[row * 8 + t] = make_uint4(hr, lr, sr2, sr2);
+                    B[(row + 1) * 8 + t] = make_uint4(hi, li, si2, si2);
+                }
                 sr += (v0.x + g0r) + (v1.x + g1r);
                 si += (v0.y + g0i) + (v1.y + g1i);
             }
@@ -1654,7 +1658,7 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
             sr += __shfl_xor_sync(0xffffffffu, sr, o);
             si += __shfl_xor_sync(0xffffffffu, si, o);
         }
-        if (live && t == 0 && dc) dc[(int64_t)by * P.ncols + col] = make_float2(sr, si);
+        if (live && t == 0 && dc && ndft_in(by < gy, err)) dc[(int64_t)by * P.ncols + col] = make_float2(sr, si);
     }
 }
 
@@ -1674,7 +1678,7 @@ template <bool ABS>
 __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict__ part, int nsplit,
                                                          int64_t split_stride, int S, int N, int p0, int nbins,
                                                          const float2 *__restrict__ dc, int gy, int ncols,
-                                                         void *__restrict__ out_v) {
+                                                         void *__restrict__ out_v, int32_t *err) {
     const int col = blockIdx.x;
     const int k = blockIdx.y * kFoldBins + threadIdx.x;
     const int64_t S2 = 2LL * S;
@@ -1683,7 +1687,7 @@ __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict
     int64_t p = ((int64_t)p0 + k) % N;
     if (p < 0) p += N;
     const int64_t c = p <= N - p ? p : N - p;
-    if (k < nbins && c > 0) {
+    if (k < nbins && c > 0 && ndft_in(c <= S && col < ncols, err)) {
         const int64_t s = c - 1;
         const float2 *pr = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col) * S2 + 2 * s);      // (a, e)
         const float2 *pi = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col + 1) * S2 + 2 * s);  // (d, b)
@@ -1827,7 +1831,7 @@ int choose_split(int64_t tiles, int kblocks, int sm, int tune, int64_t cap_units
 // y extent shrinks and the blocks loop over the K-block tiles).
 cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob, const PackProb &single,
                         int64_t rows, uint32_t flags, bool caf, const void *a_base, const void *r_base, void *B, int sm,
-                        cudaStream_t s, int max_blocks = 0) {
+                        cudaStream_t s, int32_t *err, int max_blocks = 0) {
     const int threads = 256;
     if (!probs) {
         const int gx = (single.ncols + 31) / 32;
@@ -1836,14 +1840,14 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
         if (max_blocks > 0) grid_y = std::max(1, std::min(grid_y, max_blocks / gx));
         k_pack_single<<<dim3(gx, grid_y), threads, 0, s>>>(single, flags, caf, static_cast<const float2 *>(a_base),
                                                            static_cast<const float2 *>(r_base),
-                                                           static_cast<uint4 *>(B), gy);
+                                                           static_cast<uint4 *>(B), gy, err);
         return cudaGetLastError();
     }
     const int64_t want = (rows * 8 + threads - 1) / threads;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)sm * 32);
     k_pack<<<std::max(blocks, 1), threads, 0, s>>>(probs, prefix, nprob, single, rows, flags, caf,
                                                    static_cast<const float2 *>(a_base),
-                                                   static_cast<const float2 *>(r_base), static_cast<uint4 *>(B));
+                                                   static_cast<const float2 *>(r_base), static_cast<uint4 *>(B), err);
     return cudaGetLastError();
 }
 
@@ -2018,7 +2022,7 @@ static cudaError_t pack_cols(Plan &p, PackProb pp, bool caf, int c0, int nc, int
     pp.ncols = nc;
     pp.row0 = b_row0;
     return launch_pack(nullptr, nullptr, 0, pp, (int64_t)pp.kblocks * nc, p.d.flags, caf, a_base, r_base, p.ws,
-                       p.sm_count, s, max_blocks);
+                       p.sm_count, s, p.err, max_blocks);
 }
 
 // Contraction of nc packed columns (B rows from b_row0 on) into out
@@ -2112,7 +2116,7 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
         const int gx = (ncols + 31) / 32;
         k_pack_pair<<<dim3(gx, std::min(gy, 65535)), 256, 0, s>>>(
             pp, p.d.flags, caf, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base),
-            static_cast<uint4 *>(p.ws), dc, gy);
+            static_cast<uint4 *>(p.ws), dc, gy, p.err);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         *launches += 1;
@@ -2146,10 +2150,10 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     const dim3 fgrid(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins);
     if (p.d.flags & NDFT_F_ABS_OUT)
         k_pair_fold<true><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
-                                                      gy, ncols, out);
+                                                      gy, ncols, out, p.err);
     else
         k_pair_fold<false><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
-                                                       gy, ncols, out);
+                                                       gy, ncols, out, p.err);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -2441,7 +2445,7 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
     const int64_t *tprefix = reinterpret_cast<const int64_t *>(wd + BL.tprefix);
     const Unit *units = reinterpret_cast<const Unit *>(wd + BL.units);
     k_pack_tiles<<<p.sm_count * 8, 256, 0, s>>>(packs, tprefix, p.ncpi, p.d.flags, static_cast<const float2 *>(surv),
-                                                static_cast<const float2 *>(ref), static_cast<uint4 *>(p.ws));
+                                                static_cast<const float2 *>(ref), static_cast<uint4 *>(p.ws), p.err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *launches += 1;
