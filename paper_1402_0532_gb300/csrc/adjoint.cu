@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Both gradients from G ([nsplit][nc][N] complex, split partials summed here)
+// Both gradients from G ([nsplit][nc][N] complex, split partials summed here;
+// with PLANAR fp32 [nsplit][2 nc][N], Re and Im of lag a in rows 2 a, 2 a + 1)
 // for the nc lags lag_first .. lag_first + nc - 1.  A block owns 32
 // consecutive indices t (one per lane) and warp w takes the lags w, w + 8, ...;
 // the eight warp sums are added in warp order, so the result is deterministic.
@@ -153,7 +154,19 @@ __global__ void __launch_bounds__(256)
 // stores, 1 adds to the previous chunk's values (in chunk order).
 __device__ __forceinline__ float2 sigma2(float2 v) { return make_float2(sgnf(v.x), sgnf(v.y)); }
 
-template <bool SURV, bool REF>
+// G of lag a at sample i from split sp
+template <bool PLANAR>
+__device__ __forceinline__ float2 g_at(const float2 *__restrict__ G, int64_t split_stride, int N, int64_t a, int64_t i,
+                                       int sp) {
+    if constexpr (PLANAR) {
+        const float *Gf = reinterpret_cast<const float *>(G) + 2 * sp * split_stride + 2 * a * N;
+        return make_float2(Gf[i], Gf[N + i]);
+    } else {
+        return G[sp * split_stride + a * N + i];
+    }
+}
+
+template <bool SURV, bool REF, bool PLANAR>
 __global__ void __launch_bounds__(256)
     k_grad_fold(const float2 *__restrict__ G, int nsplit, int64_t split_stride, int N, int lag_first, int nc,
                 uint32_t flags, const float2 *__restrict__ s_surv, const float2 *__restrict__ s_ref,
@@ -167,7 +180,6 @@ __global__ void __launch_bounds__(256)
 #pragma unroll 4
         for (int a = w; a < nc; a += 8) {
             const int64_t l = (int64_t)lag_first + a;
-            const float2 *Ga = G + (int64_t)a * N;
             if (SURV) {
                 int64_t j = t - l;  // the s_ref sample that meets s_surv[t] at lag l
                 if (circ) {
@@ -175,9 +187,9 @@ __global__ void __launch_bounds__(256)
                     if (j < 0) j += N;
                 }
                 if (j >= 0 && j < N) {
-                    float2 g = Ga[t];
+                    float2 g = g_at<PLANAR>(G, split_stride, N, a, t, 0);
                     for (int sp = 1; sp < nsplit; ++sp) {
-                        const float2 h = Ga[sp * split_stride + t];
+                        const float2 h = g_at<PLANAR>(G, split_stride, N, a, t, sp);
                         g.x += h.x;
                         g.y += h.y;
                     }
@@ -194,9 +206,9 @@ __global__ void __launch_bounds__(256)
                     if (i < 0) i += N;
                 }
                 if (i >= 0 && i < N) {
-                    float2 g = Ga[i];
+                    float2 g = g_at<PLANAR>(G, split_stride, N, a, i, 0);
                     for (int sp = 1; sp < nsplit; ++sp) {
-                        const float2 h = Ga[sp * split_stride + i];
+                        const float2 h = g_at<PLANAR>(G, split_stride, N, a, i, sp);
                         g.x += h.x;
                         g.y += h.y;
                     }
@@ -252,9 +264,10 @@ cudaError_t launch_caf_backward_inputs(Plan &p, const void *s_surv, const void *
         const float2 *G = nullptr;
         int nsplit = 1;
         int64_t sstride = 0;
+        bool planar = false;
         if (tern) {
-            if ((e = launch_ternary_adjoint_g(p, nc, dA2 + (int64_t)a0 * nb, &G, &nsplit, &sstride, s, launches)) !=
-                cudaSuccess)
+            if ((e = launch_ternary_adjoint_g(p, nc, dA2 + (int64_t)a0 * nb, &G, &nsplit, &sstride, &planar, s,
+                                              launches)) != cudaSuccess)
                 return e;
         } else {
             dim3 grid((N + TI - 1) / TI, (nc + TL - 1) / TL);
@@ -272,12 +285,18 @@ cudaError_t launch_caf_backward_inputs(Plan &p, const void *s_surv, const void *
         auto *os = static_cast<float2 *>(ds_surv);
         auto *orf = static_cast<float2 *>(ds_ref);
         const int acc = a0 > 0;
-        if (ds_surv)
-            k_grad_fold<true, true><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss, sr,
-                                                           os, orf, acc);
+        if (ds_surv && planar)
+            k_grad_fold<true, true, true><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss,
+                                                                 sr, os, orf, acc);
+        else if (ds_surv)
+            k_grad_fold<true, true, false><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss,
+                                                                  sr, os, orf, acc);
+        else if (planar)
+            k_grad_fold<false, true, true><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss,
+                                                                  sr, os, orf, acc);
         else
-            k_grad_fold<false, true><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags, ss,
-                                                            sr, os, orf, acc);
+            k_grad_fold<false, true, false><<<blocks, 256, 0, s>>>(G, nsplit, sstride, N, lag0 + a0, nc, p.d.flags,
+                                                                   ss, sr, os, orf, acc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
     }

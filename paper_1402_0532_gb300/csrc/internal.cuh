@@ -230,7 +230,9 @@ cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, v
 cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nlags, const void *dA, void *ds,
                                    cudaStream_t s, int *launches);
 int ternary_adjoint_g_lags(const Plan &p, int nlags);
+// G for nc lags: interleaved complex [nsplit][nc][N], or with *planar fp32
+// [nsplit][2 nc][N] (Re of lag a in row 2 a, Im in 2 a + 1)
 cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const float2 **G, int *nsplit,
-                                     int64_t *split_stride, cudaStream_t s, int *launches);
+                                     int64_t *split_stride, bool *planar, cudaStream_t s, int *launches);
 
 }  // namespace ndft

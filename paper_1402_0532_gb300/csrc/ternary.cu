@@ -388,6 +388,11 @@ __device__ __forceinline__ void adj_signs(uint32_t u, uint32_t N, uint32_t &sr2,
 
 // Rows 2 pl (Re) and 2 pl + 1 (Im), 16-byte chunk t of the 128-byte row, in the
 // 128-byte-swizzled K-major layout the MMA descriptors expect.
+// One row's 16-byte chunk t, in the same swizzled layout.
+__device__ __forceinline__ void store_row(uint32_t a_stage, int row, int t, const uint4 &v) {
+    sts128(a_stage + (uint32_t)row * 128u + (((uint32_t)t ^ ((uint32_t)row & 7u)) << 4), v.x, v.y, v.z, v.w);
+}
+
 __device__ __forceinline__ void store_pair(uint32_t a_stage, int pl, int t, const uint4 &re, const uint4 &im) {
     const uint32_t row_re = 2u * pl, row_im = row_re + 1u;
     const uint32_t base_re = a_stage + row_re * 128u + (((uint32_t)t ^ (row_re & 7u)) << 4);
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
                    int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
     static_assert(ADJ == 0 || (MH == 2 && !BT), "the adjoint runs on the 256-row tile");
-    static_assert(!PAIR || (MH == 2 && !BT && ADJ == 0), "the conjugate-paired form runs on the 256-row tile");
+    static_assert(!PAIR || (MH == 2 && !BT), "the conjugate-paired form runs on the 256-row tile");
     constexpr int GW = gemm_gen_warps(PAIR);  // A-producer warps: warps 2 .. 2 + GW - 1
     constexpr int EPI0 = 2 + GW;              // epilogue warps EPI0 .. EPI0 + 3 -> TMEM lane quarters warp % 4
     using T = typename TileOf<PAIR, MH>::type;
@@ -610,7 +615,52 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        if constexpr (ADJ != 0) {
+        if constexpr (ADJ != 0 && PAIR) {
+            // Conjugate-paired adjoint: one row per sample i, K = frequencies
+            // c = p0, p0 + 1, ... (4 entries each, [S_r, S_r, S_i, S_i] of
+            // S = sigma(W^(c i)), against the packed [u_hi, u_lo, v_hi, v_lo]
+            // of the two columns of each lag); thread (pg, t) makes rows
+            // pg + 4 GW j, frequencies 2 t and 2 t + 1 of each K block (16
+            // frequencies), signs by the integer quadrant rule.
+            constexpr int RPT = 256 / (4 * GW);
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Work w = decode(u, single, probs, units);
+                const uint32_t N = (uint32_t)w.P.N;
+                uint32_t ua[RPT], ub[RPT], dd[RPT];
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int64_t i = ((int64_t)w.mt * 256 + pg + 4 * GW * j) % (int64_t)N;  // sample
+                    int64_t c0 = ((int64_t)w.P.p0 + (int64_t)w.kb0 * 16 + 2 * t) % (int64_t)N;
+                    if (c0 < 0) c0 += N;
+                    const int64_t c1 = c0 + 1 == N ? 0 : c0 + 1;
+                    ua[j] = 4u * (uint32_t)((c0 * i) % N);
+                    ub[j] = 4u * (uint32_t)((c1 * i) % N);
+                    dd[j] = 4u * (uint32_t)((16 * i) % N);
+                }
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
+                    const uint32_t a_st = a_base + stage * T::kABytes;
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) {
+                        uint32_t sra, sia, srb, sib;
+                        sign_bits(ua[j], N, sra, sia);
+                        sign_bits(ub[j], N, srb, sib);
+                        store_row(a_st, pg + 4 * GW * j, t, make_uint4(sra, sia, srb, sib));
+                        ua[j] += dd[j];
+                        if (ua[j] >= 4u * N) ua[j] -= 4u * N;
+                        ub[j] += dd[j];
+                        if (ub[j] >= 4u * N) ub[j] -= 4u * N;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[stage]);
+                    if (++stage == STG) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        } else if constexpr (ADJ != 0) {
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 const Work w = decode(u, single, probs, units);
                 const uint32_t N = (uint32_t)w.P.N;
@@ -760,6 +810,89 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                 }
             }
         }
+    } else if constexpr (ADJ == 1 && PAIR) {
+        // ---------------- paired adjoint epilogue ----------------
+        // Lane 32 quarter + lane of row half h holds sample i = i_lo + 128 h +
+        // 32 quarter + lane, and TMEM columns 2 c, 2 c + 1 of the half hold
+        // Re, Im of G_l[i] for the tile's lag c; each lane adds
+        // conj(sigma(c_l[i])) G_l[i] over the lags in order.  The weights depend
+        // on i - l only: per half each warp stages the 32 + 127 it needs.
+        const int quarter = warp & 3;
+        float2 *wts = reinterpret_cast<float2 *>(smem + T::kSmemStage + 8192 * quarter);
+        uint32_t chain = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const Work w = decode(u, single, probs, units);
+            const int N = w.P.N;
+            const int64_t i_lo = (int64_t)w.mt * 256;  // first sample of the tile
+            const int lag_lo = w.nt * (TN / 2);        // first lag of the tile
+            const int nl = w.P.ncols / 2;              // lags of the call
+            float2 acc[MH];
+#pragma unroll
+            for (int h = 0; h < MH; ++h) acc[h] = make_float2(0.f, 0.f);
+            for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
+                const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
+                if (!(ok = mbar_wait(&tmem_full[buf], tpar, s_abort, err))) break;
+                tc_fence_after();
+#pragma unroll
+                for (int h = 0; h < MH; ++h) {
+                    const int64_t i0w = i_lo + 128 * h + 32 * quarter;  // the warp's first sample
+                    // wts[k] = sigma(c) at i - l = i0w - (lag0 + lag_lo) - 127 + k
+                    const int64_t d0 = i0w - ((int64_t)w.P.lag0 + lag_lo) - (TN / 2 - 1);
+                    __syncwarp();
+                    for (int k = lane; k < 32 + TN / 2 - 1; k += 32) {
+                        int64_t jj = d0 + k;
+                        float2 wv = make_float2(0.f, 0.f);
+                        if (w.P.flags & NDFT_F_CIRCULAR_LAG) {
+                            jj %= N;
+                            if (jj < 0) jj += N;
+                        }
+                        if (jj >= 0 && jj < N) {
+                            const float2 r = w.P.sref[jj];
+                            const float cr = (r.x > 0.f) ? 1.f : (r.x < 0.f ? -1.f : 0.f);
+                            const float cq = (r.y > 0.f) ? 1.f : (r.y < 0.f ? -1.f : 0.f);
+                            wv = make_float2(cr, (w.P.flags & NDFT_F_NO_CONJ_REF) ? cq : -cq);  // sigma(c)
+                        }
+                        wts[k] = wv;
+                    }
+                    __syncwarp();
+#pragma unroll 1
+                    for (int g = 0; g < TN / 16; ++g) {
+                        uint32_t r[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf + h) * TN + g * 16), r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int cl = g * 8 + q;  // lag within the tile
+                            if (lag_lo + cl < nl) {
+                                const float gr = __uint_as_float(r[2 * q]), gi = __uint_as_float(r[2 * q + 1]);
+                                const float2 wv = wts[lane - cl + (TN / 2 - 1)];
+                                acc[h].x = fmaf(wv.x, gr, acc[h].x);
+                                acc[h].x = fmaf(wv.y, gi, acc[h].x);
+                                acc[h].y = fmaf(wv.x, gi, acc[h].y);
+                                acc[h].y = fmaf(-wv.y, gr, acc[h].y);
+                            }
+                        }
+                    }
+                    if (MH == 2 && h == 0) {  // half 0 read: its next chain may start
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tmem_half0);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+            }
+            if (!ok) break;
+            // partial slice (n-tile, split) of the [slices][2N] partials
+            float2 *slice = reinterpret_cast<float2 *>(out_base) + (int64_t)(w.nt * w.P.nsplit + w.split) * N;
+#pragma unroll
+            for (int h = 0; h < MH; ++h) {
+                const int64_t i = i_lo + 128 * h + 32 * quarter + lane;
+                if (i < N) slice[i] = acc[h];
+            }
+        }
     } else if constexpr (ADJ == 1) {
         // ---------------- adjoint epilogue ----------------
         // Row r = 2 i + c of the tile holds component c of G_l[i] for the tile's
@@ -855,7 +988,8 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
         bool ok = true;
         for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             const Work w = decode(u, single, probs, units);
-            const int64_t limit_m = ADJ == 2 ? 2LL * w.P.N : 2LL * w.P.nbins;  // output rows
+            // output rows: G of the adjoint (two per sample, or one per sample paired), or bins
+            const int64_t limit_m = ADJ == 2 ? (PAIR ? (int64_t)w.P.N : 2LL * w.P.N) : 2LL * w.P.nbins;
             for (int c0 = w.kb0; c0 < w.kb1; c0 += chunk, ++chain) {
                 const uint32_t buf = chain % NB, tpar = (chain / NB) & 1u;
                 if (!(ok = mbar_wait(&tmem_full[buf], tpar, s_abort, err))) break;
@@ -1743,6 +1877,44 @@ __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict
     }
 }
 
+// Paired adjoint B operand: with W^(-c i) = conj(W^(c i)) the bins +c and -c
+// of dA enter G_l[i] = sum_p conj(S[p][i]) dA[l][p] as
+//     conj(S) x + S y = S_r u_r + S_i v_i + j (S_r u_i - S_i v_r),
+// x = dA[l][+c], y = dA[l][-c] (0 where the bin is not in the window, y = 0
+// when -c = +c), u = x + y, v = x - y.  Row (kb, 2 l) holds frequencies
+// 16 kb .. 16 kb + 15 as [u_r hi, lo, v_i hi, lo] and row (kb, 2 l + 1) as
+// [u_i hi, lo, -v_r hi, lo] (bf16), against the A rows' [S_r, S_r, S_i, S_i].
+// One thread per (lag, frequency), coalesced over the frequencies.
+__global__ void __launch_bounds__(256) k_pack_adjoint_pair(const float2 *__restrict__ dA, int N, int p0, int nbins,
+                                                            int nlags, int slots, int kblocks, uint2 *__restrict__ B) {
+    const int64_t total = (int64_t)nlags * kblocks * 16;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = e / ((int64_t)kblocks * 16);
+        const int c = (int)(e - l * kblocks * 16);  // frequency
+        float2 x = make_float2(0.f, 0.f), y = x;
+        if (c < slots) {
+            int64_t kx = ((int64_t)c - p0) % N;
+            if (kx < 0) kx += N;
+            int64_t ky = (-(int64_t)c - p0) % N;
+            if (ky < 0) ky += N;
+            const bool self_conj = (2LL * c) % N == 0;  // -c = +c (mod N)
+            if (kx < nbins) x = dA[l * nbins + kx];
+            if (!self_conj && ky < nbins) y = dA[l * nbins + ky];
+        }
+        const float ur = x.x + y.x, ui = x.y + y.y, vr = x.x - y.x, vi = x.y - y.y;
+        uint32_t h0, l0, h1, l1;
+        split2(ur, vi, h0, l0);   // [u_r hi, v_i hi], [u_r lo, v_i lo]
+        split2(ui, -vr, h1, l1);  // [u_i hi, -v_r hi], [u_i lo, -v_r lo]
+        const int kb = c >> 4, k = c & 15;
+        // K order per frequency: [hi(u), lo(u), hi(v), lo(v)]
+        B[((int64_t)kb * 2 * nlags + 2 * l) * 16 + k] =
+            make_uint2(__byte_perm(h0, l0, 0x5410), __byte_perm(h0, l0, 0x7632));
+        B[((int64_t)kb * 2 * nlags + 2 * l + 1) * 16 + k] =
+            make_uint2(__byte_perm(h1, l1, 0x5410), __byte_perm(h1, l1, 0x7632));
+    }
+}
+
 // Two-level angle table: entry j < nth is (cos, sin)((pi/2) 256 j / N), entry
 // nth + j (j < 256) is (cos, sin)((pi/2) j / N); fp64, rounded to fp32.
 __global__ void k_angles(int N, int nth, float2 *__restrict__ ang) {
@@ -1789,6 +1961,22 @@ cudaError_t make_out_map(void *base, int nbins, int ncols, int nsplit, CUtensorM
     cuuint64_t dims[3] = {rows, (cuuint64_t)ncols, (cuuint64_t)nsplit};
     cuuint64_t strides[2] = {rows * 4, rows * 4 * (cuuint64_t)ncols};
     cuuint32_t box[3] = {32, (cuuint32_t)box_cols, 1};  // one epilogue warp's 32 rows x 16 (paired: 32) columns
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// The same for an output of `rows` fp32 rows per column (the paired adjoint's
+// G: one row per sample), box 32 rows x 32 columns.  Needs rows * 4 bytes to
+// be a multiple of 16.
+cudaError_t make_out_rows_map(void *base, int64_t rows, int ncols, int nsplit, CUtensorMap *map) {
+    auto enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    cuuint64_t dims[3] = {(cuuint64_t)rows, (cuuint64_t)ncols, (cuuint64_t)nsplit};
+    cuuint64_t strides[2] = {(cuuint64_t)rows * 4, (cuuint64_t)rows * 4 * (cuuint64_t)ncols};
+    cuuint32_t box[3] = {32, 32, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -2230,9 +2418,63 @@ cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, i
 // G_l[i] in the epilogue.  Partials per (lag tile, split) are summed in order.
 // Returns cudaErrorNotSupported when the plan's workspace cannot hold it (the
 // caller then uses the CUDA-core kernel).
+// The paired adjoint contraction: rows = samples, columns = (lag, Re / Im),
+// K = frequencies 0 .. S (4 entries each).  Used when the window pairs and
+// it issues fewer K-block steps than one row pair per sample over the bins.
+static bool use_pair_adjoint(const Plan &p, int ncols) {
+    if (p.tune_pair == 1 || p.pair_slots < 1) return false;
+    const int64_t N = p.d.n, nb = p.d.nbins, S1 = p.pair_slots + 1;
+    if (p.tune_pair == 2) return true;
+    const int64_t paired = ((N + 255) / 256) * ((2LL * ncols + TN - 1) / TN) * ((S1 + 15) / 16);
+    const int64_t plain = ((2 * N + 255) / 256) * (((int64_t)ncols + TN - 1) / TN) * ((nb + 15) / 16);
+    return paired < plain;
+}
+
+// Packs the paired adjoint operand of nc lags of dA into the workspace.
+static cudaError_t pack_adjoint_pair(Plan &p, const void *dA, int nc, int kblocks, cudaStream_t s) {
+    const int64_t total = (int64_t)nc * kblocks * 16;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p.sm_count * 16);
+    k_pack_adjoint_pair<<<blocks, 256, 0, s>>>(static_cast<const float2 *>(dA), p.d.n, p.d.p0, p.d.nbins, nc,
+                                               p.pair_slots + 1, kblocks, static_cast<uint2 *>(p.ws));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nlags, const void *dA, void *ds,
                                    cudaStream_t s, int *launches) {
     const int N = p.d.n, nb = p.d.nbins;
+    if (use_pair_adjoint(p, nlags)) {
+        const int kblocks = (p.pair_slots + 1 + 15) / 16;
+        Problem P{};
+        P.N = N;
+        P.p0 = 0;  // frequencies 0, 1, ..
+        P.nbins = p.pair_slots + 1;
+        P.ncols = 2 * nlags;
+        P.kblocks = kblocks;
+        P.mtiles = (N + 255) / 256;
+        P.ntiles = (P.ncols + TN - 1) / TN;
+        const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+        P.nsplit = tiles >= p.sm_count
+                       ? 1
+                       : (int)std::max<int64_t>(1, std::min<int64_t>(kblocks / 16, (2LL * p.sm_count + tiles - 1) / tiles));
+        const int64_t slices = (int64_t)P.ntiles * P.nsplit;
+        if ((size_t)kblocks * P.ncols * 128 <= p.b_bytes && (size_t)slices * 2 * N * sizeof(float) <= p.part_bytes) {
+            P.b_row0 = 0;
+            P.sref = static_cast<const float2 *>(s_ref);
+            P.lag0 = lag0;
+            P.flags = p.d.flags;
+            cudaError_t e = pack_adjoint_pair(p, dA, nlags, kblocks, s);
+            if (e != cudaSuccess) return e;
+            *launches += 1;
+            float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + p.b_bytes);
+            if ((e = launch_gemm<2, false, 1, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
+                cudaSuccess)
+                return e;
+            *launches += 2;
+            p.last_variant = 2;
+            p.last_nsplit = P.nsplit;
+            return launch_reduce_splits(part, (int)slices, 2LL * N, static_cast<float *>(ds), s);
+        }
+    }
     const int kblocks = (nb + 15) / 16;
     const size_t b_need = (size_t)kblocks * nlags * 128;
     Problem P{};
@@ -2271,6 +2513,8 @@ cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nla
         cudaSuccess)
         return e;
     *launches += 2;
+    p.last_variant = 1;
+    p.last_nsplit = P.nsplit;
     return launch_reduce_splits(part, (int)slices, 2LL * N, static_cast<float *>(ds), s);
 }
 
@@ -2297,8 +2541,53 @@ int ternary_adjoint_g_lags(const Plan &p, int nlags) {
 }
 
 cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const float2 **G, int *nsplit,
-                                     int64_t *split_stride, cudaStream_t s, int *launches) {
+                                     int64_t *split_stride, bool *planar, cudaStream_t s, int *launches) {
     const int N = p.d.n, nb = p.d.nbins;
+    *planar = false;
+    if (use_pair_adjoint(p, nc)) {
+        // G as fp32 [split][2 nc][N]: Re of lag l in column 2 l, Im in 2 l + 1
+        const int kblocks = (p.pair_slots + 1 + 15) / 16;
+        const size_t g_off = (((size_t)kblocks * 2 * nc * 128) + 1023) & ~(size_t)1023;
+        Problem P{};
+        P.N = N;
+        P.p0 = 0;
+        P.nbins = p.pair_slots + 1;
+        P.ncols = 2 * nc;
+        P.kblocks = kblocks;
+        P.mtiles = (N + 255) / 256;
+        P.ntiles = (P.ncols + TN - 1) / TN;
+        const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+        int ns = tiles >= p.sm_count
+                     ? 1
+                     : (int)std::max<int64_t>(1, std::min<int64_t>(kblocks / 16, (2LL * p.sm_count + tiles - 1) / tiles));
+        ns = std::min(ns, kMaxSplit);
+        while (ns > 1 && g_off + (size_t)ns * nc * N * sizeof(float2) > p.ws_alloc) --ns;
+        if (g_off + (size_t)ns * nc * N * sizeof(float2) <= p.ws_alloc) {
+            P.nsplit = ns;
+            P.b_row0 = 0;
+            P.ld = N;
+            P.split_stride = (int64_t)2 * nc * N;
+            P.out_off = 0;
+            cudaError_t e = pack_adjoint_pair(p, dA, nc, kblocks, s);
+            if (e != cudaSuccess) return e;
+            *launches += 1;
+            float *g = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + g_off);
+            alignas(64) CUtensorMap omap;
+            const bool tma_out = (N % 4 == 0) && p.tune_drain == 0 &&
+                                 make_out_rows_map(g, N, P.ncols, ns, &omap) == cudaSuccess;
+            if ((e = launch_gemm<2, false, 2, true>(p, P, nullptr, nullptr, tiles * ns, g, tma_out ? &omap : nullptr,
+                                                    s)) != cudaSuccess)
+                return e;
+            *launches += 1;
+            p.last_variant = 2;
+            p.last_nsplit = ns;
+            *G = reinterpret_cast<const float2 *>(g);
+            *nsplit = ns;
+            *split_stride = (int64_t)nc * N;  // complex elements (2 nc N floats)
+            *planar = true;
+            return cudaSuccess;
+        }
+    }
     const int kblocks = (nb + 15) / 16;
     if (nc < 1 || adjoint_g_need(N, nb, nc, 1) > p.ws_alloc) return cudaErrorNotSupported;
     Problem P{};
@@ -2335,6 +2624,8 @@ cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const floa
         cudaSuccess)
         return e;
     *launches += 1;
+    p.last_variant = 1;
+    p.last_nsplit = ns;
     *G = reinterpret_cast<const float2 *>(g);
     *nsplit = ns;
     *split_stride = (int64_t)nc * N;  // complex elements

@@ -151,3 +151,54 @@ def test_paired_deterministic_and_graph(api):
     torch.cuda.synchronize()
     want = p.caf(ss, sr, 0, 256).cpu().numpy()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
+    (4133, -3, 100, -48, 96, 0),      # centred window, ragged sample tile
+    (700, 650, 40, -16, 33, 1),       # odd window, no conjugation
+    (700, 650, 40, -16, 33, 2),       # circular lags
+    (1024, 0, 300, 0, 1024, 0),       # every bin of N (N/2 self-conjugate), lags over two column tiles
+    (999, 2, 37, 100, 60, 0),         # asymmetric window: most frequencies have one bin only
+])
+def test_paired_adjoint(api, N, lag0, nlags, p0, nbins, flags):
+    """The adjoint contraction with conjugate pairing: W^(-c i) = conj(W^(c i))
+    makes bins +c and -c of dA enter G as S_r u + ... with u, v = dA[+c] +- dA[-c]
+    (one row per sample, half the multiply-adds); dL/ds_surv (the fused fold) and
+    both gradients (G stored, then folded) against the fp64 oracle adjoints,
+    forced on (key 6 = 2) and off (key 6 = 1)."""
+    sc = scenes.radar_scene(N=N, nlags=min(nlags, 64), nbins=min(nbins, 64), seed=66 + N % 11)
+    rng = np.random.default_rng(67)
+    dA = scenes.cn(rng, (nlags, nbins))
+    want_s = oracle.caf_adjoint(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, dA, flags=flags)
+    want_r = oracle.caf_adjoint_ref(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, dA, flags=flags)
+    for key in (2, 1):
+        p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="ternary", prec="bf16x2")
+        p.set_tuning(6, key)
+        ss, sr, d = dev(sc.s_surv), dev(sc.s_ref), dev(dA.astype(np.complex64))
+        g = p.caf_backward(ss, sr, lag0, nlags, d).cpu().numpy()
+        p.query_error()
+        assert p.query(1) == (2 if key == 2 else 1)
+        assert relerr(g, want_s) < TOL, key
+        gs, gr = p.caf_backward_inputs(ss, sr, lag0, nlags, d)
+        p.query_error()
+        assert p.query(1) == (2 if key == 2 else 1)
+        assert relerr(gs.cpu().numpy(), want_s) < TOL, key
+        assert relerr(gr.cpu().numpy(), want_r) < TOL, key
+
+
+def test_paired_adjoint_headline_sampled(api):
+    """Both gradients of the 65536-sample, 1024 x 1024 surface through the paired
+    adjoint (the default there) at sampled indices against the oracle."""
+    sc = scenes.radar_scene(N=65536)
+    rng = np.random.default_rng(68)
+    dA = (scenes.cn(rng, (1024, 1024)) * (rng.random((1024, 1024)) < 0.01)).astype(np.complex64)
+    p = api.Plan(sc.N, p0=-512, nbins=1024, max_lags=1024, form="ternary", prec="bf16x2")
+    gs, gr = p.caf_backward_inputs(dev(sc.s_surv), dev(sc.s_ref), 0, 1024, dev(dA))
+    p.query_error()
+    assert p.query(1) == 2
+    idx = np.concatenate([[0, 1, 37, 65535, 1023, 1024], rng.integers(0, 65536, 26)])
+    ws = oracle.caf_adjoint_at(sc.s_surv, sc.s_ref, 0, 1024, -512, 1024, dA, "surv", idx)
+    wr = oracle.caf_adjoint_at(sc.s_surv, sc.s_ref, 0, 1024, -512, 1024, dA, "ref", idx)
+    gs, gr = gs.cpu().numpy(), gr.cpu().numpy()
+    assert np.max(np.abs(gs[idx] - ws)) / np.max(np.abs(gs)) < TOL
+    assert np.max(np.abs(gr[idx] - wr)) / np.max(np.abs(gr)) < TOL
