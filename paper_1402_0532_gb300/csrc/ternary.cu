@@ -2109,19 +2109,6 @@ struct TernLayout {
 int pair_kblocks(int N) { return (N + 15) / 16; }
 int pair_pack_tiles(int N) { return (pair_kblocks(N) + kPairPackKb - 1) / kPairPackKb; }
 
-TernLayout layout_for(const ndft_desc &d, int sm) {
-    TernLayout L;
-    L.kblocks = (d.n + 7) / 8;
-    const int cols = max_cols(d);
-    // the unpaired layout (8 samples x 8 entries per row, one row per column)
-    // or the paired one (16 samples x 4 entries, two rows per column)
-    L.b_rows = std::max<int64_t>((int64_t)L.kblocks * cols, (int64_t)pair_kblocks(d.n) * 2 * cols);
-    L.b_bytes = (size_t)L.b_rows * 128;
-    L.part_bytes = (size_t)4 * sm * 256 * TN * sizeof(float);  // 4 waves of 256 x 256 partial tiles
-    L.dc_bytes = ((size_t)pair_pack_tiles(d.n) * cols * sizeof(float2) + 255) / 256 * 256;
-    return L;
-}
-
 // Frequencies 1 .. S that the bin window p0 .. p0 + nbins - 1 (mod N) folds
 // onto, c(p) = min(p, N - p); S = max c over the window.
 int pair_slots_for(int N, int p0, int nbins) {
@@ -2133,6 +2120,25 @@ int pair_slots_for(int N, int p0, int nbins) {
     }
     return (int)cmax;
 }
+
+TernLayout layout_for(const ndft_desc &d, int sm) {
+    TernLayout L;
+    L.kblocks = (d.n + 7) / 8;
+    const int cols = max_cols(d);
+    // the unpaired layout (8 samples x 8 entries per row, one row per column)
+    // or the paired one (16 samples x 4 entries, two rows per column)
+    L.b_rows = std::max<int64_t>((int64_t)L.kblocks * cols, (int64_t)pair_kblocks(d.n) * 2 * cols);
+    L.b_bytes = (size_t)L.b_rows * 128;
+    L.part_bytes = (size_t)4 * sm * 256 * TN * sizeof(float);  // 4 waves of 256 x 256 partial tiles
+    L.dc_bytes = ((size_t)pair_pack_tiles(d.n) * cols * sizeof(float2) + 255) / 256 * 256;
+    // the paired contraction writes at least one split of partials [2 cols][2 S]
+    // (the fold writes the output): room for it at the plan's largest call
+    const int S = pair_slots_for(d.n, d.p0, d.nbins ? d.nbins : d.n);
+    if (S > 0) L.part_bytes = std::max(L.part_bytes, (size_t)2 * cols * 2 * S * sizeof(float));
+    return L;
+}
+
+
 
 // Device-side description of a batched plan (one allocation, laid out by
 // ternary_batched_init): Problem[ncpi], PackProb[ncpi], int64 prefix[ncpi + 1]
