@@ -71,6 +71,11 @@ struct Plan {
     int tune_parts = 1;          // ternary form: 1 one part (default); 0 two parts, half each; else part 0's columns
     int tune_pair = 0;           // ternary form: 0 conjugate-paired rows where they save work (default), 1 never
     int pair_slots = 0;          // ternary form: frequencies 1 .. pair_slots cover the bin window (0: none)
+    int tune_atab = 0;           // ternary form: 0 paired A tiles from the plan's table when built, 1 generated on chip
+    void *atab = nullptr;        // ternary form: the paired contraction's A operand, [K block][rows] x 128 B
+    size_t atab_bytes = 0;
+    int32_t atab_ld = 0;         // its rows per K block
+    void *tmap_a = nullptr;      // its TMA descriptor (host copy)
     size_t dc_bytes = 0;         // ternary form: per-tile DC sums of the paired packing
     // ternary form: side stream and events of the two-part contraction (the
     // second part's packing runs under the first part's contraction)

@@ -105,6 +105,8 @@ void free_plan(Plan &p) {
     cudaFree(p.nfft_ws);
     cudaFree(p.comb);
     cudaFree(p.ws);
+    cudaFree(p.atab);
+    std::free(p.tmap_a);
     cudaFree(p.err);
     cudaFree(p.cpis_dev);
     cudaFree(p.tab_arena);
@@ -463,6 +465,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
     } else if (key == 6) {
         if (value > 2) return NDFT_E_INVALID;
         plan->p.tune_pair = value;
+    } else if (key == 7) {
+        if (value > 1) return NDFT_E_INVALID;
+        plan->p.tune_atab = value;
     } else {
         return NDFT_E_INVALID;
     }

@@ -56,8 +56,13 @@ constexpr int kThreads = (2 + kGenWarps + 4) * 32;
 // unpaired one and runs twice the A-producer warps (4 per SM sub-partition) to
 // hide their latency
 constexpr int kGenWarpsPair = 16;
-__host__ __device__ constexpr int gemm_gen_warps(bool pair) { return pair ? kGenWarpsPair : kGenWarps; }
-__host__ __device__ constexpr int gemm_threads(bool pair) { return (2 + gemm_gen_warps(pair) + 4) * 32; }
+// A tiles loaded from a plan-time table (ATAB) need no producer warps
+__host__ __device__ constexpr int gemm_gen_warps(bool pair, bool atab = false) {
+    return atab ? 0 : (pair ? kGenWarpsPair : kGenWarps);
+}
+__host__ __device__ constexpr int gemm_threads(bool pair, bool atab = false) {
+    return (2 + gemm_gen_warps(pair, atab) + 4) * 32;
+}
 constexpr int kMaxSplit = 32;
 constexpr int kChunk = 64;  // K blocks per TMEM accumulation chain (512 samples)
 // paired form: 64 K blocks of 16 samples (1024 samples, the same 256 MMA K
@@ -67,6 +72,9 @@ constexpr int kChunk = 64;  // K blocks per TMEM accumulation chain (512 samples
 // 64 / 128 / 256 paired blocks give 2.5e-6 / 4.0e-6 / 8.2e-6 / 1.6e-5 of max|X|
 // (the unpaired form 2.6e-6 / 4.9e-6 / 8.4e-6 / 1.7e-5 at the same K steps)
 constexpr int kChunkPair = 64;
+// largest plan-time A table of the paired contraction (512 MiB for a
+// 65536-sample surface of 1024 bins)
+constexpr size_t kAtabMaxBytes = (size_t)2 << 30;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 
@@ -80,6 +88,7 @@ struct Problem {
     int64_t split_stride;  // floats between split partials
     const float2 *ang;     // two-level table: [nth] (r_hi) then [256] (r_lo)
     int32_t nth;
+    int32_t a_ld;          // paired A table: rows per K block (the padded row count)
     int32_t crow0;         // batched: first column of this problem in the output tensor map
     // adjoint mode: s_ref and the lag window of the forward call
     const float2 *sref;
@@ -449,14 +458,18 @@ struct TileOf<true, MH> {
 // ADJ selects the adjoint contractions (rows = samples, columns = lags, K =
 // bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
 // forward epilogue on a [lags][2N] fp32 output).
-template <int MH, bool BT, int ADJ, bool PAIR = false>
-__global__ void __launch_bounds__(gemm_threads(PAIR), 1)
+// ATAB (paired forward only): the A tiles come by TMA from a table the plan
+// built (rows [K block][padded rows] of 128 bytes) instead of producer warps.
+template <int MH, bool BT, int ADJ, bool PAIR = false, bool ATAB = false>
+__global__ void __launch_bounds__(gemm_threads(PAIR, ATAB), 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
                    Problem single, const Problem *__restrict__ probs, const Unit *__restrict__ units, int64_t nunits,
-                   int chunk, int starve, float *__restrict__ out_base, int32_t *err) {
+                   int chunk, int starve, float *__restrict__ out_base, int32_t *err,
+                   const __grid_constant__ CUtensorMap amap) {
     static_assert(ADJ == 0 || (MH == 2 && !BT), "the adjoint runs on the 256-row tile");
     static_assert(!PAIR || (MH == 2 && !BT), "the conjugate-paired form runs on the 256-row tile");
-    constexpr int GW = gemm_gen_warps(PAIR);  // A-producer warps: warps 2 .. 2 + GW - 1
+    static_assert(!ATAB || (PAIR && ADJ == 0), "the A table is for the paired forward contraction");
+    constexpr int GW = gemm_gen_warps(PAIR, ATAB);  // A-producer warps: warps 2 .. 2 + GW - 1
     constexpr int EPI0 = 2 + GW;              // epilogue warps EPI0 .. EPI0 + 3 -> TMEM lane quarters warp % 4
     using T = typename TileOf<PAIR, MH>::type;
     constexpr int STG = T::kStages;
@@ -493,6 +506,7 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+        if constexpr (ATAB) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&amap)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -516,9 +530,13 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     if (starve) continue;  // tests: the stage never fills, every wait runs out
-                    mbar_arrive_tx(&full[stage], B_BYTES);
+                    mbar_arrive_tx(&full[stage], B_BYTES + (ATAB ? (uint32_t)T::kABytes : 0u));
                     const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN;
                     tma_load_b(b_base + stage * B_BYTES, &tmap, (int32_t)row, &full[stage]);
+                    if constexpr (ATAB) {
+                        const int64_t arow = (int64_t)kb * w.P.a_ld + (int64_t)w.mt * T::kRows;
+                        tma_load_b(a_base + stage * T::kABytes, &amap, (int32_t)arow, &full[stage]);
+                    }
                     if (++stage == STG) {
                         stage = 0;
                         phase ^= 1u;
@@ -700,6 +718,8 @@ __global__ void __launch_bounds__(gemm_threads(PAIR), 1)
                     }
                 }
             }
+        } else if constexpr (ATAB) {
+            // no producer warps: the TMA warp loads the A tiles from the table
         } else if constexpr (PAIR) {
             // Conjugate-paired rows: slot k of the unit is the frequency
             // c = p0 + k (p0 = the first paired frequency); its R row (2 k) and
@@ -1925,6 +1945,34 @@ __global__ void k_angles(int N, int nth, float2 *__restrict__ ang) {
     ang[e] = (r == 0) ? make_float2(1.f, 0.f) : make_float2(__double2float_rn(cos(a)), __double2float_rn(sin(a)));
 }
 
+// The paired contraction's A operand for a whole plan: row (kb, m) holds the
+// 64 K entries of row m (slot s = m / 2, frequency c = p0 + s; m even the R
+// row, odd the I row) for samples 16 kb .. 16 kb + 15, in the chunk order of
+// gen_conj_chunk, with each twiddle from the two-level table (no rotation)
+// and its signs from the exact twiddle index.  Rows past 2 S are zero.
+__global__ void k_atab(int N, int p0, int S, int rows, int kblocks, const float2 *__restrict__ ang, int nth,
+                       uint4 *__restrict__ out) {
+    const int64_t total = (int64_t)kblocks * (rows / 2) * 8;  // (kb, slot, chunk)
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e & 7);
+        const int64_t r = e >> 3;
+        const int sl = (int)(r % (rows / 2));
+        const int64_t kb = r / (rows / 2);
+        uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
+        if (sl < S) {
+            int64_t c = ((int64_t)p0 + sl) % N;
+            if (c < 0) c += N;
+            const int64_t i0 = (kb * 16 + 2 * t) % N, i1 = (i0 + 1) % N;
+            const uint32_t ua = 4u * (uint32_t)((c * i0) % N), ub = 4u * (uint32_t)((c * i1) % N);
+            const float2 wa = tw_table_g(ua, (uint32_t)N, ang, nth), wb = tw_table_g(ub, (uint32_t)N, ang, nth);
+            gen_conj_chunk((float)ua, (float)ub, wa, wb, (float)N, re, im);
+        }
+        out[(kb * rows + 2 * sl) * 8 + t] = re;
+        out[(kb * rows + 2 * sl + 1) * 8 + t] = im;
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -2039,11 +2087,11 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
     return cudaGetLastError();
 }
 
-template <int MH, bool BT = false, int ADJ = 0, bool PAIR = false>
+template <int MH, bool BT = false, int ADJ = 0, bool PAIR = false, bool ATAB = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
     constexpr size_t smem = TileOf<PAIR, MH>::type::kSmemTotal;
-    auto kern = k_ternary_gemm<MH, BT, ADJ, PAIR>;
+    auto kern = k_ternary_gemm<MH, BT, ADJ, PAIR, ATAB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
@@ -2054,8 +2102,9 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
     const int out_tma = omap ? 1 : 0;
     timer_begin(p, s);
     const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
-    kern<<<grid, gemm_threads(PAIR), smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk, p.test_starve,
-                                      out_base, p.err);
+    const CUtensorMap &am = (ATAB && p.tmap_a) ? *static_cast<const CUtensorMap *>(p.tmap_a) : none;
+    kern<<<grid, gemm_threads(PAIR, ATAB), smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk,
+                                                      p.test_starve, out_base, p.err, am);
     e = cudaGetLastError();
     timer_end(p, s);
     return e;
@@ -2186,6 +2235,27 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
     p.part_bytes = L.part_bytes;
     p.dc_bytes = L.dc_bytes;
     p.pair_slots = pair_slots_for(N, p.d.p0, p.d.nbins);
+    // the paired A operand as a table when it is modest (it depends on the
+    // window and N only; the contraction then needs no producer warps)
+    if (p.pair_slots > 0) {
+        const int rows = (2 * p.pair_slots + 255) / 256 * 256;
+        const int kbp = pair_kblocks(N);
+        const size_t bytes = (size_t)kbp * rows * 128;
+        if (bytes <= kAtabMaxBytes && (int64_t)kbp * rows < (1LL << 31)) {
+            if ((e = cudaMalloc(&p.atab, bytes)) != cudaSuccess) return e;
+            p.atab_bytes = bytes;
+            p.atab_ld = rows;
+            p.table_bytes += bytes;
+            const int64_t items = (int64_t)kbp * (rows / 2) * 8;
+            const int blocks = (int)std::min<int64_t>((items + 255) / 256, (int64_t)p.sm_count * 32);
+            k_atab<<<blocks, 256, 0, s>>>(N, 1, p.pair_slots, rows, kbp, p.ang, nth, static_cast<uint4 *>(p.atab));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            p.tmap_a = std::aligned_alloc(64, sizeof(CUtensorMap));
+            if (!p.tmap_a) return cudaErrorMemoryAllocation;
+            if ((e = make_tmap(p.atab, (int64_t)kbp * rows, static_cast<CUtensorMap *>(p.tmap_a))) != cudaSuccess)
+                return e;
+        }
+    }
     p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));  // CUtensorMap wants 64-byte alignment
     if (!p.tmap_host) return cudaErrorMemoryAllocation;
     if ((e = make_tmap(p.ws, std::max<int64_t>(L.b_rows, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
@@ -2335,8 +2405,12 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     alignas(64) CUtensorMap omap;
     const bool tma_out =
         (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap, 32) == cudaSuccess;
-    cudaError_t e = launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
-                                                   tma_out ? &omap : nullptr, s);
+    P.a_ld = p.atab_ld;
+    const bool atab = p.atab && p.tune_atab == 0;
+    cudaError_t e = atab ? launch_gemm<2, false, 0, true, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
+                                                               tma_out ? &omap : nullptr, s)
+                         : launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
+                                                          tma_out ? &omap : nullptr, s);
     if (e != cudaSuccess) return e;
     *launches += 1;
     p.last_variant = 2;

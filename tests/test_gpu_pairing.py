@@ -5,7 +5,8 @@ so bins +c and -c of the NDFT come from one pair of real contractions,
 U = S_r v + F_r sigma(v) and V = S_i v + F_i sigma(v): X[+c] = U + jV,
 X[-c] = U - jV; bin 0 is the packing kernel's sum of v + sigma(v).  Every case
 is checked against the fp64 oracle at the fp32 bar (1e-5 of max |X|), with the
-paired path forced (tuning key 6 = 2) and cross-checked against the unpaired
+paired path forced (tuning key 6 = 2; its A operand from the plan's table or,
+with key 7 = 1, generated on chip) and cross-checked against the unpaired
 rows (key 6 = 1) on the same inputs: centred and full windows, windows that
 wrap past bin 0, contain N/2 or give an odd number of paired frequencies (the
 element-wise fold-out), ragged N, both CAF flags and several sample-axis
@@ -64,16 +65,18 @@ def test_paired_ndft(api, N, batch, p0, nbins):
     nb = nbins or N
     ref = oracle.ndft(x.astype(np.complex128), p0=p0, nbins=nb)
     outs = {}
-    for key in (2, 1):
+    for key, atab in ((2, 0), (2, 1), (1, 0)):  # paired (A from the table / generated), unpaired
         p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="ternary", prec="bf16x2")
         assert p.query(0) == slots(N, p0, nb)
         p.set_tuning(6, key)
+        p.set_tuning(7, atab)
         got = p.ndft(dev(x)).cpu().numpy()
         p.query_error()
         assert p.query(1) == (2 if key == 2 else 1)
-        assert relerr(got, ref) < TOL, key
-        outs[key] = got
-    assert np.max(np.abs(outs[2] - outs[1])) / np.max(np.abs(ref)) < 2 * TOL
+        assert relerr(got, ref) < TOL, (key, atab)
+        outs[(key, atab)] = got
+    assert np.max(np.abs(outs[(2, 0)] - outs[(1, 0)])) / np.max(np.abs(ref)) < 2 * TOL
+    assert np.max(np.abs(outs[(2, 0)] - outs[(2, 1)])) / np.max(np.abs(ref)) < 2 * TOL
 
 
 @pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
@@ -86,22 +89,21 @@ def test_paired_ndft(api, N, batch, p0, nbins):
 def test_paired_caf(api, N, lag0, nlags, p0, nbins, flags):
     sc = scenes.radar_scene(N=N, nlags=min(nlags, 64), nbins=min(nbins, 64), seed=61 + N % 97)
     ref = oracle.caf(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, flags=flags, z32=True)
-    outs = {}
-    for key in (2, 1):
+    for key, atab in ((2, 0), (2, 1), (1, 0)):  # paired (A from the table / generated), unpaired
         p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="ternary", prec="bf16x2")
         p.set_tuning(6, key)
+        p.set_tuning(7, atab)
         got = p.caf(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags).cpu().numpy()
         p.query_error()
         assert p.query(1) == (2 if key == 2 else 1)
         if np.max(np.abs(ref)) == 0:
             assert np.max(np.abs(got)) == 0
         else:
-            assert relerr(got, ref) < TOL, key
-        outs[key] = got
+            assert relerr(got, ref) < TOL, (key, atab)
 
 
-@pytest.mark.parametrize("split", [0, 1, 3, 19])
-def test_paired_caf_splits_sampled(api, split):
+@pytest.mark.parametrize("split,atab", [(0, 0), (1, 0), (3, 0), (19, 0), (0, 1), (19, 1)])
+def test_paired_caf_splits_sampled(api, split, atab):
     """The headline layout at N = 16384: 1024 lags x bins -512..511 (512 paired
     frequencies, bin 0 from the DC sums), every sample-axis split count giving
     the same cells within the bar; the default choice pairs."""
@@ -109,6 +111,7 @@ def test_paired_caf_splits_sampled(api, split):
     p = api.Plan(sc.N, p0=-512, nbins=1024, max_lags=1024, form="ternary", prec="bf16x2")
     assert p.query(0) == 512
     p.set_tuning(0, split)
+    p.set_tuning(7, atab)  # 0: A tiles from the plan's table, 1: generated on chip
     A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 1024)
     idx, _ = api.argmax(A.reshape(1, -1))
     got = A.cpu().numpy()
