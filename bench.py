@@ -636,7 +636,8 @@ def main():
     long_run = t_total / 1000.0 > 1.0 and sus is not None
     peak_used = sus if long_run else bf16_peak
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_used, "unit": "TFLOP/s",
-                "frac": achieved / peak_used, "traffic": gemm_traffic(per_step), "kernel": "k_ternary_gemm",
+                "frac": achieved / peak_used, "traffic": gemm_traffic(per_step),
+                "kernel": "k_ternary_gemm_pair (2-SM pair tile)" if plan.query(3) == 258 else "k_ternary_gemm",
                 "peak_source": f"{peak_src} bf16 dense ({'sustained' if long_run else 'burst'})",
                 "frac_burst": achieved / bf16_peak,
                 "frac_sustained": achieved / sus if sus else None,

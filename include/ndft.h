@@ -259,10 +259,13 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
 
 /* Tile / split choice for the plan's kernels: key 0 = split count along the
  * sample axis (0 = automatic); key 1 = ternary-GEMM tile (256: 256 rows in one
- * CTA with one tensor-memory accumulator pair, the default; 128: 128 rows with
- * two accumulators used in turn; 258: the 256-row tile on a 2-SM pair, M = 256
+ * CTA with one tensor-memory accumulator pair; 128: 128 rows with two
+ * accumulators used in turn; 258: the 256-row tile on a 2-SM pair, M = 256
  * MMAs with each CTA holding half of A and of B and two tensor-memory
- * accumulators used in turn); key 2 = ternary-GEMM K blocks
+ * accumulators used in turn, so that one chain's fold-out runs under the next
+ * chain's MMAs; 0, the default: the 2-SM pair for the conjugate-paired
+ * contraction with its A operand from the plan's table (key 7 = 0), 256
+ * everywhere else); key 2 = ternary-GEMM K blocks
  * per tensor-memory accumulation chain before it is folded into the fp32
  * result (0 = the default: 64 blocks of 8 samples, or of 16 samples in the
  * conjugate-paired contraction of key 6); key 3 = ternary-GEMM fold path (0: bulk
@@ -287,8 +290,14 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * U = S_r v + F_r sigma(v), V = S_i v + F_i sigma(v): X[+c] = U + jV,
  * X[-c] = U - jV, half the multiply-adds per bin; bin 0 is summed by the
  * packing kernel); 1 = never; 2 = wherever the window allows it.  Pairing is
- * used with the default tile and one column part only.  Same bar, different
- * fp32 rounding. */
+ * used with 256-row tiles (key 1 = 0, 256, or 258 with the A table) and one
+ * column part only.  Same bar, different fp32 rounding.
+ * Key 7 = the paired contraction's A operand (the S/F rows of Eq. 6 for
+ * frequencies 1 .. S in bf16 hi/lo): 0 (default) = loaded by TMA from a table
+ * the plan builds at creation (16 MiB per 1024 samples of a 1024-bin window;
+ * built only while it stays within 2 GiB), 1 = generated on chip per K block
+ * by producer warps from the twiddle table (the only form for larger tables).
+ * Same bar either way. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
 
 /* Read-only facts about a plan and its last exec call, into *value:
@@ -297,7 +306,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
  * key 1 = the contraction variant of the last exec call: 0 none or not a
  *         tensor-core call, 1 one row pair per bin, 2 conjugate-paired rows;
  * key 2 = the sample-axis split count of the last exec call's contraction
- *         (0 if none).
+ *         (0 if none);
+ * key 3 = the tile of that contraction: 256 or 128 rows on one CTA, 258 the
+ *         256-row tile on a 2-SM pair (0 if none).
  * NDFT_E_INVALID for another key or a NULL argument. */
 ndft_status ndft_plan_query(ndft_plan_t plan, int32_t key, int64_t *value);
 

@@ -105,7 +105,8 @@ class Plan:
     def query(self, key: int) -> int:
         """ndft_plan_query: 0 = paired frequencies S of the window, 1 = last call's
         contraction variant (0 none, 1 unpaired rows, 2 conjugate-paired rows),
-        2 = last call's sample-axis split count."""
+        2 = last call's sample-axis split count, 3 = its tile (256 / 128 rows on
+        one CTA, 258 the 2-SM pair)."""
         v = ctypes.c_int64()
         L.check(self.lib.ndft_plan_query(self.handle, int(key), ctypes.byref(v)), "ndft_plan_query")
         return v.value

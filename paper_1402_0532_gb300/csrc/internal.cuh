@@ -71,11 +71,13 @@ struct Plan {
     int tune_parts = 1;          // ternary form: 1 one part (default); 0 two parts, half each; else part 0's columns
     int tune_pair = 0;           // ternary form: 0 conjugate-paired rows where they save work (default), 1 never
     int pair_slots = 0;          // ternary form: frequencies 1 .. pair_slots cover the bin window (0: none)
+    int tune_bgen = 0;           // ternary form: paired B operand 0/1 packed by a kernel, 2 formed in the pair tile
     int tune_atab = 0;           // ternary form: 0 paired A tiles from the plan's table when built, 1 generated on chip
     void *atab = nullptr;        // ternary form: the paired contraction's A operand, [K block][rows] x 128 B
     size_t atab_bytes = 0;
     int32_t atab_ld = 0;         // its rows per K block
     void *tmap_a = nullptr;      // its TMA descriptor (host copy)
+    void *tmap_a2 = nullptr;     // the same with a 128-row box (2-SM pair tile)
     size_t dc_bytes = 0;         // ternary form: per-tile DC sums of the paired packing
     // ternary form: side stream and events of the two-part contraction (the
     // second part's packing runs under the first part's contraction)
@@ -84,6 +86,7 @@ struct Plan {
     int last_launches = 0;
     int last_variant = 0;        // contraction of the last exec call: 0 none, 1 unpaired rows, 2 paired rows
     int last_nsplit = 0;         // its sample-axis split count
+    int last_tile = 0;           // its tile: 256 / 128 rows on one CTA, 258 the 2-SM pair
     // optional timing of the main contraction kernel (event pairs, see ndft_timer_start)
     mutable cudaEvent_t *tev = nullptr;
     mutable int tcap = 0;

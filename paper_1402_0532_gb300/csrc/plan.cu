@@ -68,9 +68,9 @@ const char *variant_name(int v) { return v == 2 ? "paired" : v == 1 ? "unpaired"
 
 ndft_status log_exec(const char *what, const Plan &p, int64_t cols, ndft_status st) {
     if (log_on())
-        logf("%s N=%d bins=%d@%d cols=%lld form=%s prec=%s variant=%s splits=%d launches=%d status=%d", what, p.d.n,
-             p.d.nbins, p.d.p0, (long long)cols, form_name(p.d.form), prec_name(p.d.prec),
-             variant_name(p.last_variant), p.last_nsplit, p.last_launches, (int)st);
+        logf("%s N=%d bins=%d@%d cols=%lld form=%s prec=%s variant=%s tile=%d splits=%d launches=%d status=%d", what,
+             p.d.n, p.d.nbins, p.d.p0, (long long)cols, form_name(p.d.form), prec_name(p.d.prec),
+             variant_name(p.last_variant), p.last_tile, p.last_nsplit, p.last_launches, (int)st);
     return st;
 }
 
@@ -107,6 +107,7 @@ void free_plan(Plan &p) {
     cudaFree(p.ws);
     cudaFree(p.atab);
     std::free(p.tmap_a);
+    std::free(p.tmap_a2);
     cudaFree(p.err);
     cudaFree(p.cpis_dev);
     cudaFree(p.tab_arena);
@@ -240,7 +241,7 @@ ndft_status ndft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
     if (!plan || plan->p.batched || batch < 0 || batch > plan->p.d.max_batch) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X) || x == X) return NDFT_E_INVALID;
     if (p.d.flags & NDFT_F_ABS_OUT) return NDFT_E_UNSUPPORTED;
@@ -267,7 +268,7 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
         return NDFT_E_INVALID;
     if ((p.d.flags & NDFT_F_NFFT_DIF) && p.d.n > 65536) return NDFT_E_UNSUPPORTED;
     p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     if (batch == 0) return NDFT_OK;
     if (!aligned16(x) || !aligned16(X)) return NDFT_E_INVALID;
     return log_exec("nfft_exec", p, batch, from_cuda(launch_nfft(p, x, X, batch, stream, &p.last_launches)));
@@ -281,7 +282,7 @@ ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, in
     if (A == s_surv || A == s_ref) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     cudaError_t e;
     if (p.d.form == NDFT_FORM_DIRECT)
         e = launch_direct_caf(p, s_surv, s_ref, lag0, nlags, A, stream, &p.last_launches);
@@ -304,13 +305,13 @@ ndft_status caf_backward(ndft_plan_t plan, const void *s_surv, const void *s_ref
     if (!aligned16(s_ref) || !aligned16(dA) || !aligned16(ds)) return NDFT_E_INVALID;
     if (ds == s_ref || ds == dA) return NDFT_E_INVALID;
     p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     if (p.d.form == NDFT_FORM_TERNARY_GEMM) {
         // the transposed ternary contraction on the tensor cores (CUDA cores if it does not fit)
         const cudaError_t e = launch_ternary_adjoint(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches);
         if (e != cudaErrorNotSupported) return from_cuda(e);
         p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     }
     return from_cuda(launch_caf_backward(p, s_ref, lag0, nlags, dA, ds, stream, &p.last_launches));
 }
@@ -329,7 +330,7 @@ ndft_status caf_backward_inputs(ndft_plan_t plan, const void *s_surv, const void
         ds_surv == s_ref || ds_surv == dA)
         return NDFT_E_INVALID;  // the fold reads both inputs while it writes the gradients
     p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     const cudaError_t e =
         launch_caf_backward_inputs(p, s_surv, s_ref, lag0, nlags, dA, ds_surv, ds_ref, stream, &p.last_launches);
     if (e == cudaErrorNotSupported) return NDFT_E_UNSUPPORTED;
@@ -438,6 +439,7 @@ ndft_status ndft_plan_query(ndft_plan_t plan, int32_t key, int64_t *value) {
     if (key == 0) *value = p.pair_slots;
     else if (key == 1) *value = p.last_variant;
     else if (key == 2) *value = p.last_nsplit;
+    else if (key == 3) *value = p.last_tile;
     else return NDFT_E_INVALID;
     return NDFT_OK;
 }
@@ -468,6 +470,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
     } else if (key == 7) {
         if (value > 1) return NDFT_E_INVALID;
         plan->p.tune_atab = value;
+    } else if (key == 8) {
+        if (value > 2) return NDFT_E_INVALID;
+        plan->p.tune_bgen = value;
     } else {
         return NDFT_E_INVALID;
     }
@@ -600,7 +605,7 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
     if (out_base == surv_base || out_base == ref_base) return NDFT_E_INVALID;
     Plan &p = plan->p;
     p.last_launches = 0;
-    p.last_variant = p.last_nsplit = 0;
+    p.last_variant = p.last_nsplit = p.last_tile = 0;
     if (p.d.form == NDFT_FORM_TERNARY_GEMM)
         return from_cuda(launch_ternary_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));
     return from_cuda(launch_direct_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));

@@ -358,6 +358,103 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_
     lo = bf2(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xFFFF0000u));
 }
 
+struct PackProb {
+    int64_t a_off;    // elements from the launch's first input base: x (NDFT) or s_surv (CAF)
+    int64_t r_off;    // elements from the launch's second input base: s_ref (CAF)
+    int32_t N, lag0, ncols, kblocks;
+    int64_t ldx;      // row stride of x
+    int64_t row0;     // first packed row
+};
+
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
+// Real a (x) b = sgn(a) (sgn(b) |a| + b): the fma rounds sgn(b)(|a| + |b|)
+// once (round to nearest is sign-symmetric) and the outer sign is exact, so
+// this is |a| + |b| rounded once with the sign of Eq. 2; a zero operand gives
+// a zero (of either sign, which no later step distinguishes).
+__device__ __forceinline__ float ox_fma(float a, float sa, float b, float sb) { return sa * fmaf(sb, fabsf(a), b); }
+
+// Eq. 6 for the lag product s (x) c, c = conj(r) (or r with NDFT_F_NO_CONJ_REF).
+__device__ __forceinline__ float2 lag_ox(float2 s, float2 r, bool conj) {
+    const float cr = r.x, ci = conj ? -r.y : r.y;
+    const float ss_r = sgnf(s.x), ss_i = sgnf(s.y), sc_r = sgnf(cr), sc_i = sgnf(ci);
+    const float t1 = ox_fma(s.x, ss_r, cr, sc_r), t2 = ox_fma(s.y, ss_i, ci, sc_i);
+    const float t3 = ox_fma(s.y, ss_i, cr, sc_r), t4 = ox_fma(ci, sc_i, s.x, ss_r);
+    return make_float2(__fsub_rn(t1, t2), __fadd_rn(t3, t4));
+}
+
+// ---- the conjugate-paired B operand, two samples of one input column ----------
+// Samples i (even) and i + 1 of column `lag` - lag0: the CAF lag products
+// v = s_surv[i] (x) conj(s_ref[i - lag]) (Eq. 12a; zero where i - lag falls
+// outside the reference, wrapped with circular lags) or, for the NDFT, the
+// input row itself (`a` = that row); zero past N.  `vec`: `a` is 16-byte
+// aligned, so the two samples are one 16-byte load.
+// The loads: v0, v1 = the inputs at i, i + 1 and (CAF) r0, r1 = the reference
+// at i - lag, i + 1 - lag; pair_combine forms the lag products from them.
+__device__ __forceinline__ void pair_loads(const float2 *__restrict__ a, const float2 *__restrict__ r, int i, int N,
+                                           int64_t lag, bool caf, bool circ, bool vec, float2 &v0, float2 &v1,
+                                           float2 &r0, float2 &r1) {
+    const float2 zero = make_float2(0.f, 0.f);
+    v0 = v1 = r0 = r1 = zero;
+    if (i + 1 < N && vec) {
+        const float4 s2 = *reinterpret_cast<const float4 *>(a + i);
+        v0 = make_float2(s2.x, s2.y);
+        v1 = make_float2(s2.z, s2.w);
+    } else {
+        if (i < N) v0 = a[i];
+        if (i + 1 < N) v1 = a[i + 1];
+    }
+    if (caf) {
+        int64_t j = (int64_t)i - lag;
+        if (circ) {
+            j %= N;
+            if (j < 0) j += N;
+        }
+        int64_t j1 = j + 1;
+        if (circ && j1 == N) j1 = 0;
+        if (i < N && j >= 0 && j < N) r0 = r[j];
+        if (i + 1 < N && j1 >= 0 && j1 < N) r1 = r[j1];
+    }
+}
+__device__ __forceinline__ void pair_combine(bool caf, bool conj, float2 r0, float2 r1, float2 &v0, float2 &v1) {
+    if (caf) {
+        v0 = lag_ox(v0, r0, conj);
+        v1 = lag_ox(v1, r1, conj);
+    }
+}
+__device__ __forceinline__ void pair_samples(const float2 *__restrict__ a, const float2 *__restrict__ r, int i, int N,
+                                             int64_t lag, bool caf, bool conj, bool circ, bool vec, float2 &v0,
+                                             float2 &v1) {
+    float2 r0, r1;
+    pair_loads(a, r, i, N, lag, caf, circ, vec, v0, v1, r0, r1);
+    pair_combine(caf, conj, r0, r1, v0, v1);
+}
+
+// The (col, r) and (col, i) chunks of v0, v1 ([v_hi, v_lo, sigma, sigma] as
+// bf16x2 words of the two samples) and their terms v + sigma(v) of the
+// column's bin-0 sum.
+__device__ __forceinline__ void pair_chunks(float2 v0, float2 v1, uint4 &re, uint4 &im, float &dr, float &di) {
+    uint32_t hr, lr, hi, li;
+    split2(v0.x, v1.x, hr, lr);
+    split2(v0.y, v1.y, hi, li);
+    const float g0r = sgnf(v0.x), g1r = sgnf(v1.x), g0i = sgnf(v0.y), g1i = sgnf(v1.y);
+    const uint32_t sr2 = bf2(g0r, g1r), si2 = bf2(g0i, g1i);
+    re = make_uint4(hr, lr, sr2, sr2);
+    im = make_uint4(hi, li, si2, si2);
+    dr = (v0.x + g0r) + (v1.x + g1r);
+    di = (v0.y + g0i) + (v1.y + g1i);
+}
+
+// Operand generation inside the 2-SM pair tile: what the packing kernel reads.
+struct BGen {
+    PackProb pp;
+    const float2 *a;  // launch's first input base (x or s_surv)
+    const float2 *r;  // s_ref (CAF)
+    float2 *dc;       // bin-0 sums [nsplit][ncols]
+    uint32_t flags;
+    int32_t caf;
+};
+
 // The R and I chunks of one frequency for samples a and a + 1 (twiddles Wa, Wb
 // at indices ua, ub).
 __device__ __forceinline__ void gen_conj_chunk(float ua, float ub, float2 Wa, float2 Wb, float fN, uint4 &re,
@@ -1281,10 +1378,24 @@ __device__ __forceinline__ void commit2_mc(uint64_t *bar) {
 
 // `tmap` has a 128-row box (one CTA's B half).  Forward single-surface
 // contraction only (the batched and adjoint modes keep the one-CTA tile).
-__global__ void __launch_bounds__(kThreads, 1)
+// ATAB: the conjugate-paired contraction with its A operand from the plan's
+// table (`amap`, 128-row box: each CTA loads its 128 rows, completion on the
+// even CTA's barrier like B); no A producer warps run.
+// BGEN (with ATAB): the B operand is not loaded but formed in shared memory by
+// 16 producer warps of each CTA from the inputs (`bg`), the same chunks the
+// packing kernel writes: thread g of a CTA forms chunk t = g & 7 of the CTA's
+// lag column j = g >> 3 (rows 2 j, 2 j + 1 of its 128-row half).
+// The m-tile-0 units also sum v + sigma(v) of their columns over their K range
+// into bg.dc[split][col] (bin 0), in a fixed order.
+__host__ __device__ constexpr int pair_gen_warps(bool bgen) { return bgen ? 16 : kGenWarps; }
+__host__ __device__ constexpr int pair_threads(bool bgen) { return (2 + pair_gen_warps(bgen) + 4) * 32; }
+
+template <bool ATAB, bool BGEN>
+__global__ void __launch_bounds__(pair_threads(BGEN), 1)
     k_ternary_gemm_pair(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap,
                         int out_tma, Problem single, int64_t nunits, int chunk, int starve, float *__restrict__ out_base,
-                        int32_t *err) {
+                        int32_t *err, const __grid_constant__ CUtensorMap amap, const BGen bg) {
+    static_assert(ATAB || !BGEN, "operand generation goes with the A table");
     using namespace pair2;
     const uint32_t rank = cluster_rank();
     const bool lead = rank == 0;
@@ -1305,7 +1416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1 + 2 * kGenWarps);
+            mbar_init(&full[s], (ATAB && !BGEN) ? 1 : 1 + 2 * pair_gen_warps(BGEN));
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -1340,10 +1451,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     if (starve) continue;
-                    if (lead) mbar_arrive_tx(&full[stage], 2 * kBBytes);
-                    const int64_t row = w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN + rank * (TN / 2);
-                    tma_load_b_pair(b_base + stage * kBBytes, &tmap, (int32_t)row,
-                                    peer_addr(smem_u32(&full[stage]), 0u));
+                    if (lead) mbar_arrive_tx(&full[stage], (BGEN ? 0 : 2 * kBBytes) + (ATAB ? 2 * kABytes : 0));
+                    if constexpr (!BGEN) {
+                        const int64_t row =
+                            w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN + rank * (TN / 2);
+                        tma_load_b_pair(b_base + stage * kBBytes, &tmap, (int32_t)row,
+                                        peer_addr(smem_u32(&full[stage]), 0u));
+                    }
+                    if constexpr (ATAB) {
+                        const int64_t arow = (int64_t)kb * w.P.a_ld + (int64_t)w.mt * 256 + rank * 128;
+                        tma_load_b_pair(a_base + stage * kABytes, &amap, (int32_t)arow,
+                                        peer_addr(smem_u32(&full[stage]), 0u));
+                    }
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -1384,7 +1503,68 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
-    } else if (warp < kEpiWarp0) {
+    } else if (warp < 2 + pair_gen_warps(BGEN)) {
+        if constexpr (BGEN) {
+        // ---------------- B producers: this CTA's 64 lag columns (128 rows) ----------------
+        const int g = threadIdx.x - 64;  // 0..511
+        const int t = g & 7, j0 = g >> 3;  // chunk t of lag column j0 (rows 2 j0, 2 j0 + 1)
+        const PackProb &pp = bg.pp;
+        const int N = pp.N;
+        const bool caf = bg.caf != 0, conj = !(bg.flags & NDFT_F_NO_CONJ_REF),
+                   circ = (bg.flags & NDFT_F_CIRCULAR_LAG) != 0;
+        const float2 *r = bg.r + pp.r_off;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
+            const Work w = decode(u, single, nullptr, nullptr);
+            const bool dcw = w.mt == 0 && bg.dc != nullptr;
+            const int64_t col = (int64_t)w.nt * (TN / 2) + rank * (TN / 4) + j0;
+            const bool live = col < pp.ncols;
+            const int64_t lag = (int64_t)pp.lag0 + col;
+            const float2 *a = bg.a + pp.a_off + (caf || !live ? 0 : col * pp.ldx);
+            const bool vec = (reinterpret_cast<uintptr_t>(a) & 15u) == 0;
+            float dsr = 0.f, dsi = 0.f;
+            // inputs of the next K block, loaded while this one is formed and stored
+            float2 nv0, nv1, nr0, nr1;
+            const float2 zero = make_float2(0.f, 0.f);
+            nv0 = nv1 = nr0 = nr1 = zero;
+            if (live && w.kb0 < w.kb1) pair_loads(a, r, w.kb0 * 16 + 2 * t, N, lag, caf, circ, vec, nv0, nv1, nr0, nr1);
+            for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                float2 v0 = nv0, v1 = nv1;
+                const float2 r0 = nr0, r1 = nr1;
+                if (live && kb + 1 < w.kb1)
+                    pair_loads(a, r, (kb + 1) * 16 + 2 * t, N, lag, caf, circ, vec, nv0, nv1, nr0, nr1);
+                pair_combine(caf, conj, r0, r1, v0, v1);
+                uint4 cre, cim;
+                float dr, di;
+                pair_chunks(v0, v1, cre, cim, dr, di);
+                dsr += dr;
+                dsi += di;
+                // warp-uniform, so that an abandoned wait leaves no lane behind at the shuffles
+                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&empty[stage], phase ^ 1u, s_abort, err)))) break;
+                store_pair(b_base + stage * kBBytes, j0, t, cre, cim);
+                // the even CTA's MMA reads this CTA's tile through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    if (lead) mbar_arrive(&full[stage]);
+                    else arrive_remote(peer_addr(smem_u32(&full[stage]), 0u));
+                }
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (!ok || !dcw) continue;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                dsr += __shfl_xor_sync(0xffffffffu, dsr, o);
+                dsi += __shfl_xor_sync(0xffffffffu, dsi, o);
+            }
+            if (t == 0 && live) bg.dc[(int64_t)w.split * pp.ncols + col] = make_float2(dsr, dsi);
+        }
+        } else if constexpr (!ATAB) {
         // ---------------- A producers: this CTA's 64 bins (128 rows) ----------------
         const int g = threadIdx.x - 64;  // 0..255
         const int t = g & 7, pg = g >> 3;
@@ -1442,6 +1622,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     phase ^= 1u;
                 }
             }
+        }
         }
     } else {
         // ---------------- epilogue: this CTA's 128 rows ----------------
@@ -1561,13 +1742,6 @@ __device__ __forceinline__ uint4 pack_entry(float2 v) {
     return make_uint4(__byte_perm(uh, ul, 0x5410), __byte_perm(uh, ul, 0x7632), sr, si);
 }
 
-struct PackProb {
-    int64_t a_off;    // elements from the launch's first input base: x (NDFT) or s_surv (CAF)
-    int64_t r_off;    // elements from the launch's second input base: s_ref (CAF)
-    int32_t N, lag0, ncols, kblocks;
-    int64_t ldx;      // row stride of x
-    int64_t row0;     // first packed row
-};
 
 __device__ __forceinline__ float2 lag_product(const PackProb &P, const float2 *__restrict__ a,
                                               const float2 *__restrict__ r, int64_t col, int64_t i, uint32_t flags) {
@@ -1731,22 +1905,6 @@ __global__ void __launch_bounds__(256) k_pack_adjoint(const float2 *__restrict__
 // order and written per K-block tile (dc[tile][col]).
 constexpr int kPairPackKb = 16;  // K blocks (16 samples each) per packing tile
 
-__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
-
-// Real a (x) b = sgn(a) (sgn(b) |a| + b): the fma rounds sgn(b)(|a| + |b|)
-// once (round to nearest is sign-symmetric) and the outer sign is exact, so
-// this is |a| + |b| rounded once with the sign of Eq. 2; a zero operand gives
-// a zero (of either sign, which no later step distinguishes).
-__device__ __forceinline__ float ox_fma(float a, float sa, float b, float sb) { return sa * fmaf(sb, fabsf(a), b); }
-
-// Eq. 6 for the lag product s (x) c, c = conj(r) (or r with NDFT_F_NO_CONJ_REF).
-__device__ __forceinline__ float2 lag_ox(float2 s, float2 r, bool conj) {
-    const float cr = r.x, ci = conj ? -r.y : r.y;
-    const float ss_r = sgnf(s.x), ss_i = sgnf(s.y), sc_r = sgnf(cr), sc_i = sgnf(ci);
-    const float t1 = ox_fma(s.x, ss_r, cr, sc_r), t2 = ox_fma(s.y, ss_i, ci, sc_i);
-    const float t3 = ox_fma(s.y, ss_i, cr, sc_r), t4 = ox_fma(ci, sc_i, s.x, ss_r);
-    return make_float2(__fsub_rn(t1, t2), __fadd_rn(t3, t4));
-}
 
 __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, bool caf,
                                                    const float2 *__restrict__ a_base,
@@ -1770,41 +1928,18 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
         if (live) {
             for (int kb = kb0; kb < kb1; ++kb) {
                 const int i = kb * 16 + 2 * t;  // < 2^18 + 16
-                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-                if (i + 1 < N && vec) {
-                    const float4 s2 = *reinterpret_cast<const float4 *>(a + i);  // i even, a 16-byte aligned
-                    v0 = make_float2(s2.x, s2.y);
-                    v1 = make_float2(s2.z, s2.w);
-                } else {
-                    if (i < N) v0 = a[i];
-                    if (i + 1 < N) v1 = a[i + 1];
-                }
-                if (caf) {
-                    int64_t j = (int64_t)i - lag;
-                    if (circ) {
-                        j %= N;
-                        if (j < 0) j += N;
-                    }
-                    int64_t j1 = j + 1;
-                    if (circ && j1 == N) j1 = 0;
-                    const float2 zero = make_float2(0.f, 0.f);
-                    const float2 r0 = (i < N && j >= 0 && j < N) ? r[j] : zero;
-                    const float2 r1 = (i + 1 < N && j1 >= 0 && j1 < N) ? r[j1] : zero;
-                    v0 = lag_ox(v0, r0, conj);
-                    v1 = lag_ox(v1, r1, conj);
-                }
+                float2 v0, v1;
+                pair_samples(a, r, i, N, lag, caf, conj, circ, vec, v0, v1);
                 const int64_t row = P.row0 + (int64_t)kb * ncols2 + 2LL * col;
-                uint32_t hr, lr, hi, li;
-                split2(v0.x, v1.x, hr, lr);
-                split2(v0.y, v1.y, hi, li);
-                const float g0r = sgnf(v0.x), g1r = sgnf(v1.x), g0i = sgnf(v0.y), g1i = sgnf(v1.y);
-                const uint32_t sr2 = bf2(g0r, g1r), si2 = bf2(g0i, g1i);
+                uint4 cre, cim;
+                float dr, di;
+                pair_chunks(v0, v1, cre, cim, dr, di);
                 if (ndft_in(row >= P.row0 && row + 1 < row_end, err)) {
-                    B[row * 8 + t] = make_uint4(hr, lr, sr2, sr2);
-                    B[(row + 1) * 8 + t] = make_uint4(hi, li, si2, si2);
+                    B[row * 8 + t] = cre;
+                    B[(row + 1) * 8 + t] = cim;
                 }
-                sr += (v0.x + g0r) + (v1.x + g1r);
-                si += (v0.y + g0i) + (v1.y + g1i);
+                sr += dr;
+                si += di;
             }
         }
 #pragma unroll
@@ -2111,10 +2246,17 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
 }
 
 // The 2-SM pair tile: one unit per pair, 2 x min(units, SMs / 2) CTAs in clusters of 2.
+template <bool ATAB = false, bool BGEN = false>
 cudaError_t launch_gemm_pair(const Plan &p, const Problem &single, int64_t nunits, float *out_base,
-                             const CUtensorMap *omap, cudaStream_t s) {
+                             const CUtensorMap *omap, cudaStream_t s, const BGen *bgen = nullptr) {
     constexpr size_t smem = pair2::kSmemTotal;
-    cudaError_t e = cudaFuncSetAttribute(k_ternary_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ATAB && !p.tmap_a2) return cudaErrorInvalidValue;
+    if (BGEN && !bgen) return cudaErrorInvalidValue;
+    BGen bg{};
+    if (bgen) bg = *bgen;
+    auto kern = k_ternary_gemm_pair<ATAB, BGEN>;
+    constexpr int threads = pair_threads(BGEN);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host2);  // 128-row box
     const int chunk = p.tune_chunk > 0 ? p.tune_chunk : kChunk;
@@ -2124,7 +2266,7 @@ cudaError_t launch_gemm_pair(const Plan &p, const Problem &single, int64_t nunit
     const int out_tma = omap ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(nunits, p.sm_count / 2)));
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -2135,15 +2277,18 @@ cudaError_t launch_gemm_pair(const Plan &p, const Problem &single, int64_t nunit
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     timer_begin(p, s);
-    e = cudaLaunchKernelEx(&cfg, k_ternary_gemm_pair, *map, om, out_tma, single, nunits, chunk, p.test_starve,
-                           out_base, p.err);
+    const CUtensorMap &am = (ATAB && p.tmap_a2) ? *static_cast<const CUtensorMap *>(p.tmap_a2) : none;
+    e = cudaLaunchKernelEx(&cfg, kern, *map, om, out_tma, single, nunits, chunk, p.test_starve, out_base, p.err, am,
+                           bg);
     timer_end(p, s);
     return e;
 }
 
-// Tile shape (tuning key 1): 256 rows in one CTA (one accumulator pair, the
-// default), 128 rows with two accumulators used in turn (128), or the 256 x 256
-// tile on a 2-SM pair (258, cta_group::2).
+// Tile shape (tuning key 1): 256 rows in one CTA (one accumulator pair), 128
+// rows with two accumulators used in turn (128), or the 256 x 256 tile on a
+// 2-SM pair (258, cta_group::2).  The default (0) is the 2-SM pair for the
+// conjugate-paired contraction with its A operand from the plan's table and the
+// one-CTA 256-row tile everywhere else.
 int tile_halves(const Plan &p) { return p.tune_cols == 128 ? 1 : 2; }
 bool tile_pair(const Plan &p) { return p.tune_cols == 258; }
 
@@ -2254,6 +2399,11 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
             if (!p.tmap_a) return cudaErrorMemoryAllocation;
             if ((e = make_tmap(p.atab, (int64_t)kbp * rows, static_cast<CUtensorMap *>(p.tmap_a))) != cudaSuccess)
                 return e;
+            p.tmap_a2 = std::aligned_alloc(64, sizeof(CUtensorMap));  // 128-row box for the 2-SM pair tile
+            if (!p.tmap_a2) return cudaErrorMemoryAllocation;
+            if ((e = make_tmap(p.atab, (int64_t)kbp * rows, static_cast<CUtensorMap *>(p.tmap_a2), TN / 2)) !=
+                cudaSuccess)
+                return e;
         }
     }
     p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));  // CUtensorMap wants 64-byte alignment
@@ -2335,6 +2485,7 @@ static cudaError_t gemm_cols(Plan &p, int nc, int64_t b_row0, void *out, cudaStr
     *launches += 1;
     p.last_variant = 1;
     p.last_nsplit = P.nsplit;
+    p.last_tile = pair ? 258 : rows;
     if (abs_out) {
         *launches += 1;
         return launch_reduce_abs(reinterpret_cast<const float2 *>(part), P.nsplit, (int64_t)nc * nb,
@@ -2376,7 +2527,16 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     pp.kblocks = kblocks;
     pp.ncols = ncols;
     pp.row0 = 0;
-    {
+    const int64_t tiles = (int64_t)((2 * S + 255) / 256) * ((2LL * ncols + TN - 1) / TN);
+    const int64_t cap_units = (int64_t)(p.part_bytes / ((size_t)256 * TN * sizeof(float)));
+    // A from the plan's table: the 2-SM pair tile unless key 1 asks for the one-CTA tile
+    const bool atab = p.atab && p.tune_atab == 0;
+    const bool pair_tile = atab && (p.tune_cols == 0 || tile_pair(p));
+    const int nsplit = choose_split(tiles, kblocks, pair_tile ? p.sm_count / 2 : p.sm_count, p.tune_split, cap_units);
+    // B formed inside the pair tile (key 8 = 2), its bin-0 sums one row per split
+    const bool bgen =
+        pair_tile && p.tune_bgen == 2 && (size_t)nsplit * ncols * sizeof(float2) <= p.dc_bytes;
+    if (!bgen) {
         const int gx = (ncols + 31) / 32;
         k_pack_pair<<<dim3(gx, std::min(gy, 65535)), 256, 0, s>>>(
             pp, p.d.flags, caf, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base),
@@ -2393,9 +2553,7 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     P.kblocks = kblocks;
     P.mtiles = (2 * S + 255) / 256;
     P.ntiles = (P.ncols + TN - 1) / TN;
-    const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
-    const int64_t cap_units = (int64_t)(p.part_bytes / ((size_t)256 * TN * sizeof(float)));
-    P.nsplit = choose_split(tiles, kblocks, p.sm_count, p.tune_split, cap_units);
+    P.nsplit = nsplit;
     P.b_row0 = 0;
     P.ld = 2LL * S;
     P.split_stride = (int64_t)P.ncols * 2 * S;
@@ -2406,22 +2564,39 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     const bool tma_out =
         (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap, 32) == cudaSuccess;
     P.a_ld = p.atab_ld;
-    const bool atab = p.atab && p.tune_atab == 0;
-    cudaError_t e = atab ? launch_gemm<2, false, 0, true, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
-                                                               tma_out ? &omap : nullptr, s)
-                         : launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
-                                                          tma_out ? &omap : nullptr, s);
+    cudaError_t e;
+    if (pair_tile) {
+        // the 2-SM pair tile: two accumulators in turn, the fold-out under the next chain
+        alignas(64) CUtensorMap omap16;
+        const bool tma16 =
+            (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap16) == cudaSuccess;
+        if (bgen) {
+            const BGen bg{pp, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base), dc,
+                          p.d.flags, caf ? 1 : 0};
+            e = launch_gemm_pair<true, true>(p, P, tiles * P.nsplit, part, tma16 ? &omap16 : nullptr, s, &bg);
+        } else {
+            e = launch_gemm_pair<true>(p, P, tiles * P.nsplit, part, tma16 ? &omap16 : nullptr, s);
+        }
+    } else if (atab) {
+        e = launch_gemm<2, false, 0, true, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
+                                                 tma_out ? &omap : nullptr, s);
+    } else {
+        e = launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, tma_out ? &omap : nullptr,
+                                           s);
+    }
     if (e != cudaSuccess) return e;
     *launches += 1;
     p.last_variant = 2;
     p.last_nsplit = P.nsplit;
+    p.last_tile = pair_tile ? 258 : 256;
     const dim3 fgrid(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins);
+    const int dc_rows = bgen ? P.nsplit : gy;  // bin-0 partials: per split, or per packing tile
     if (p.d.flags & NDFT_F_ABS_OUT)
         k_pair_fold<true><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
-                                                      gy, ncols, out, p.err);
+                                                      dc_rows, ncols, out, p.err);
     else
         k_pair_fold<false><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
-                                                       gy, ncols, out, p.err);
+                                                       dc_rows, ncols, out, p.err);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -2431,8 +2606,8 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
 // the partials of one split fit, and the paired contraction issues fewer
 // K-block steps than the unpaired one.
 static bool use_pair(const Plan &p, int ncols) {
-    if (p.tune_pair == 1 || p.pair_slots < 1 || tile_pair(p) || tile_halves(p) != 2 || first_part_cols(p, ncols))
-        return false;
+    if (p.tune_pair == 1 || p.pair_slots < 1 || tile_halves(p) != 2 || first_part_cols(p, ncols)) return false;
+    if (tile_pair(p) && !(p.atab && p.tune_atab == 0)) return false;  // the pair tile needs the A table
     const int64_t S = p.pair_slots, nb = p.d.nbins, N = p.d.n;
     if ((size_t)2 * ncols * 2 * S * sizeof(float) > p.part_bytes) return false;
     if ((size_t)pair_pack_tiles((int)N) * ncols * sizeof(float2) > p.dc_bytes) return false;
@@ -2552,6 +2727,7 @@ cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nla
             *launches += 2;
             p.last_variant = 2;
             p.last_nsplit = P.nsplit;
+            p.last_tile = 256;
             return launch_reduce_splits(part, (int)slices, 2LL * N, static_cast<float *>(ds), s);
         }
     }
@@ -2595,6 +2771,7 @@ cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nla
     *launches += 2;
     p.last_variant = 1;
     p.last_nsplit = P.nsplit;
+    p.last_tile = 256;
     return launch_reduce_splits(part, (int)slices, 2LL * N, static_cast<float *>(ds), s);
 }
 
@@ -2661,6 +2838,7 @@ cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const floa
             *launches += 1;
             p.last_variant = 2;
             p.last_nsplit = ns;
+            p.last_tile = 256;
             *G = reinterpret_cast<const float2 *>(g);
             *nsplit = ns;
             *split_stride = (int64_t)nc * N;  // complex elements (2 nc N floats)
@@ -2706,6 +2884,7 @@ cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const floa
     *launches += 1;
     p.last_variant = 1;
     p.last_nsplit = ns;
+    p.last_tile = 256;
     *G = reinterpret_cast<const float2 *>(g);
     *nsplit = ns;
     *split_stride = (int64_t)nc * N;  // complex elements

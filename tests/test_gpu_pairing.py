@@ -5,9 +5,11 @@ so bins +c and -c of the NDFT come from one pair of real contractions,
 U = S_r v + F_r sigma(v) and V = S_i v + F_i sigma(v): X[+c] = U + jV,
 X[-c] = U - jV; bin 0 is the packing kernel's sum of v + sigma(v).  Every case
 is checked against the fp64 oracle at the fp32 bar (1e-5 of max |X|), with the
-paired path forced (tuning key 6 = 2; its A operand from the plan's table or,
-with key 7 = 1, generated on chip) and cross-checked against the unpaired
-rows (key 6 = 1) on the same inputs: centred and full windows, windows that
+paired path forced (tuning key 6 = 2; its A operand from the plan's table on
+the 2-SM pair tile, the default, or on the one-CTA tile, key 1 = 256, or
+generated on chip, key 7 = 1; its B operand packed by a kernel or, key 8 = 2,
+formed inside the pair tile) and cross-checked against the unpaired rows (key 6 = 1) on the
+same inputs: centred and full windows, windows that
 wrap past bin 0, contain N/2 or give an odd number of paired frequencies (the
 element-wise fold-out), ragged N, both CAF flags and several sample-axis
 splits."""
@@ -41,6 +43,26 @@ def relerr(got, ref):
     return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
 
 
+# (key 6, key 7, key 1, key 8) -> tile: paired with A from the table on the
+# 2-SM pair (default), the same with B formed in the tile, A from the table on
+# one CTA, A generated on chip; unpaired
+COMBOS = ((2, 0, 0, 0), (2, 0, 0, 2), (2, 0, 256, 0), (2, 1, 0, 0), (1, 0, 0, 0))
+TILE = {(2, 0, 0, 0): 258, (2, 0, 0, 2): 258, (2, 0, 256, 0): 256, (2, 1, 0, 0): 256, (1, 0, 0, 0): 256}
+
+
+def configure(p, key, atab, tile, bgen):
+    p.set_tuning(6, key)
+    p.set_tuning(7, atab)
+    p.set_tuning(1, tile)
+    p.set_tuning(8, bgen)
+
+
+def bin0_index(N, p0, nbins):
+    """Index of bin 0 (frequency 0) in the window, or None."""
+    k = (-p0) % N
+    return k if k < nbins else None
+
+
 def slots(N, p0, nbins):
     p = (p0 + np.arange(nbins)) % N
     return int(np.max(np.minimum(p, N - p)))
@@ -65,18 +87,28 @@ def test_paired_ndft(api, N, batch, p0, nbins):
     nb = nbins or N
     ref = oracle.ndft(x.astype(np.complex128), p0=p0, nbins=nb)
     outs = {}
-    for key, atab in ((2, 0), (2, 1), (1, 0)):  # paired (A from the table / generated), unpaired
+    for combo in COMBOS:
         p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="ternary", prec="bf16x2")
         assert p.query(0) == slots(N, p0, nb)
-        p.set_tuning(6, key)
-        p.set_tuning(7, atab)
+        configure(p, *combo)
         got = p.ndft(dev(x)).cpu().numpy()
         p.query_error()
-        assert p.query(1) == (2 if key == 2 else 1)
-        assert relerr(got, ref) < TOL, (key, atab)
-        outs[(key, atab)] = got
-    assert np.max(np.abs(outs[(2, 0)] - outs[(1, 0)])) / np.max(np.abs(ref)) < 2 * TOL
-    assert np.max(np.abs(outs[(2, 0)] - outs[(2, 1)])) / np.max(np.abs(ref)) < 2 * TOL
+        assert p.query(1) == (2 if combo[0] == 2 else 1)
+        assert p.query(3) == TILE[combo]
+        assert relerr(got, ref) < TOL, combo
+        outs[combo] = got
+    for combo in COMBOS[1:]:
+        assert np.max(np.abs(outs[COMBOS[0]] - outs[combo])) / np.max(np.abs(ref)) < 2 * TOL, combo
+    # B formed in the tile: the same operand as the packing kernel's, so every
+    # bin but 0 (whose sum is grouped per split instead of per packing tile) is
+    # the same to the bit
+    same = np.ones(nb, bool)
+    k0 = bin0_index(N, p0, nb)
+    if k0 is not None:
+        same[k0] = False
+    a = np.ascontiguousarray(outs[(2, 0, 0, 0)][:, same])
+    b = np.ascontiguousarray(outs[(2, 0, 0, 2)][:, same])
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
 @pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
@@ -89,21 +121,33 @@ def test_paired_ndft(api, N, batch, p0, nbins):
 def test_paired_caf(api, N, lag0, nlags, p0, nbins, flags):
     sc = scenes.radar_scene(N=N, nlags=min(nlags, 64), nbins=min(nbins, 64), seed=61 + N % 97)
     ref = oracle.caf(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, flags=flags, z32=True)
-    for key, atab in ((2, 0), (2, 1), (1, 0)):  # paired (A from the table / generated), unpaired
+    outs = {}
+    for combo in COMBOS:
         p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="ternary", prec="bf16x2")
-        p.set_tuning(6, key)
-        p.set_tuning(7, atab)
+        configure(p, *combo)
         got = p.caf(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags).cpu().numpy()
         p.query_error()
-        assert p.query(1) == (2 if key == 2 else 1)
+        assert p.query(1) == (2 if combo[0] == 2 else 1)
+        assert p.query(3) == TILE[combo]
         if np.max(np.abs(ref)) == 0:
             assert np.max(np.abs(got)) == 0
         else:
-            assert relerr(got, ref) < TOL, (key, atab)
+            assert relerr(got, ref) < TOL, combo
+        outs[combo] = got
+    same = np.ones(nbins, bool)
+    k0 = bin0_index(N, p0, nbins)
+    if k0 is not None:
+        same[k0] = False
+    a = np.ascontiguousarray(outs[(2, 0, 0, 0)][:, same])
+    b = np.ascontiguousarray(outs[(2, 0, 0, 2)][:, same])
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
-@pytest.mark.parametrize("split,atab", [(0, 0), (1, 0), (3, 0), (19, 0), (0, 1), (19, 1)])
-def test_paired_caf_splits_sampled(api, split, atab):
+@pytest.mark.parametrize("split,atab,tile,bgen", [
+    (0, 0, 0, 0), (1, 0, 0, 0), (3, 0, 0, 0), (19, 0, 0, 0), (0, 1, 0, 0), (19, 1, 0, 0),
+    (0, 0, 256, 0), (3, 0, 256, 0), (19, 0, 256, 0), (7, 0, 258, 0),
+    (0, 0, 0, 2), (1, 0, 0, 2), (5, 0, 0, 2), (19, 0, 0, 2)])
+def test_paired_caf_splits_sampled(api, split, atab, tile, bgen):
     """The headline layout at N = 16384: 1024 lags x bins -512..511 (512 paired
     frequencies, bin 0 from the DC sums), every sample-axis split count giving
     the same cells within the bar; the default choice pairs."""
@@ -112,6 +156,8 @@ def test_paired_caf_splits_sampled(api, split, atab):
     assert p.query(0) == 512
     p.set_tuning(0, split)
     p.set_tuning(7, atab)  # 0: A tiles from the plan's table, 1: generated on chip
+    p.set_tuning(1, tile)  # 0 / 258: the 2-SM pair tile with the table, 256: one CTA
+    p.set_tuning(8, bgen)  # 2: B formed inside the pair tile
     A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 1024)
     idx, _ = api.argmax(A.reshape(1, -1))
     got = A.cpu().numpy()
@@ -136,7 +182,7 @@ def test_paired_deterministic_and_graph(api):
     ss, sr = dev(sc.s_surv), dev(sc.s_ref)
     a1 = p.caf(ss, sr, 0, 256).cpu().numpy()
     a2 = p.caf(ss, sr, 0, 256).cpu().numpy()
-    assert p.query(1) == 2
+    assert p.query(1) == 2 and p.query(3) == 258  # the 2-SM pair tile, a cluster launch
     assert np.array_equal(a1.view(np.uint32), a2.view(np.uint32))
     out = torch.empty((256, 512), dtype=torch.complex64, device="cuda")
     s = torch.cuda.Stream()
