@@ -650,6 +650,31 @@ def main():
     if per_step > 1:
         roofline["note"] = ("two column parts: the second part's packing runs on the SMs beside the first "
                             "part's contraction, whose event time includes that interference")
+    if plan.query(3) == 258 and plan.query(1) == 2 and not args.profile:
+        # the pair tile packs its own B operand (the lag products, 1.07 GB written)
+        # just ahead of its loads; for reference, the contraction alone with the
+        # operand packed by a separate kernel beforehand (tuning key 8 = 1),
+        # timed the same way right after the timed region
+        plan.set_tuning(8, 1)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        k2 = min(K, 100)
+        plan.timer_start(8 * k2)
+        for k in range(k2):
+            flush.fill_(k & 0xFF)
+            step()
+        torch.cuda.synchronize()
+        g2_ms, g2_n = plan.timer_read()
+        plan.set_tuning(8, 0)
+        c_s = g2_ms / max(g2_n, 1) / 1000.0
+        roofline["note"] = ("the timed kernel also packs its B operand (the lag products as bf16 hi/lo and "
+                            "signs, 1.07 GB written) just ahead of its own loads; contraction_alone is the same "
+                            "contraction with that operand packed by a separate kernel beforehand")
+        roofline["contraction_alone"] = {"kernel_ms_per_launch": c_s * 1000.0, "achieved": alg_flops / c_s / 1e12,
+                                         "frac_burst": alg_flops / c_s / 1e12 / bf16_peak,
+                                         "frac_sustained": alg_flops / c_s / 1e12 / sus if sus else None,
+                                         "steps": k2}
 
     if args.profile:
         if rank == 0:
@@ -700,9 +725,12 @@ def main():
         plan.caf_from_host_many([(hss, hsr)] * args.e2e_steps, 0, NLAGS, hA, staging, overlap=overlap)
         e2e_vals[overlap] = world * cells * args.e2e_steps / max_over_ranks(time.perf_counter() - t0, dist, dev)
         del staging
-    e2e = {"value": e2e_vals[True], "unit": "cells/s",
+    # both are the public call (caf_from_host_many's `overlap`); the faster is reported
+    best = max(e2e_vals, key=lambda o: e2e_vals[o])
+    e2e = {"value": e2e_vals[best], "unit": "cells/s",
            "h2d_bytes_per_step": hss.numel() * 8 + hsr.numel() * 8, "d2h_bytes_per_step": hA.numel() * 8,
-           "compute_streams": 2, "one_compute_stream_value": e2e_vals[False]}
+           "compute_streams": 2 if best else 1, "one_compute_stream_value": e2e_vals[False],
+           "two_compute_streams_value": e2e_vals[True]}
 
     # error against the fp64 oracle on sampled cells (outside every timed region)
     err = None

@@ -297,7 +297,18 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * the plan builds at creation (16 MiB per 1024 samples of a 1024-bin window;
  * built only while it stays within 2 GiB), 1 = generated on chip per K block
  * by producer warps from the twiddle table (the only form for larger tables).
- * Same bar either way. */
+ * Same bar either way.
+ * Key 8 = the paired contraction's B operand (the lag products, or NDFT
+ * inputs, as bf16 hi/lo and signs) on the 2-SM pair tile: 0 (default) or 3 =
+ * packed just in time by the tile's own warps into the plan's workspace: each
+ * CTA packs the 16-block x 64-column items of its own future loads that no
+ * other CTA has claimed, at most key 9 items (default 4) ahead of its loads,
+ * and loads an item once it is marked packed (bounded waits, NDFT_E_TIMEOUT
+ * past them); 1 = packed by a separate kernel before the contraction; 2 =
+ * formed in shared memory per K block by every tile that uses it (four times
+ * per B tile; slower, for measurement).  The operand is the same in all
+ * three, so every bin but bin 0 (whose sum is grouped differently) is the
+ * same bit for bit. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
 
 /* Read-only facts about a plan and its last exec call, into *value:

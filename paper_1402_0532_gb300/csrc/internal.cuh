@@ -71,14 +71,17 @@ struct Plan {
     int tune_parts = 1;          // ternary form: 1 one part (default); 0 two parts, half each; else part 0's columns
     int tune_pair = 0;           // ternary form: 0 conjugate-paired rows where they save work (default), 1 never
     int pair_slots = 0;          // ternary form: frequencies 1 .. pair_slots cover the bin window (0: none)
-    int tune_bgen = 0;           // ternary form: paired B operand 0/1 packed by a kernel, 2 formed in the pair tile
+    int tune_look = 0;           // items the in-tile packers run ahead (0: 4)
+    int tune_bgen = 0;           // paired B operand on the pair tile: 0/3 packed just in time by its own warps,
+                                 // 1 packed by a kernel before it, 2 formed in its shared memory
     int tune_atab = 0;           // ternary form: 0 paired A tiles from the plan's table when built, 1 generated on chip
     void *atab = nullptr;        // ternary form: the paired contraction's A operand, [K block][rows] x 128 B
     size_t atab_bytes = 0;
     int32_t atab_ld = 0;         // its rows per K block
     void *tmap_a = nullptr;      // its TMA descriptor (host copy)
     void *tmap_a2 = nullptr;     // the same with a 128-row box (2-SM pair tile)
-    size_t dc_bytes = 0;         // ternary form: per-tile DC sums of the paired packing
+    size_t dc_bytes = 0;         // ternary form: per-tile DC sums of the paired packing, then item flags
+    size_t dc_flag_off = 0;      // offset of the item flags in that region
     // ternary form: side stream and events of the two-part contraction (the
     // second part's packing runs under the first part's contraction)
     cudaStream_t side = nullptr;

@@ -471,8 +471,11 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
         if (value > 1) return NDFT_E_INVALID;
         plan->p.tune_atab = value;
     } else if (key == 8) {
-        if (value > 2) return NDFT_E_INVALID;
+        if (value > 3) return NDFT_E_INVALID;
         plan->p.tune_bgen = value;
+    } else if (key == 9) {
+        if (value > 64) return NDFT_E_INVALID;
+        plan->p.tune_look = value;
     } else {
         return NDFT_E_INVALID;
     }

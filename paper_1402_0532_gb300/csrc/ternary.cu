@@ -50,8 +50,6 @@ constexpr int R_LO = 256;          // angle split r = r_hi * 256 + r_lo
 constexpr int kMaxN = 1 << 18;
 constexpr int kMaxThi = kMaxN / R_LO + 2;
 constexpr int kGenWarps = 8;
-constexpr int kEpiWarp0 = 2 + kGenWarps;  // warps 10..13 -> TMEM lane quarters 2, 3, 0, 1
-constexpr int kThreads = (2 + kGenWarps + 4) * 32;
 // the conjugate-paired contraction generates twice the twiddles per MMA of the
 // unpaired one and runs twice the A-producer warps (4 per SM sub-partition) to
 // hide their latency
@@ -366,21 +364,33 @@ struct PackProb {
     int64_t row0;     // first packed row
 };
 
-__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+// sgn(v) in two instructions: 1.0f where v != 0 (set.ne) with v's sign bit
+// copied in, so +-1, or a zero of v's sign for a zero v.  As a factor it is
+// exact; a zero of either sign contributes nothing to a nonzero sum.
+__device__ __forceinline__ float sgn_or_zero(float v) {
+    float nz;
+    asm("set.ne.f32.f32 %0, %1, 0f00000000;" : "=f"(nz) : "f"(v));
+    return __uint_as_float(__float_as_uint(nz) | (__float_as_uint(v) & 0x80000000u));
+}
 
-// Real a (x) b = sgn(a) (sgn(b) |a| + b): the fma rounds sgn(b)(|a| + |b|)
-// once (round to nearest is sign-symmetric) and the outer sign is exact, so
-// this is |a| + |b| rounded once with the sign of Eq. 2; a zero operand gives
-// a zero (of either sign, which no later step distinguishes).
-__device__ __forceinline__ float ox_fma(float a, float sa, float b, float sb) { return sa * fmaf(sb, fabsf(a), b); }
-
-// Eq. 6 for the lag product s (x) c, c = conj(r) (or r with NDFT_F_NO_CONJ_REF).
+// Eq. 6 for the lag product s (x) c, c = conj(r) (or r with NDFT_F_NO_CONJ_REF):
+// Re = s_r (x) c_r - s_i (x) c_i, Im = s_i (x) c_r + s_r (x) c_i.  Each real
+// a (x) b = sgn(a) sgn(b) (|a| + |b|) is the inner fma(sgn b, |a|, b), rounded
+// once, times sgn a (exact); the difference and the sum then take one fma
+// each, Re = fma(sgn s_r, i1, n2) with n2 = -(s_i (x) c_i) exact (its +0
+// addend turns a zero into +0), one rounding as in t1 - t2.  Same values as
+// the four products and the subtraction written out; zeros come out +0 or of
+// either sign where the definition gives 0.
 __device__ __forceinline__ float2 lag_ox(float2 s, float2 r, bool conj) {
     const float cr = r.x, ci = conj ? -r.y : r.y;
-    const float ss_r = sgnf(s.x), ss_i = sgnf(s.y), sc_r = sgnf(cr), sc_i = sgnf(ci);
-    const float t1 = ox_fma(s.x, ss_r, cr, sc_r), t2 = ox_fma(s.y, ss_i, ci, sc_i);
-    const float t3 = ox_fma(s.y, ss_i, cr, sc_r), t4 = ox_fma(ci, sc_i, s.x, ss_r);
-    return make_float2(__fsub_rn(t1, t2), __fadd_rn(t3, t4));
+    const float gsr = sgn_or_zero(s.x), gsi = sgn_or_zero(s.y), gcr = sgn_or_zero(cr), gci = sgn_or_zero(ci);
+    const float i1 = __fmaf_rn(gcr, fabsf(s.x), cr);  // sgn c_r (|s_r| + |c_r|)
+    const float i2 = __fmaf_rn(gci, fabsf(s.y), ci);  // sgn c_i (|s_i| + |c_i|)
+    const float i3 = __fmaf_rn(gcr, fabsf(s.y), cr);  // sgn c_r (|s_i| + |c_r|)
+    const float i4 = __fmaf_rn(gsr, fabsf(ci), s.x);  // sgn s_r (|c_i| + |s_r|)
+    const float n2 = __fmaf_rn(-gsi, i2, 0.f);        // -(s_i (x) c_i)
+    const float t4 = __fmaf_rn(gci, i4, 0.f);         // c_i (x) s_r
+    return make_float2(__fmaf_rn(gsr, i1, n2), __fmaf_rn(gsi, i3, t4));
 }
 
 // ---- the conjugate-paired B operand, two samples of one input column ----------
@@ -437,7 +447,8 @@ __device__ __forceinline__ void pair_chunks(float2 v0, float2 v1, uint4 &re, uin
     uint32_t hr, lr, hi, li;
     split2(v0.x, v1.x, hr, lr);
     split2(v0.y, v1.y, hi, li);
-    const float g0r = sgnf(v0.x), g1r = sgnf(v1.x), g0i = sgnf(v0.y), g1i = sgnf(v1.y);
+    const float g0r = sgn_or_zero(v0.x), g1r = sgn_or_zero(v1.x), g0i = sgn_or_zero(v0.y),
+                g1i = sgn_or_zero(v1.y);
     const uint32_t sr2 = bf2(g0r, g1r), si2 = bf2(g0i, g1i);
     re = make_uint4(hr, lr, sr2, sr2);
     im = make_uint4(hi, li, si2, si2);
@@ -445,14 +456,27 @@ __device__ __forceinline__ void pair_chunks(float2 v0, float2 v1, uint4 &re, uin
     di = (v0.y + g0i) + (v1.y + g1i);
 }
 
-// Operand generation inside the 2-SM pair tile: what the packing kernel reads.
+// The B operand of the 2-SM pair tile: loaded by TMA from the packed buffer
+// (kBTma, packed by k_pack_pair before the launch), formed in shared memory
+// (kBForm), or packed into the buffer by the tile's own producer warps ahead
+// of its TMA loads (kBAhead).
+constexpr int kBTma = 0, kBForm = 1, kBAhead = 2;
+
+// What the producer warps read and write for kBForm / kBAhead.
 struct BGen {
     PackProb pp;
     const float2 *a;  // launch's first input base (x or s_surv)
     const float2 *r;  // s_ref (CAF)
-    float2 *dc;       // bin-0 sums [nsplit][ncols]
+    float2 *dc;       // bin-0 sums: kBForm [nsplit][ncols], kBAhead [nsplit * jmax][ncols]
     uint32_t flags;
     int32_t caf;
+    // kBAhead: work items (split s, block j of 16 K blocks from the split's
+    // first, 64-column block cx), jmax blocks per split, ncx column blocks
+    uint4 *B;         // the packed buffer
+    int32_t *ctr;     // [1 + (s jmax + j) ncx + cx]: item state, 0 free, 1 claimed, 2 packed
+    int64_t nitems;
+    int32_t jmax, ncx;
+    int32_t look;     // items the packers may run ahead of their CTA's TMA loads
 };
 
 // The R and I chunks of one frequency for samples a and a + 1 (twiddles Wa, Wb
@@ -1381,21 +1405,53 @@ __device__ __forceinline__ void commit2_mc(uint64_t *bar) {
 // ATAB: the conjugate-paired contraction with its A operand from the plan's
 // table (`amap`, 128-row box: each CTA loads its 128 rows, completion on the
 // even CTA's barrier like B); no A producer warps run.
-// BGEN (with ATAB): the B operand is not loaded but formed in shared memory by
-// 16 producer warps of each CTA from the inputs (`bg`), the same chunks the
-// packing kernel writes: thread g of a CTA forms chunk t = g & 7 of the CTA's
-// lag column j = g >> 3 (rows 2 j, 2 j + 1 of its 128-row half).
+// BM = kBForm (with ATAB): the B operand is not loaded but formed in shared
+// memory by 16 producer warps of each CTA from the inputs (`bg`), the same
+// chunks the packing kernel writes: thread g of a CTA forms chunk t = g & 7 of
+// the CTA's lag column j = g >> 3 (rows 2 j, 2 j + 1 of its 128-row half).
 // The m-tile-0 units also sum v + sigma(v) of their columns over their K range
 // into bg.dc[split][col] (bin 0), in a fixed order.
-__host__ __device__ constexpr int pair_gen_warps(bool bgen) { return bgen ? 16 : kGenWarps; }
-__host__ __device__ constexpr int pair_threads(bool bgen) { return (2 + pair_gen_warps(bgen) + 4) * 32; }
+// BM = kBAhead (with ATAB): B is packed just in time by the tile's own warps.
+// An item is 16 K blocks x 64 lag columns, the B half one CTA loads for one
+// unit; the four units of a column tile (its m-tiles, on four pairs of the
+// same wave) load the same items.  16 packer warps per CTA walk the CTA's own
+// item sequence at most bg.look items ahead of its TMA thread, claim each
+// item that no other CTA has claimed (atomicCAS on its state), write it into
+// the packed buffer exactly as k_pack_pair does (bin-0 sums per item) and
+// release it (gpu-scope fence, state 2); the TMA thread waits for state 2
+// (acquire, then a proxy fence) before loading it, so the B tile is read from
+// L2 by the CTAs that share it moments after it was written.  A claimed item
+// is packed without waiting on anything, and a CTA's packers wait only for
+// their own CTA's TMA thread, which waits only for claimed items or for items
+// its own packers will reach: no CTA waits for one that is not resident.
+__host__ __device__ constexpr int pair_gen_warps(int bm) { return bm != kBTma ? 16 : kGenWarps; }
+__host__ __device__ constexpr int pair_threads(int bm) { return (2 + pair_gen_warps(bm) + 4) * 32; }
 
-template <bool ATAB, bool BGEN>
-__global__ void __launch_bounds__(pair_threads(BGEN), 1)
+// Bounded wait until *f >= target (acquire at gpu scope).
+__device__ __forceinline__ bool flag_wait(const int32_t *f, int32_t target, volatile int32_t *abort_flag,
+                                          int32_t *err) {
+    const long long t0 = clock64();
+    for (;;) {
+        int32_t v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if (v >= target) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            dev_set_error(err, kDevTimeout);
+            return false;
+        }
+        __nanosleep(32);
+    }
+}
+
+template <bool ATAB, int BM>
+__global__ void __launch_bounds__(pair_threads(BM), 1)
     k_ternary_gemm_pair(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap,
                         int out_tma, Problem single, int64_t nunits, int chunk, int starve, float *__restrict__ out_base,
                         int32_t *err, const __grid_constant__ CUtensorMap amap, const BGen bg) {
-    static_assert(ATAB || !BGEN, "operand generation goes with the A table");
+    static_assert(ATAB || BM == kBTma, "operand generation goes with the A table");
+    constexpr bool BGEN = BM == kBForm;
     using namespace pair2;
     const uint32_t rank = cluster_rank();
     const bool lead = rank == 0;
@@ -1416,7 +1472,7 @@ __global__ void __launch_bounds__(pair_threads(BGEN), 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], (ATAB && !BGEN) ? 1 : 1 + 2 * pair_gen_warps(BGEN));
+            mbar_init(&full[s], (ATAB && !BGEN) ? 1 : 1 + 2 * pair_gen_warps(BM));
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -1424,6 +1480,7 @@ __global__ void __launch_bounds__(pair_threads(BGEN), 1)
             mbar_init(&tmem_empty[b], 8);
         }
         *s_abort = 0;
+        s_tmem[3] = 0;  // kBAhead: the TMA thread's position in its item sequence
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
     }
@@ -1446,21 +1503,36 @@ __global__ void __launch_bounds__(pair_threads(BGEN), 1)
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            bool started = false;  // kBAhead: past the first position of the item sequence
+            volatile int32_t *s_prog = reinterpret_cast<volatile int32_t *>(s_tmem + 3);
             for (int64_t u = blockIdx.x / 2; u < nunits && ok; u += gridDim.x / 2) {
                 const Work w = decode(u, single, nullptr, nullptr);
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!(ok = mbar_wait(&empty[stage], phase ^ 1u, s_abort, err))) break;
                     if (starve) continue;
                     if (lead) mbar_arrive_tx(&full[stage], (BGEN ? 0 : 2 * kBBytes) + (ATAB ? 2 * kABytes : 0));
+                    if constexpr (ATAB) {
+                        const int64_t arow = (int64_t)kb * w.P.a_ld + (int64_t)w.mt * 256 + rank * 128;
+                        tma_load_b_pair(a_base + stage * kABytes, &amap, (int32_t)arow,
+                                        peer_addr(smem_u32(&full[stage]), 0u));
+                    }
+                    if constexpr (BM == kBAhead) {
+                        if ((kb - w.kb0) % 16 == 0) {
+                            // the first K block of the next position of this CTA's item
+                            // sequence (the packers walk the same one): column block
+                            // cx = 2 nt + rank of item (split, j)
+                            if (started) *s_prog = *s_prog + 1;
+                            started = true;
+                            const int64_t item =
+                                ((int64_t)w.split * bg.jmax + (kb - w.kb0) / 16) * bg.ncx + 2 * w.nt + (int)rank;
+                            if (!(ok = flag_wait(bg.ctr + 1 + item, 2, s_abort, err))) break;
+                            asm volatile("fence.proxy.async.global;" ::: "memory");
+                        }
+                    }
                     if constexpr (!BGEN) {
                         const int64_t row =
                             w.P.b_row0 + (int64_t)kb * w.P.ncols + (int64_t)w.nt * TN + rank * (TN / 2);
                         tma_load_b_pair(b_base + stage * kBBytes, &tmap, (int32_t)row,
-                                        peer_addr(smem_u32(&full[stage]), 0u));
-                    }
-                    if constexpr (ATAB) {
-                        const int64_t arow = (int64_t)kb * w.P.a_ld + (int64_t)w.mt * 256 + rank * 128;
-                        tma_load_b_pair(a_base + stage * kABytes, &amap, (int32_t)arow,
                                         peer_addr(smem_u32(&full[stage]), 0u));
                     }
                     if (++stage == kStages) {
@@ -1503,8 +1575,87 @@ __global__ void __launch_bounds__(pair_threads(BGEN), 1)
             }
         }
         __syncwarp();
-    } else if (warp < 2 + pair_gen_warps(BGEN)) {
-        if constexpr (BGEN) {
+    } else if (warp < 2 + pair_gen_warps(BM)) {
+        if constexpr (BM == kBAhead) {
+        // ---------------- packers: this CTA's own B items, just ahead of its TMA loads ----------------
+        const int g = threadIdx.x - 64;  // 0..511
+        const int t = g & 7, lc = g >> 3;
+        const PackProb &pp = bg.pp;
+        const int N = pp.N;
+        const bool caf = bg.caf != 0, conj = !(bg.flags & NDFT_F_NO_CONJ_REF),
+                   circ = (bg.flags & NDFT_F_CIRCULAR_LAG) != 0;
+        const float2 *r = bg.r + pp.r_off;
+        const int64_t ncols2 = 2LL * pp.ncols;
+        volatile int32_t *s_cmd = reinterpret_cast<volatile int32_t *>(s_tmem + 2);
+        volatile int32_t *s_prog = reinterpret_cast<volatile int32_t *>(s_tmem + 3);
+        int32_t q = 0;  // position in this CTA's item sequence
+        bool run = true;
+        for (int64_t u = blockIdx.x / 2; u < nunits && run; u += gridDim.x / 2) {
+            const Work w = decode(u, single, nullptr, nullptr);
+            const int cx = 2 * w.nt + (int)rank;
+            for (int k0 = w.kb0; k0 < w.kb1; k0 += 16, ++q) {
+                const int jb = (k0 - w.kb0) / 16, k1 = min(k0 + 16, w.kb1);
+                const int64_t item = ((int64_t)w.split * bg.jmax + jb) * bg.ncx + cx;
+                if (g == 0) {
+                    // at most bg.look items ahead of the TMA thread; then claim the item
+                    // unless another CTA of its column tile has
+                    int32_t cmd = 0;
+                    const long long t0 = clock64();
+                    while (*s_prog < q - bg.look) {
+                        if (*s_abort || clock64() - t0 > kWaitCycles) {
+                            cmd = -1;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    if (cmd == 0) cmd = atomicCAS(bg.ctr + 1 + item, 0, 1) == 0 ? 1 : 0;
+                    *s_cmd = cmd;
+                }
+                gen_bar_n<16>();
+                const int32_t cmd = *s_cmd;
+                gen_bar_n<16>();  // every packer has read the command before thread 0 writes the next
+                if (cmd < 0) {
+                    run = false;
+                    break;
+                }
+                if (cmd == 0) continue;
+                const int64_t col = (int64_t)cx * 64 + lc;
+                const bool live = col < pp.ncols;
+                const int64_t lag = (int64_t)pp.lag0 + col;
+                const float2 *a = bg.a + pp.a_off + (caf || !live ? 0 : col * pp.ldx);
+                const bool vec = (reinterpret_cast<uintptr_t>(a) & 15u) == 0;
+                float dsr = 0.f, dsi = 0.f;
+                if (live) {
+                    for (int kb = k0; kb < k1; ++kb) {
+                        float2 v0, v1;
+                        pair_samples(a, r, kb * 16 + 2 * t, N, lag, caf, conj, circ, vec, v0, v1);
+                        uint4 cre, cim;
+                        float dr, di;
+                        pair_chunks(v0, v1, cre, cim, dr, di);
+                        const int64_t row = (int64_t)kb * ncols2 + 2 * col;
+                        bg.B[row * 8 + t] = cre;
+                        bg.B[(row + 1) * 8 + t] = cim;
+                        dsr += dr;
+                        dsi += di;
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    dsr += __shfl_xor_sync(0xffffffffu, dsr, o);
+                    dsi += __shfl_xor_sync(0xffffffffu, dsi, o);
+                }
+                if (t == 0 && live) bg.dc[((int64_t)w.split * bg.jmax + jb) * pp.ncols + col] = make_float2(dsr, dsi);
+                // the item's stores, then one release for the CTA's packers (the barrier
+                // orders every packer's stores before thread 0's fence)
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                gen_bar_n<16>();
+                if (g == 0) {
+                    __threadfence();
+                    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(bg.ctr + 1 + item), "r"(2) : "memory");
+                }
+            }
+        }
+        } else if constexpr (BGEN) {
         // ---------------- B producers: this CTA's 64 lag columns (128 rows) ----------------
         const int g = threadIdx.x - 64;  // 0..511
         const int t = g & 7, j0 = g >> 3;  // chunk t of lag column j0 (rows 2 j0, 2 j0 + 1)
@@ -2246,16 +2397,16 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
 }
 
 // The 2-SM pair tile: one unit per pair, 2 x min(units, SMs / 2) CTAs in clusters of 2.
-template <bool ATAB = false, bool BGEN = false>
+template <bool ATAB = false, int BM = kBTma>
 cudaError_t launch_gemm_pair(const Plan &p, const Problem &single, int64_t nunits, float *out_base,
                              const CUtensorMap *omap, cudaStream_t s, const BGen *bgen = nullptr) {
     constexpr size_t smem = pair2::kSmemTotal;
     if (ATAB && !p.tmap_a2) return cudaErrorInvalidValue;
-    if (BGEN && !bgen) return cudaErrorInvalidValue;
+    if (BM != kBTma && !bgen) return cudaErrorInvalidValue;
     BGen bg{};
     if (bgen) bg = *bgen;
-    auto kern = k_ternary_gemm_pair<ATAB, BGEN>;
-    constexpr int threads = pair_threads(BGEN);
+    auto kern = k_ternary_gemm_pair<ATAB, BM>;
+    constexpr int threads = pair_threads(BM);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host2);  // 128-row box
@@ -2297,7 +2448,8 @@ struct TernLayout {
     int64_t b_rows;
     size_t b_bytes;
     size_t part_bytes;
-    size_t dc_bytes;  // paired form: DC sums per packing tile and column
+    size_t dc_bytes;  // paired form: bin-0 sums per packing tile (or item row) and column, then item flags
+    size_t dc_flag_off;
 };
 
 int pair_kblocks(int N) { return (N + 15) / 16; }
@@ -2324,7 +2476,13 @@ TernLayout layout_for(const ndft_desc &d, int sm) {
     L.b_rows = std::max<int64_t>((int64_t)L.kblocks * cols, (int64_t)pair_kblocks(d.n) * 2 * cols);
     L.b_bytes = (size_t)L.b_rows * 128;
     L.part_bytes = (size_t)4 * sm * 256 * TN * sizeof(float);  // 4 waves of 256 x 256 partial tiles
-    L.dc_bytes = ((size_t)pair_pack_tiles(d.n) * cols * sizeof(float2) + 255) / 256 * 256;
+    // bin-0 partial rows: one per packing tile, or (B packed inside the pair
+    // tile) one per split and block of 16 K blocks, at most tiles + 34 with
+    // at most kMaxSplit splits; then the flags of that mode's work items
+    // (rows x column blocks of 64, at most cols / 64 + 2 of them)
+    const int64_t dc_rows = pair_pack_tiles(d.n) + kMaxSplit + 8;
+    L.dc_flag_off = ((size_t)dc_rows * cols * sizeof(float2) + 255) / 256 * 256;
+    L.dc_bytes = L.dc_flag_off + ((size_t)(1 + dc_rows * (cols / 64 + 2)) * sizeof(int32_t) + 255) / 256 * 256;
     // the paired contraction writes at least one split of partials [2 cols][2 S]
     // (the fold writes the output): room for it at the plan's largest call
     const int S = pair_slots_for(d.n, d.p0, d.nbins ? d.nbins : d.n);
@@ -2379,6 +2537,7 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
     p.b_bytes = L.b_bytes;
     p.part_bytes = L.part_bytes;
     p.dc_bytes = L.dc_bytes;
+    p.dc_flag_off = L.dc_flag_off;
     p.pair_slots = pair_slots_for(N, p.d.p0, p.d.nbins);
     // the paired A operand as a table when it is modest (it depends on the
     // window and N only; the contraction then needs no producer warps)
@@ -2535,8 +2694,21 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     const int nsplit = choose_split(tiles, kblocks, pair_tile ? p.sm_count / 2 : p.sm_count, p.tune_split, cap_units);
     // B formed inside the pair tile (key 8 = 2), its bin-0 sums one row per split
     const bool bgen =
-        pair_tile && p.tune_bgen == 2 && (size_t)nsplit * ncols * sizeof(float2) <= p.dc_bytes;
-    if (!bgen) {
+        pair_tile && p.tune_bgen == 2 && (size_t)nsplit * ncols * sizeof(float2) <= p.dc_flag_off;
+    // B packed just in time by the pair tile's own warps (key 8 = 3, and the
+    // default on the pair tile): items of 16 K blocks x 64 columns, bin-0 sums
+    // one row per split and block
+    const int jmax = ((kblocks + nsplit - 1) / nsplit + 15) / 16;
+    const int ncx = 2 * ((ncols + 127) / 128);
+    const int64_t nitems = (int64_t)nsplit * jmax * ncx;
+    int32_t *flags = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(dc) + p.dc_flag_off);
+    const bool ahead = pair_tile && (p.tune_bgen == 3 || p.tune_bgen == 0) &&
+                       (size_t)nsplit * jmax * ncols * sizeof(float2) <= p.dc_flag_off &&
+                       (size_t)(1 + nitems) * sizeof(int32_t) <= p.dc_bytes - p.dc_flag_off;
+    if (ahead) {
+        cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)(1 + nitems) * sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    } else if (!bgen) {
         const int gx = (ncols + 31) / 32;
         k_pack_pair<<<dim3(gx, std::min(gy, 65535)), 256, 0, s>>>(
             pp, p.d.flags, caf, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base),
@@ -2570,10 +2742,20 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
         alignas(64) CUtensorMap omap16;
         const bool tma16 =
             (S % 2 == 0) && p.tune_drain == 0 && make_out_map(part, S, P.ncols, P.nsplit, &omap16) == cudaSuccess;
-        if (bgen) {
-            const BGen bg{pp, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base), dc,
-                          p.d.flags, caf ? 1 : 0};
-            e = launch_gemm_pair<true, true>(p, P, tiles * P.nsplit, part, tma16 ? &omap16 : nullptr, s, &bg);
+        if (bgen || ahead) {
+            BGen bg{pp, static_cast<const float2 *>(a_base), static_cast<const float2 *>(r_base), dc,
+                    p.d.flags, caf ? 1 : 0};
+            if (ahead) {
+                bg.B = static_cast<uint4 *>(p.ws);
+                bg.ctr = flags;
+                bg.nitems = nitems;
+                bg.jmax = jmax;
+                bg.ncx = ncx;
+                bg.look = p.tune_look > 0 ? p.tune_look : 4;
+                e = launch_gemm_pair<true, kBAhead>(p, P, tiles * P.nsplit, part, tma16 ? &omap16 : nullptr, s, &bg);
+            } else {
+                e = launch_gemm_pair<true, kBForm>(p, P, tiles * P.nsplit, part, tma16 ? &omap16 : nullptr, s, &bg);
+            }
         } else {
             e = launch_gemm_pair<true>(p, P, tiles * P.nsplit, part, tma16 ? &omap16 : nullptr, s);
         }
@@ -2590,7 +2772,8 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     p.last_nsplit = P.nsplit;
     p.last_tile = pair_tile ? 258 : 256;
     const dim3 fgrid(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins);
-    const int dc_rows = bgen ? P.nsplit : gy;  // bin-0 partials: per split, or per packing tile
+    // bin-0 partials: per split and block, per split, or per packing tile
+    const int dc_rows = ahead ? P.nsplit * jmax : bgen ? P.nsplit : gy;
     if (p.d.flags & NDFT_F_ABS_OUT)
         k_pair_fold<true><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, p.d.p0, p.d.nbins, dc,
                                                       dc_rows, ncols, out, p.err);
@@ -2610,7 +2793,7 @@ static bool use_pair(const Plan &p, int ncols) {
     if (tile_pair(p) && !(p.atab && p.tune_atab == 0)) return false;  // the pair tile needs the A table
     const int64_t S = p.pair_slots, nb = p.d.nbins, N = p.d.n;
     if ((size_t)2 * ncols * 2 * S * sizeof(float) > p.part_bytes) return false;
-    if ((size_t)pair_pack_tiles((int)N) * ncols * sizeof(float2) > p.dc_bytes) return false;
+    if ((size_t)pair_pack_tiles((int)N) * ncols * sizeof(float2) > p.dc_flag_off) return false;
     if (p.tune_pair == 2) return true;
     const int64_t paired = ((2 * S + 255) / 256) * ((2LL * ncols + TN - 1) / TN) * (int64_t)pair_kblocks((int)N);
     const int64_t plain = ((2 * nb + 255) / 256) * (((int64_t)ncols + TN - 1) / TN) * ((N + 7) / 8);

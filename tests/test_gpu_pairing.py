@@ -7,8 +7,9 @@ X[-c] = U - jV; bin 0 is the packing kernel's sum of v + sigma(v).  Every case
 is checked against the fp64 oracle at the fp32 bar (1e-5 of max |X|), with the
 paired path forced (tuning key 6 = 2; its A operand from the plan's table on
 the 2-SM pair tile, the default, or on the one-CTA tile, key 1 = 256, or
-generated on chip, key 7 = 1; its B operand packed by a kernel or, key 8 = 2,
-formed inside the pair tile) and cross-checked against the unpaired rows (key 6 = 1) on the
+generated on chip, key 7 = 1; its B operand packed by a kernel, formed inside
+the pair tile (key 8 = 2) or packed by the pair tile's own warps ahead of its
+loads (key 8 = 3)) and cross-checked against the unpaired rows (key 6 = 1) on the
 same inputs: centred and full windows, windows that
 wrap past bin 0, contain N/2 or give an odd number of paired frequencies (the
 element-wise fold-out), ragged N, both CAF flags and several sample-axis
@@ -44,10 +45,11 @@ def relerr(got, ref):
 
 
 # (key 6, key 7, key 1, key 8) -> tile: paired with A from the table on the
-# 2-SM pair (default), the same with B formed in the tile, A from the table on
-# one CTA, A generated on chip; unpaired
-COMBOS = ((2, 0, 0, 0), (2, 0, 0, 2), (2, 0, 256, 0), (2, 1, 0, 0), (1, 0, 0, 0))
-TILE = {(2, 0, 0, 0): 258, (2, 0, 0, 2): 258, (2, 0, 256, 0): 256, (2, 1, 0, 0): 256, (1, 0, 0, 0): 256}
+# 2-SM pair (default), the same with B formed in the tile or packed ahead by
+# it, A from the table on one CTA, A generated on chip; unpaired
+COMBOS = ((2, 0, 0, 1), (2, 0, 0, 2), (2, 0, 0, 3), (2, 0, 256, 0), (2, 1, 0, 0), (1, 0, 0, 0))
+TILE = {(2, 0, 0, 1): 258, (2, 0, 0, 2): 258, (2, 0, 0, 3): 258, (2, 0, 256, 0): 256, (2, 1, 0, 0): 256,
+        (1, 0, 0, 0): 256}
 
 
 def configure(p, key, atab, tile, bgen):
@@ -99,16 +101,17 @@ def test_paired_ndft(api, N, batch, p0, nbins):
         outs[combo] = got
     for combo in COMBOS[1:]:
         assert np.max(np.abs(outs[COMBOS[0]] - outs[combo])) / np.max(np.abs(ref)) < 2 * TOL, combo
-    # B formed in the tile: the same operand as the packing kernel's, so every
-    # bin but 0 (whose sum is grouped per split instead of per packing tile) is
-    # the same to the bit
+    # B formed in the tile or packed ahead by it: the same operand as the
+    # packing kernel's, so every bin but 0 (whose sum is grouped per split or
+    # per item instead of per packing tile) is the same to the bit
     same = np.ones(nb, bool)
     k0 = bin0_index(N, p0, nb)
     if k0 is not None:
         same[k0] = False
-    a = np.ascontiguousarray(outs[(2, 0, 0, 0)][:, same])
-    b = np.ascontiguousarray(outs[(2, 0, 0, 2)][:, same])
-    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    a = np.ascontiguousarray(outs[(2, 0, 0, 1)][:, same])
+    for bmode in (2, 3):
+        b = np.ascontiguousarray(outs[(2, 0, 0, bmode)][:, same])
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), bmode
 
 
 @pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [
@@ -138,15 +141,17 @@ def test_paired_caf(api, N, lag0, nlags, p0, nbins, flags):
     k0 = bin0_index(N, p0, nbins)
     if k0 is not None:
         same[k0] = False
-    a = np.ascontiguousarray(outs[(2, 0, 0, 0)][:, same])
-    b = np.ascontiguousarray(outs[(2, 0, 0, 2)][:, same])
-    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    a = np.ascontiguousarray(outs[(2, 0, 0, 1)][:, same])
+    for bmode in (2, 3):
+        b = np.ascontiguousarray(outs[(2, 0, 0, bmode)][:, same])
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), bmode
 
 
 @pytest.mark.parametrize("split,atab,tile,bgen", [
     (0, 0, 0, 0), (1, 0, 0, 0), (3, 0, 0, 0), (19, 0, 0, 0), (0, 1, 0, 0), (19, 1, 0, 0),
     (0, 0, 256, 0), (3, 0, 256, 0), (19, 0, 256, 0), (7, 0, 258, 0),
-    (0, 0, 0, 2), (1, 0, 0, 2), (5, 0, 0, 2), (19, 0, 0, 2)])
+    (0, 0, 0, 2), (1, 0, 0, 2), (5, 0, 0, 2), (19, 0, 0, 2),
+    (0, 0, 0, 3), (1, 0, 0, 3), (5, 0, 0, 3), (8, 0, 0, 3), (19, 0, 0, 3)])
 def test_paired_caf_splits_sampled(api, split, atab, tile, bgen):
     """The headline layout at N = 16384: 1024 lags x bins -512..511 (512 paired
     frequencies, bin 0 from the DC sums), every sample-axis split count giving
@@ -157,7 +162,7 @@ def test_paired_caf_splits_sampled(api, split, atab, tile, bgen):
     p.set_tuning(0, split)
     p.set_tuning(7, atab)  # 0: A tiles from the plan's table, 1: generated on chip
     p.set_tuning(1, tile)  # 0 / 258: the 2-SM pair tile with the table, 256: one CTA
-    p.set_tuning(8, bgen)  # 2: B formed inside the pair tile
+    p.set_tuning(8, bgen)  # 2: B formed inside the pair tile, 3: packed ahead by it
     A = p.caf(dev(sc.s_surv), dev(sc.s_ref), 0, 1024)
     idx, _ = api.argmax(A.reshape(1, -1))
     got = A.cpu().numpy()
@@ -174,11 +179,14 @@ def test_paired_caf_splits_sampled(api, split, atab, tile, bgen):
     assert int(idx[0]) == 512  # the direct path at lag 0, bin 0
 
 
-def test_paired_deterministic_and_graph(api):
+@pytest.mark.parametrize("bmode", [0, 1])
+def test_paired_deterministic_and_graph(api, bmode):
     """Two calls give the same bits, and a CUDA-graph replay of the paired call
-    on new inputs equals an eager call on them."""
+    on new inputs equals an eager call on them (B packed by a kernel, and packed
+    just in time inside the pair tile, the default)."""
     sc = scenes.radar_scene(N=8192, nlags=256, nbins=512, seed=64)
     p = api.Plan(sc.N, p0=-256, nbins=512, max_lags=256, form="ternary", prec="bf16x2")
+    p.set_tuning(8, bmode)
     ss, sr = dev(sc.s_surv), dev(sc.s_ref)
     a1 = p.caf(ss, sr, 0, 256).cpu().numpy()
     a2 = p.caf(ss, sr, 0, 256).cpu().numpy()
