@@ -174,6 +174,23 @@ struct OpNL {
     __device__ static float2 mul(float4 w, float2 o) { return cox_ready(w, o); }
 };
 
+// cox_ready for the two axis twiddles, same bits in 8 instructions instead of
+// 12.  W = 1, ready form (1, 0, 1, 0): i1 = sgn Or + Or, i3 = 0 sgn Or + Or,
+// n2 = -0 i2 + 0 = +0, t4 = i4 + 0 with i4 = sgn Oi + Oi, so
+// Re = i1 + 0 and Im = 0 i3 + t4 = t4 (t4 is never -0):
+//     W (x) O = (sgn Or + Or + 0, sgn Oi + Oi + 0).
+// W = -j (table entry N/4: (+0, -1)), ready form (0, 1, 0, -1): n2 = i2 + 0
+// with i2 = sgn Oi + Oi, t4 = 0 i4 + 0 = +0, Re = 0 i1 + n2 = n2,
+// Im = -i3 + 0 with i3 = sgn Or + Or:
+//     W (x) O = (sgn Oi + Oi + 0, -(sgn Or + Or) + 0).
+// (fma(s, 1, o) is the rounded s + o; the + 0 turns a -0 into +0.)
+__device__ __forceinline__ float2 cox_one(float2 o) {
+    return make_float2(__fadd_rn(__fadd_rn(sgn_mul(o.x), o.x), 0.f), __fadd_rn(__fadd_rn(sgn_mul(o.y), o.y), 0.f));
+}
+__device__ __forceinline__ float2 cox_mj(float2 o) {
+    return make_float2(__fadd_rn(__fadd_rn(sgn_mul(o.y), o.y), 0.f), __fadd_rn(-__fadd_rn(sgn_mul(o.x), o.x), 0.f));
+}
+
 struct OpLin {
     __device__ static float4 prep(float2 w) { return make_float4(w.x, w.y, 0.f, 0.f); }
     __device__ static float2 mul(float4 w, float2 o) {
@@ -200,6 +217,22 @@ template <class Op, bool DIF>
 __device__ __forceinline__ void bfly(float2 &e, float2 &o, float4 w) {
     if constexpr (DIF) bfly_dif<Op>(e, o, w);
     else bfly_dit<Op>(e, o, w);
+}
+
+// The nonlinear butterfly with the twiddle W = 1 (AXIS = 0) or W = -j (AXIS = 1).
+template <bool DIF, int AXIS>
+__device__ __forceinline__ void bfly_axis(float2 &e, float2 &o) {
+    const float2 E = e;
+    if constexpr (DIF) {
+        const float2 O = o;
+        e = add2(E, O);
+        const float2 d = sub2(E, O);
+        o = AXIS == 0 ? cox_one(d) : cox_mj(d);
+    } else {
+        const float2 tt = AXIS == 0 ? cox_one(o) : cox_mj(o);
+        e = add2(E, tt);
+        o = sub2(E, tt);
+    }
 }
 
 // ---- N <= 4: one thread per vector ----------------------------------------------------
@@ -267,6 +300,18 @@ __device__ __forceinline__ void reg_stages(float2 (&r)[8], int tlow, const float
         for (int j = 0; j < 8; ++j) {
             if (j & (1 << hb)) continue;
             const int k = tlow | ((j & ((1 << hb) - 1)) << W);  // (base | j << W) mod 2^b
+            if constexpr (W == 0 && std::is_same<Op, OpNL>::value) {
+                // tlow = 0 here, so k is known once the loops are unrolled: the
+                // axis twiddles W^0 = 1 and W^(2^(b-1)) = -j take the short forms
+                if (k == 0) {
+                    bfly_axis<DIF, 0>(r[j], r[j | (1 << hb)]);
+                    continue;
+                }
+                if (b > 0 && k == (1 << (b - 1))) {
+                    bfly_axis<DIF, 1>(r[j], r[j | (1 << hb)]);
+                    continue;
+                }
+            }
             bfly<Op, DIF>(r[j], r[j | (1 << hb)], tb[k]);
         }
     }
