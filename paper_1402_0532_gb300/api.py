@@ -18,6 +18,18 @@ _FORMS = {"direct": L.FORM_DIRECT, "ternary": L.FORM_TERNARY_GEMM, "nfft": L.FOR
 _PRECS = {"fp32": L.PREC_FP32, "bf16x2": L.PREC_BF16X2, "q14": L.PREC_Q14}
 
 
+def choose_form(n: int) -> tuple[str, str]:
+    """(form, prec) of the faster exact-⊗ evaluation of Eq. 8 / Eq. 12a for
+    N = n samples, by the measured crossover on one GB300 (NDFT batches of
+    16..4096 columns, 32..1024 bins, N = 64..16384): the plain form on the CUDA
+    cores for N <= 64 (there the tensor-core form's packing and launch costs
+    dominate: 0.021 against 0.027 ms for 4096 vectors), the tensor-core form
+    everywhere else (from ties at N = 256 to 33x at N = 16384).  Both meet the
+    same 1e-5 bar; for bit-reproducible integer results use prec="q14" with
+    the plain form."""
+    return ("direct", "fp32") if int(n) <= 64 else ("ternary", "bf16x2")
+
+
 def _stream(device) -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
@@ -45,10 +57,13 @@ class Plan:
     <= 65536.  flags: F_NO_CONJ_REF, F_CIRCULAR_LAG, F_NFFT_DIF (decimation in
     frequency for ``nfft`` and the nfft form);
     prec: "fp32" / "q14" (direct), "bf16x2" (ternary), "fp32" (nfft, fft).
-    Bins are p0 .. p0 + nbins - 1 (nbins = 0 -> N)."""
+    form="auto" takes the form and precision ``choose_form(n)`` names (prec is
+    then ignored).  Bins are p0 .. p0 + nbins - 1 (nbins = 0 -> N)."""
 
     def __init__(self, n: int, *, p0: int = 0, nbins: int = 0, max_lags: int = 0, max_batch: int = 0,
                  form: str = "direct", prec: str = "fp32", flags: int = 0, device=None):
+        if form == "auto":
+            form, prec = choose_form(n)
         self.lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.n, self.p0 = int(n), int(p0)

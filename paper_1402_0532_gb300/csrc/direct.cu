@@ -405,14 +405,16 @@ cudaError_t prep_kernel(K kernel, size_t smem) {
 
 }  // namespace
 
-// Splits of the sample axis: the count in [1, 16] (and at most N / 256) whose
-// blocks fill the resident slots (2 blocks per SM) in the best-quantised
-// waves; the smallest such count when several are within 1 %.
+// Splits of the sample axis: the count in [1, 16] (and at most N / 64, four
+// 16-sample chunks per block) whose blocks fill the resident slots (2 blocks
+// per SM) in the best-quantised waves; the smallest such count when several
+// are within 1 %.  Small problems (few tiles) split most: a block runs its
+// samples one after another.
 int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune) {
     if (tune > 0) return std::max(1, std::min(tune, std::max(1, N / KC)));
     const int64_t tiles = (int64_t)((nbins + BP - 1) / BP) * ((nlags + BC - 1) / BC);
     const int64_t slots = 2LL * sm_count;
-    const int cap = std::max(1, std::min(16, N / 256));
+    const int cap = std::max(1, std::min(16, N / (4 * KC)));
     int best_s = 1;
     double best = -1.0;
     for (int c = 1; c <= cap; ++c) {
@@ -426,51 +428,75 @@ int direct_caf_splits(int N, int nlags, int nbins, int sm_count, int tune) {
     return best_s;
 }
 
+// NDFT calls split their sample axis only while the partials fit in this
+// much of the workspace (a split pays off only for calls of few tiles).
+constexpr size_t kNdftSplitBytes = (size_t)32 << 20;
+
 size_t direct_ws_bytes(const ndft_desc &d, int sm_count) {
-    if (d.max_lags <= 0) return 0;
     const int nb = d.nbins ? d.nbins : d.n;
     const int s = 16;  // upper bound of direct_caf_splits
     (void)sm_count;
-    return (size_t)s * d.max_lags * nb * sizeof(float2);
+    size_t b = 0;
+    if (d.max_lags > 0) b = (size_t)s * d.max_lags * nb * sizeof(float2);
+    if (d.max_batch > 0) b = std::max(b, std::min((size_t)s * d.max_batch * nb * sizeof(float2), kNdftSplitBytes));
+    return b;
 }
 
 cudaError_t launch_direct_ndft(const Plan &p, const void *x, void *X, int64_t batch, cudaStream_t s,
                                int *launches) {
     const int N = p.d.n, nb = p.d.nbins ? p.d.nbins : N;
     if (batch == 0) return cudaSuccess;
-    dim3 grid((nb + BP - 1) / BP, (unsigned)((batch + BC - 1) / BC), 1);
+    const bool chk = p.d.prec == NDFT_PREC_Q14 && (p.d.flags & NDFT_F_Q14_RANGE);
+    // split the sample axis like the CAF when the call has few tiles and the
+    // partials fit the workspace (the range check needs whole sums: no split)
+    int nsplit = chk || batch > INT32_MAX ? 1 : direct_caf_splits(N, (int)batch, nb, p.sm_count, p.tune_split);
+    while (nsplit > 1 && (size_t)nsplit * batch * nb * sizeof(float2) > p.ws_alloc) --nsplit;
+    const int64_t per = ((int64_t)N + nsplit - 1) / nsplit;
+    const int64_t per_al = ((per + KC - 1) / KC) * KC;
+    const int ns = (int)((N + per_al - 1) / per_al);
+    dim3 grid((nb + BP - 1) / BP, (unsigned)((batch + BC - 1) / BC), ns);
     if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    const bool split = ns > 1;
     cudaError_t e;
     if (p.d.prec == NDFT_PREC_FP32) {
         const size_t sm = Smem::bytes_for<PrecF32>();
         auto k = k_direct<PrecF32, NdftSrc<PrecF32>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        float2 *dst = split ? static_cast<float2 *>(p.ws) : static_cast<float2 *>(X);
         timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.tw32, N, p.d.p0, nb, (int)batch,
-                                     NdftSrc<PrecF32>{static_cast<const float2 *>(x), N}, N,
-                                     static_cast<float2 *>(X), p.err);
+                                     NdftSrc<PrecF32>{static_cast<const float2 *>(x), N}, per_al, dst, p.err);
         timer_end(p, s);
-    } else if (p.d.flags & NDFT_F_Q14_RANGE) {
+    } else if (chk) {
         const size_t sm = Smem::bytes_for<PrecQ14, true>();
         auto k = k_direct<PrecQ14, NdftSrc<PrecQ14>, true>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
         timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, (int)batch,
-                                     NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, N,
+                                     NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, per_al,
                                      static_cast<uint2 *>(X), p.err);
         timer_end(p, s);
     } else {
         const size_t sm = Smem::bytes_for<PrecQ14>();
         auto k = k_direct<PrecQ14, NdftSrc<PrecQ14>>;
         if ((e = prep_kernel(k, sm)) != cudaSuccess) return e;
+        uint2 *dst = split ? static_cast<uint2 *>(p.ws) : static_cast<uint2 *>(X);
         timer_begin(p, s);
         k<<<grid, kThreads, sm, s>>>(p.twq, N, p.d.p0, nb, (int)batch,
-                                     NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, N,
-                                     static_cast<uint2 *>(X), p.err);
+                                     NdftSrc<PrecQ14>{static_cast<const short2 *>(x), N}, per_al, dst, p.err);
         timer_end(p, s);
     }
     *launches += 1;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (split) {
+        *launches += 1;
+        if (p.d.prec == NDFT_PREC_FP32)
+            return launch_reduce_splits(static_cast<const float *>(p.ws), ns, batch * nb * 2, static_cast<float *>(X),
+                                        s);
+        return launch_reduce_splits_i32(static_cast<const uint32_t *>(p.ws), ns, batch * nb * 2,
+                                        static_cast<uint32_t *>(X), s);
+    }
+    return cudaSuccess;
 }
 
 cudaError_t direct_caf_preload() {

@@ -83,3 +83,14 @@ def test_binding_refuses_cpu_tensors():
     from paper_1402_0532_gb300 import api
     with pytest.raises(TypeError):
         api._need(torch.zeros(4, dtype=torch.complex64), torch.complex64, "x")
+
+
+def test_choose_form_crossover():
+    """The form chooser: the plain form up to N = 64, the tensor-core form above
+    (its measured crossover), each with its own precision."""
+    pytest.importorskip("torch")
+    from paper_1402_0532_gb300 import api
+    assert api.choose_form(2) == ("direct", "fp32")
+    assert api.choose_form(64) == ("direct", "fp32")
+    assert api.choose_form(65) == ("ternary", "bf16x2")
+    assert api.choose_form(65536) == ("ternary", "bf16x2")

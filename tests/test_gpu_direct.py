@@ -333,3 +333,28 @@ def test_invalid_arguments(api):
     with pytest.raises(L.NdftError):
         p.caf(s[:100], s[:100], 0, 9)  # nlags > max_lags
     p.query_error()
+
+
+@pytest.mark.parametrize("N,nbins,batch", [(1024, 32, 16), (4133, 96, 7), (16384, 128, 3)])
+def test_direct_ndft_split_sample_axis(api, N, nbins, batch):
+    """Small NDFT calls (few bin x column tiles) split their sample axis over
+    blocks and sum the partials in order: fp32 within the bar, Q1.14 bit-exact,
+    ragged N included; form="auto" picks the tensor cores above N = 64."""
+    rng = np.random.default_rng(70 + N % 13)
+    x = scenes.cn(rng, (batch, N)).astype(np.complex64)
+    p0 = -(nbins // 2)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="direct", prec="fp32")
+    got = p.ndft(dev(x)).cpu().numpy()
+    p.query_error()
+    assert p.last_launches() == 2  # the split tile kernel and the ordered sum
+    ref = oracle.ndft(x.astype(np.complex128), p0=p0, nbins=nbins)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-5
+    xq = scenes.quantize_q14(scenes.cn(rng, (batch, N)) * 0.25)
+    q = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="direct", prec="q14")
+    gq = q.ndft(dev(xq)).cpu().numpy()
+    q.query_error()
+    assert q.last_launches() == 2
+    want, _ = oracle.ndft_q14(xq, p0=p0, nbins=nbins)
+    assert np.array_equal(gq, want)
+    a = api.Plan(N, p0=p0, nbins=nbins, max_batch=batch, form="auto")
+    assert a.form == "ternary" and a.prec == "bf16x2"
