@@ -2103,11 +2103,12 @@ __global__ void __launch_bounds__(256) k_pack_pair(PackProb P, uint32_t flags, b
 }
 
 // Split-K sum and pair fold into the output [cols][nbins]: block (x, y) =
-// output column x, bins 256 y .. 256 y + 255, one bin per thread.  Bin p0 + k
-// of the window is frequency c = min(p, N - p), p = (p0 + k) mod N: c = 0 from
-// the DC tiles; else slot c - 1 of the partials [split][2 cols][2 S] (rows 2 s,
-// 2 s + 1 = R, I; columns 2 col, 2 col + 1 = r, i), each of a, b, d, e summed
-// over the splits in order, then combined for the sign of the bin.  The split
+// output column x, frequencies c = 1 + 256 y .. 256 y + 256, one per thread.
+// Slot c - 1 of the partials [split][2 cols][2 S] (rows 2 s, 2 s + 1 = R, I;
+// columns 2 col, 2 col + 1 = r, i): each of a, b, d, e summed over the splits
+// in order, once, then combined into X[+c] and X[-c], written to the window's
+// bins p = c and p = N - c (mod N) that it holds (once where they coincide).
+// Bin 0 (c = 0) from the DC tiles, by warp 0 of the y = 0 block.  The split
 // loads are issued ahead of the (ordered) additions.  Deterministic.
 // With ABS the magnitude |X| (fp32, each operation rounded once) is written.
 constexpr int kFoldBins = 256;
@@ -2120,51 +2121,62 @@ __global__ void __launch_bounds__(kFoldBins) k_pair_fold(const float *__restrict
                                                          const float2 *__restrict__ dc, int gy, int ncols,
                                                          void *__restrict__ out_v, int32_t *err) {
     const int col = blockIdx.x;
-    const int k = blockIdx.y * kFoldBins + threadIdx.x;
+    const int64_t c = 1 + (int64_t)blockIdx.y * kFoldBins + threadIdx.x;
     const int64_t S2 = 2LL * S;
     float2 *o = static_cast<float2 *>(out_v) + (int64_t)col * nbins;
     float *oa = static_cast<float *>(out_v) + (int64_t)col * nbins;
-    int64_t p = ((int64_t)p0 + k) % N;
-    if (p < 0) p += N;
-    const int64_t c = p <= N - p ? p : N - p;
-    if (k < nbins && c > 0 && ndft_in(c <= S && col < ncols, err)) {
-        const int64_t s = c - 1;
-        const float2 *pr = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col) * S2 + 2 * s);      // (a, e)
-        const float2 *pi = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col + 1) * S2 + 2 * s);  // (d, b)
-        const int64_t st = split_stride / 2;  // float2 elements between splits
-        float2 ae = pr[0], db = pi[0];
-        int sp = 1;
-        for (; sp + 4 <= nsplit; sp += 4) {
-            float2 u[4], v[4];
+    if (c <= S && ndft_in(col < ncols, err)) {
+        // the window positions of bins +c and -c (>= nbins: not in the window)
+        int64_t kp = (c - p0) % N, km = (N - c - p0) % N;
+        if (kp < 0) kp += N;
+        if (km < 0) km += N;
+        const bool wp = kp < nbins, wm = km < nbins && km != kp;
+        if (wp || wm) {
+            const int64_t s = c - 1;
+            const float2 *pr = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col) * S2 + 2 * s);      // (a, e)
+            const float2 *pi = reinterpret_cast<const float2 *>(part + (int64_t)(2 * col + 1) * S2 + 2 * s);  // (d, b)
+            const int64_t st = split_stride / 2;  // float2 elements between splits
+            float2 ae = pr[0], db = pi[0];
+            int sp = 1;
+            for (; sp + 4 <= nsplit; sp += 4) {
+                float2 u[4], v[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                u[q] = pr[(sp + q) * st];
-                v[q] = pi[(sp + q) * st];
+                for (int q = 0; q < 4; ++q) {
+                    u[q] = pr[(sp + q) * st];
+                    v[q] = pi[(sp + q) * st];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ae.x = __fadd_rn(ae.x, u[q].x);
+                    ae.y = __fadd_rn(ae.y, u[q].y);
+                    db.x = __fadd_rn(db.x, v[q].x);
+                    db.y = __fadd_rn(db.y, v[q].y);
+                }
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                ae.x = __fadd_rn(ae.x, u[q].x);
-                ae.y = __fadd_rn(ae.y, u[q].y);
-                db.x = __fadd_rn(db.x, v[q].x);
-                db.y = __fadd_rn(db.y, v[q].y);
+            for (; sp < nsplit; ++sp) {
+                const float2 u = pr[sp * st], v = pi[sp * st];
+                ae.x = __fadd_rn(ae.x, u.x);
+                ae.y = __fadd_rn(ae.y, u.y);
+                db.x = __fadd_rn(db.x, v.x);
+                db.y = __fadd_rn(db.y, v.y);
+            }
+            // X[+c] = (a - b) + j (d + e), X[-c] = (a + b) + j (d - e)
+            const float2 Xp = make_float2(__fsub_rn(ae.x, db.y), __fadd_rn(db.x, ae.y));
+            const float2 Xm = make_float2(__fadd_rn(ae.x, db.y), __fsub_rn(db.x, ae.y));
+            if (wp) {
+                if constexpr (ABS) oa[kp] = cabs_rn(Xp);
+                else o[kp] = Xp;
+            }
+            if (wm) {
+                if constexpr (ABS) oa[km] = cabs_rn(Xm);
+                else o[km] = Xm;
             }
         }
-        for (; sp < nsplit; ++sp) {
-            const float2 u = pr[sp * st], v = pi[sp * st];
-            ae.x = __fadd_rn(ae.x, u.x);
-            ae.y = __fadd_rn(ae.y, u.y);
-            db.x = __fadd_rn(db.x, v.x);
-            db.y = __fadd_rn(db.y, v.y);
-        }
-        const float2 X = p == c ? make_float2(__fsub_rn(ae.x, db.y), __fadd_rn(db.x, ae.y))
-                                : make_float2(__fadd_rn(ae.x, db.y), __fsub_rn(db.x, ae.y));
-        if constexpr (ABS) oa[k] = cabs_rn(X);
-        else o[k] = X;
     }
-    // bin 0 (if in this block's bins): the DC tiles in a fixed order, warp 0
+    // bin 0 (if in the window): the DC tiles in a fixed order, warp 0 of the y = 0 block
     int64_t k0 = (-(int64_t)p0) % N;
     if (k0 < 0) k0 += N;
-    if (threadIdx.x < 32 && k0 < nbins && k0 / kFoldBins == blockIdx.y) {
+    if (threadIdx.x < 32 && k0 < nbins && blockIdx.y == 0) {
         float sr = 0.f, si = 0.f;
         for (int g = threadIdx.x; g < gy; g += 32) {
             const float2 v = dc[(int64_t)g * ncols + col];
@@ -2771,7 +2783,7 @@ static cudaError_t pair_cols(Plan &p, const PackProb &pp0, bool caf, int ncols, 
     p.last_variant = 2;
     p.last_nsplit = P.nsplit;
     p.last_tile = pair_tile ? 258 : 256;
-    const dim3 fgrid(ncols, (p.d.nbins + kFoldBins - 1) / kFoldBins);
+    const dim3 fgrid(ncols, (S + kFoldBins - 1) / kFoldBins);
     // bin-0 partials: per split and block, per split, or per packing tile
     const int dc_rows = ahead ? P.nsplit * jmax : bgen ? P.nsplit : gy;
     if (p.d.flags & NDFT_F_ABS_OUT)
