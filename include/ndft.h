@@ -308,7 +308,15 @@ ndft_status ndft_last_launches(ndft_plan_t plan, int32_t *count);
  * formed in shared memory per K block by every tile that uses it (four times
  * per B tile; slower, for measurement).  The operand is the same in all
  * three, so every bin but bin 0 (whose sum is grouped differently) is the
- * same bit for bit. */
+ * same bit for bit.
+ * Key 9 = items the key 8 = 0/3 packers may run ahead of their CTA's loads
+ * (0 = 4).  Key 10 = the paired adjoint's A operand (the sign rows
+ * sigma(W^(c i)), one row per sample, K over frequencies), which CAF plans
+ * build as a table at creation (kblocks x 128-byte rows per 256 samples,
+ * 277 MB for 65536 samples and 513 frequencies; within 2 GiB): 0 (default) =
+ * from the table for caf_backward's contraction and generated on chip for
+ * caf_backward_inputs' (there the table measured 2 % slower), 2 = from the
+ * table for both, 1 = generated for both.  The same bits in every case. */
 ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value);
 
 /* Read-only facts about a plan and its last exec call, into *value:

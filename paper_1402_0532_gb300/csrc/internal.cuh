@@ -80,6 +80,11 @@ struct Plan {
     int32_t atab_ld = 0;         // its rows per K block
     void *tmap_a = nullptr;      // its TMA descriptor (host copy)
     void *tmap_a2 = nullptr;     // the same with a 128-row box (2-SM pair tile)
+    void *atab_adj = nullptr;    // ternary CAF plans: the paired adjoint's sign rows
+    size_t atab_adj_bytes = 0;
+    int32_t atab_adj_ld = 0;     // its rows per K block (samples padded to 256)
+    void *tmap_adj = nullptr;    // its TMA descriptor (host copy)
+    int tune_adj_atab = 0;       // the adjoint's A tiles from that table: 0 for dL/ds_surv, 2 for both, 1 neither
     size_t dc_bytes = 0;         // ternary form: per-tile DC sums of the paired packing, then item flags
     size_t dc_flag_off = 0;      // offset of the item flags in that region
     // ternary form: side stream and events of the two-part contraction (the

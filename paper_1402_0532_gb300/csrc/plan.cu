@@ -106,8 +106,10 @@ void free_plan(Plan &p) {
     cudaFree(p.comb);
     cudaFree(p.ws);
     cudaFree(p.atab);
+    cudaFree(p.atab_adj);
     std::free(p.tmap_a);
     std::free(p.tmap_a2);
+    std::free(p.tmap_adj);
     cudaFree(p.err);
     cudaFree(p.cpis_dev);
     cudaFree(p.tab_arena);
@@ -476,6 +478,9 @@ ndft_status ndft_set_tuning(ndft_plan_t plan, int32_t key, int32_t value) {
     } else if (key == 9) {
         if (value > 64) return NDFT_E_INVALID;
         plan->p.tune_look = value;
+    } else if (key == 10) {
+        if (value > 2) return NDFT_E_INVALID;
+        plan->p.tune_adj_atab = value;
     } else {
         return NDFT_E_INVALID;
     }

@@ -579,8 +579,9 @@ struct TileOf<true, MH> {
 // ADJ selects the adjoint contractions (rows = samples, columns = lags, K =
 // bins): 1 folds G into dL/ds_surv in the epilogue, 2 stores G itself (the
 // forward epilogue on a [lags][2N] fp32 output).
-// ATAB (paired forward only): the A tiles come by TMA from a table the plan
-// built (rows [K block][padded rows] of 128 bytes) instead of producer warps.
+// ATAB (paired rows only): the A tiles come by TMA from a table the plan built
+// (rows [K block][padded rows] of 128 bytes) instead of producer warps: the
+// forward's R/I rows, or the paired adjoint's sign rows.
 template <int MH, bool BT, int ADJ, bool PAIR = false, bool ATAB = false>
 __global__ void __launch_bounds__(gemm_threads(PAIR, ATAB), 1)
     k_ternary_gemm(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap, int out_tma,
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(gemm_threads(PAIR, ATAB), 1)
                    const __grid_constant__ CUtensorMap amap) {
     static_assert(ADJ == 0 || (MH == 2 && !BT), "the adjoint runs on the 256-row tile");
     static_assert(!PAIR || (MH == 2 && !BT), "the conjugate-paired form runs on the 256-row tile");
-    static_assert(!ATAB || (PAIR && ADJ == 0), "the A table is for the paired forward contraction");
+    static_assert(!ATAB || PAIR, "the A tables are for the paired contractions");
     constexpr int GW = gemm_gen_warps(PAIR, ATAB);  // A-producer warps: warps 2 .. 2 + GW - 1
     constexpr int EPI0 = 2 + GW;              // epilogue warps EPI0 .. EPI0 + 3 -> TMEM lane quarters warp % 4
     using T = typename TileOf<PAIR, MH>::type;
@@ -754,7 +755,9 @@ __global__ void __launch_bounds__(gemm_threads(PAIR, ATAB), 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        if constexpr (ADJ != 0 && PAIR) {
+        if constexpr (ATAB) {
+            // no producer warps: the TMA warp loads the A tiles from the table
+        } else if constexpr (ADJ != 0 && PAIR) {
             // Conjugate-paired adjoint: one row per sample i, K = frequencies
             // c = p0, p0 + 1, ... (4 entries each, [S_r, S_r, S_i, S_i] of
             // S = sigma(W^(c i)), against the packed [u_hi, u_lo, v_hi, v_lo]
@@ -839,8 +842,6 @@ __global__ void __launch_bounds__(gemm_threads(PAIR, ATAB), 1)
                     }
                 }
             }
-        } else if constexpr (ATAB) {
-            // no producer warps: the TMA warp loads the A tiles from the table
         } else if constexpr (PAIR) {
             // Conjugate-paired rows: slot k of the unit is the frequency
             // c = p0 + k (p0 = the first paired frequency); its R row (2 k) and
@@ -2271,6 +2272,27 @@ __global__ void k_atab(int N, int p0, int S, int rows, int kblocks, const float2
     }
 }
 
+// The paired adjoint's A rows as a table: [K block][row] of 128-byte rows,
+// row i (a sample; rows past N repeat i mod N) holding for frequencies c =
+// 16 kb + 2 t and c + 1 the sign words [S_r, S_r], [S_i, S_i] of
+// S = sigma(W^(c i)) (the integer quadrant rule), exactly what the adjoint's
+// producer warps write.
+__global__ void k_atab_adj(int N, int rows, int kblocks, uint4 *__restrict__ out) {
+    const int64_t total = (int64_t)kblocks * rows * 8;  // (kb, row, chunk)
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e & 7);
+        const int64_t r = e >> 3;
+        const int64_t row = r % rows, kb = r / rows;
+        const int64_t i = row % N;
+        const int64_t c0 = (kb * 16 + 2 * t) % N, c1 = c0 + 1 == N ? 0 : c0 + 1;
+        uint32_t sra, sia, srb, sib;
+        sign_bits(4u * (uint32_t)((c0 * i) % N), (uint32_t)N, sra, sia);
+        sign_bits(4u * (uint32_t)((c1 * i) % N), (uint32_t)N, srb, sib);
+        out[r * 8 + t] = make_uint4(sra, sia, srb, sib);
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -2387,7 +2409,8 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
 
 template <int MH, bool BT = false, int ADJ = 0, bool PAIR = false, bool ATAB = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
-                        int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s) {
+                        int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s,
+                        const void *amap = nullptr) {
     constexpr size_t smem = TileOf<PAIR, MH>::type::kSmemTotal;
     auto kern = k_ternary_gemm<MH, BT, ADJ, PAIR, ATAB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2400,7 +2423,9 @@ cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *pro
     const int out_tma = omap ? 1 : 0;
     timer_begin(p, s);
     const int grid = (int)std::min<int64_t>(nunits, p.sm_count);
-    const CUtensorMap &am = (ATAB && p.tmap_a) ? *static_cast<const CUtensorMap *>(p.tmap_a) : none;
+    if (ATAB && !amap) amap = p.tmap_a;  // the forward table unless another is given
+    if (ATAB && !amap) return cudaErrorInvalidValue;
+    const CUtensorMap &am = ATAB ? *static_cast<const CUtensorMap *>(amap) : none;
     kern<<<grid, gemm_threads(PAIR, ATAB), smem, s>>>(*map, om, out_tma, single, probs, units, nunits, chunk,
                                                       p.test_starve, out_base, p.err, am);
     e = cudaGetLastError();
@@ -2573,6 +2598,26 @@ cudaError_t ternary_plan_init(Plan &p, cudaStream_t s) {
             p.tmap_a2 = std::aligned_alloc(64, sizeof(CUtensorMap));  // 128-row box for the 2-SM pair tile
             if (!p.tmap_a2) return cudaErrorMemoryAllocation;
             if ((e = make_tmap(p.atab, (int64_t)kbp * rows, static_cast<CUtensorMap *>(p.tmap_a2), TN / 2)) !=
+                cudaSuccess)
+                return e;
+        }
+        // CAF plans: the paired adjoint's sign rows as a table too ([frequency
+        // block][sample row], 277 MB for 65536 samples and 513 frequencies)
+        const int kba = (p.pair_slots + 1 + 15) / 16;
+        const int arows = (N + 255) / 256 * 256;
+        const size_t abytes = (size_t)kba * arows * 128;
+        if (p.d.max_lags > 0 && abytes <= kAtabMaxBytes && (int64_t)kba * arows < (1LL << 31)) {
+            if ((e = cudaMalloc(&p.atab_adj, abytes)) != cudaSuccess) return e;
+            p.atab_adj_bytes = abytes;
+            p.atab_adj_ld = arows;
+            p.table_bytes += abytes;
+            const int64_t items = (int64_t)kba * arows * 8;
+            const int blocks = (int)std::min<int64_t>((items + 255) / 256, (int64_t)p.sm_count * 32);
+            k_atab_adj<<<blocks, 256, 0, s>>>(N, arows, kba, static_cast<uint4 *>(p.atab_adj));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            p.tmap_adj = std::aligned_alloc(64, sizeof(CUtensorMap));
+            if (!p.tmap_adj) return cudaErrorMemoryAllocation;
+            if ((e = make_tmap(p.atab_adj, (int64_t)kba * arows, static_cast<CUtensorMap *>(p.tmap_adj))) !=
                 cudaSuccess)
                 return e;
         }
@@ -2871,6 +2916,11 @@ cudaError_t launch_ternary_caf(Plan &p, const void *s_surv, const void *s_ref, i
 // The paired adjoint contraction: rows = samples, columns = (lag, Re / Im),
 // K = frequencies 0 .. S (4 entries each).  Used when the window pairs and
 // it issues fewer K-block steps than one row pair per sample over the bins.
+// The paired adjoint's A rows from the plan's table (built for CAF plans while
+// it stays within kAtabMaxBytes): tuning key 10 = 0 (default) for dL/ds_surv's
+// contraction, 2 for both adjoint contractions, 1 for neither.
+static bool adj_table(const Plan &p) { return p.atab_adj && p.tmap_adj && p.tune_adj_atab != 1; }
+
 static bool use_pair_adjoint(const Plan &p, int ncols) {
     if (p.tune_pair == 1 || p.pair_slots < 1) return false;
     const int64_t N = p.d.n, nb = p.d.nbins, S1 = p.pair_slots + 1;
@@ -2916,9 +2966,14 @@ cudaError_t launch_ternary_adjoint(Plan &p, const void *s_ref, int lag0, int nla
             if (e != cudaSuccess) return e;
             *launches += 1;
             float *part = reinterpret_cast<float *>(static_cast<unsigned char *>(p.ws) + p.b_bytes);
-            if ((e = launch_gemm<2, false, 1, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s)) !=
-                cudaSuccess)
-                return e;
+            if (adj_table(p)) {
+                P.a_ld = p.atab_adj_ld;
+                e = launch_gemm<2, false, 1, true, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s,
+                                                         p.tmap_adj);
+            } else {
+                e = launch_gemm<2, false, 1, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part, nullptr, s);
+            }
+            if (e != cudaSuccess) return e;
             *launches += 2;
             p.last_variant = 2;
             p.last_nsplit = P.nsplit;
@@ -3027,9 +3082,16 @@ cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const floa
             alignas(64) CUtensorMap omap;
             const bool tma_out = (N % 4 == 0) && p.tune_drain == 0 &&
                                  make_out_rows_map(g, N, P.ncols, ns, &omap) == cudaSuccess;
-            if ((e = launch_gemm<2, false, 2, true>(p, P, nullptr, nullptr, tiles * ns, g, tma_out ? &omap : nullptr,
-                                                    s)) != cudaSuccess)
-                return e;
+            if (adj_table(p) && p.tune_adj_atab == 2) {
+                // (the G-storing contraction is bound by its epilogue: the table
+                // measured 2 % slower there, so it runs with generated rows by default)
+                P.a_ld = p.atab_adj_ld;
+                e = launch_gemm<2, false, 2, true, true>(p, P, nullptr, nullptr, tiles * ns, g,
+                                                         tma_out ? &omap : nullptr, s, p.tmap_adj);
+            } else {
+                e = launch_gemm<2, false, 2, true>(p, P, nullptr, nullptr, tiles * ns, g, tma_out ? &omap : nullptr, s);
+            }
+            if (e != cudaSuccess) return e;
             *launches += 1;
             p.last_variant = 2;
             p.last_nsplit = ns;

@@ -222,15 +222,19 @@ def test_paired_adjoint(api, N, lag0, nlags, p0, nbins, flags):
     makes bins +c and -c of dA enter G as S_r u + ... with u, v = dA[+c] +- dA[-c]
     (one row per sample, half the multiply-adds); dL/ds_surv (the fused fold) and
     both gradients (G stored, then folded) against the fp64 oracle adjoints,
-    forced on (key 6 = 2) and off (key 6 = 1)."""
+    forced on (key 6 = 2; the sign rows from the plan's table for one or both
+    contractions, key 10 = 0 / 2, or generated on chip, key 10 = 1, the same
+    bits) and off (key 6 = 1)."""
     sc = scenes.radar_scene(N=N, nlags=min(nlags, 64), nbins=min(nbins, 64), seed=66 + N % 11)
     rng = np.random.default_rng(67)
     dA = scenes.cn(rng, (nlags, nbins))
     want_s = oracle.caf_adjoint(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, dA, flags=flags)
     want_r = oracle.caf_adjoint_ref(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, dA, flags=flags)
-    for key in (2, 1):
+    outs = {}
+    for key, gen in ((2, 0), (2, 2), (2, 1), (1, 0)):
         p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, flags=flags, form="ternary", prec="bf16x2")
         p.set_tuning(6, key)
+        p.set_tuning(10, gen)
         ss, sr, d = dev(sc.s_surv), dev(sc.s_ref), dev(dA.astype(np.complex64))
         g = p.caf_backward(ss, sr, lag0, nlags, d).cpu().numpy()
         p.query_error()
@@ -241,6 +245,11 @@ def test_paired_adjoint(api, N, lag0, nlags, p0, nbins, flags):
         assert p.query(1) == (2 if key == 2 else 1)
         assert relerr(gs.cpu().numpy(), want_s) < TOL, key
         assert relerr(gr.cpu().numpy(), want_r) < TOL, key
+        outs[(key, gen)] = (g, gs.cpu().numpy(), gr.cpu().numpy())
+    for other in ((2, 1), (2, 2)):
+        for a, b in zip(outs[(2, 0)], outs[other]):
+            a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), other
 
 
 def test_paired_adjoint_headline_sampled(api):
