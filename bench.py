@@ -177,8 +177,8 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
         X = torch.empty_like(xt)
         ms = _time_ms(lambda: p.ndft(xt, out=X), 20, flush)
         out[f"ndft_64_x4096_{form}"] = {"ms": ms, "vectors_per_s": 4096 / (ms / 1e3)}
-    # 256 CPIs: the tensor-core form as one captured CUDA graph (pack + one
-    # persistent contraction), the plain form in fp32 and Q1.14 (eager, one run)
+    # 256 CPIs: the tensor-core form as one captured CUDA graph (a conjugate-paired
+    # call per CPI), the plain form in fp32 and Q1.14 (eager, one run)
     scs = scenes.cpi_batch()
     surv, ref, qsurv, qref, cpis, oo, so = [], [], [], [], [], 0, 0
     for sc in scs:

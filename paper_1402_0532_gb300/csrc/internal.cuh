@@ -35,6 +35,14 @@ struct CpiDev {
     int32_t kblocks;    // 64-wide K blocks (ternary form)
 };
 
+// One CPI of a batched tensor-core plan, for its conjugate-paired call.
+struct PairCpi {
+    int32_t n, p0, nbins, lag0, nlags, slots;
+    int64_t off_surv, off_ref, off_out;  // elements from the call's bases
+    const float2 *ang;                   // its two-level (cos, sin) table
+    int32_t nth;
+};
+
 struct Plan {
     ndft_desc d{};
     bool batched = false;
@@ -107,6 +115,10 @@ struct Plan {
     size_t part_bytes = 0;       // split-K partials region of the workspace
     // batched ternary plans: the output viewed as one [rows][2 nbins] fp32 tensor
     // for the bulk-copy fold-out (0 rows: CPIs differ in nbins or are not row-aligned)
+    PairCpi *pair_cpis = nullptr;  // batched tensor-core plans: the CPIs, longest first, when all pair
+    int32_t npair = 0;
+    size_t bp_b_bytes = 0, bp_part_bytes = 0, bp_dc_bytes = 0;  // their workspace regions
+    void *tmap_bpair = nullptr;    // TMA descriptor of their packed B region
     int32_t bt_nbins = 0;
     int64_t bt_rows = 0;
 };

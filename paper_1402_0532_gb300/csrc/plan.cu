@@ -118,6 +118,8 @@ void free_plan(Plan &p) {
     cudaFree(p.tmap_dev);
     std::free(p.tmap_host);
     std::free(p.tmap_host2);
+    std::free(p.tmap_bpair);
+    delete[] p.pair_cpis;
     delete[] p.cpis_host;
     if (p.tev) {
         for (int i = 0; i < 2 * p.tcap; ++i) cudaEventDestroy(p.tev[i]);

@@ -2410,12 +2410,12 @@ cudaError_t launch_pack(const PackProb *probs, const int64_t *prefix, int nprob,
 template <int MH, bool BT = false, int ADJ = 0, bool PAIR = false, bool ATAB = false>
 cudaError_t launch_gemm(const Plan &p, const Problem &single, const Problem *probs, const Unit *units,
                         int64_t nunits, float *out_base, const CUtensorMap *omap, cudaStream_t s,
-                        const void *amap = nullptr) {
+                        const void *amap = nullptr, const void *bmap = nullptr) {
     constexpr size_t smem = TileOf<PAIR, MH>::type::kSmemTotal;
     auto kern = k_ternary_gemm<MH, BT, ADJ, PAIR, ATAB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const CUtensorMap *map = static_cast<const CUtensorMap *>(p.tmap_host);
+    const CUtensorMap *map = static_cast<const CUtensorMap *>(bmap ? bmap : p.tmap_host);
     const int chunk = p.tune_chunk > 0 ? p.tune_chunk : (PAIR ? kChunkPair : kChunk);
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
@@ -3236,15 +3236,118 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // `host` must outlive the copy
     p.nwork = (int64_t)units.size();
     p.b_bytes = (size_t)std::max<int64_t>(rows_total, 1) * 128;
-    p.ws_bytes = p.b_bytes;
+    // the conjugate-paired calls, one CPI after another (longest first), when
+    // every CPI's window pairs: regions for the largest CPI's packed B, split
+    // partials and bin-0 sums
+    bool pairs = true;
+    std::vector<PairCpi> pc;
+    int64_t bp_rows = 1;
+    size_t bp_part = (size_t)4 * p.sm_count * 256 * TN * sizeof(float), bp_dc = 256;
+    for (int c : order) {
+        const ndft_cpi &q = cpis[c];
+        const int S = pair_slots_for(q.n, q.p0, q.nbins);
+        if (S < 1) {
+            pairs = false;
+            break;
+        }
+        pc.push_back(PairCpi{q.n, q.p0, q.nbins, q.lag0, q.nlags, S, q.off_surv, q.off_ref, q.off_out, probs[c].ang,
+                             probs[c].nth});
+        bp_rows = std::max<int64_t>(bp_rows, (int64_t)pair_kblocks(q.n) * 2 * q.nlags);
+        bp_part = std::max(bp_part, (size_t)2 * q.nlags * 2 * S * sizeof(float));
+        bp_dc = std::max(bp_dc, (size_t)pair_pack_tiles(q.n) * q.nlags * sizeof(float2));
+    }
+    size_t ws = p.b_bytes;
+    if (pairs && bp_rows < (1LL << 31)) {
+        p.bp_b_bytes = ((size_t)bp_rows * 128 + 1023) & ~(size_t)1023;
+        p.bp_part_bytes = (bp_part + 1023) & ~(size_t)1023;
+        p.bp_dc_bytes = (bp_dc + 255) & ~(size_t)255;
+        ws = std::max(ws, p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes);
+        p.pair_cpis = new (std::nothrow) PairCpi[pc.size()];
+        if (!p.pair_cpis) return cudaErrorMemoryAllocation;
+        std::copy(pc.begin(), pc.end(), p.pair_cpis);
+        p.npair = (int32_t)pc.size();
+    }
+    p.ws_bytes = ws;
+    p.ws_alloc = ws;
     if ((e = cudaMalloc(&p.ws, p.ws_bytes)) != cudaSuccess) return e;
     p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));
     if (!p.tmap_host) return cudaErrorMemoryAllocation;
-    return make_tmap(p.ws, std::max<int64_t>(rows_total, 1), static_cast<CUtensorMap *>(p.tmap_host));
+    if ((e = make_tmap(p.ws, std::max<int64_t>(rows_total, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
+        cudaSuccess)
+        return e;
+    if (p.npair > 0) {
+        p.tmap_bpair = std::aligned_alloc(64, sizeof(CUtensorMap));
+        if (!p.tmap_bpair) return cudaErrorMemoryAllocation;
+        if ((e = make_tmap(p.ws, bp_rows, static_cast<CUtensorMap *>(p.tmap_bpair))) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The batched plan's CPIs one after another as conjugate-paired calls (the
+// single-surface path with generated A rows): per CPI the paired packing,
+// the contraction and the fold into its surface.
+static cudaError_t batched_pair_calls(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
+                                      int *launches) {
+    unsigned char *ws = static_cast<unsigned char *>(p.ws);
+    float *part = reinterpret_cast<float *>(ws + p.bp_b_bytes);
+    float2 *dc = reinterpret_cast<float2 *>(ws + p.bp_b_bytes + p.bp_part_bytes);
+    const bool caf = true;
+    for (int k = 0; k < p.npair; ++k) {
+        const PairCpi &q = p.pair_cpis[k];
+        const int N = q.n, S = q.slots, ncols = q.nlags;
+        const int kblocks = pair_kblocks(N), gy = pair_pack_tiles(N);
+        PackProb pp{};
+        pp.a_off = q.off_surv;
+        pp.r_off = q.off_ref;
+        pp.N = N;
+        pp.lag0 = q.lag0;
+        pp.ncols = ncols;
+        pp.kblocks = kblocks;
+        pp.ldx = 0;
+        pp.row0 = 0;
+        k_pack_pair<<<dim3((ncols + 31) / 32, std::min(gy, 65535)), 256, 0, s>>>(
+            pp, p.d.flags, caf, static_cast<const float2 *>(surv), static_cast<const float2 *>(ref),
+            static_cast<uint4 *>(p.ws), dc, gy, p.err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        Problem P{};
+        P.N = N;
+        P.p0 = 1;
+        P.nbins = S;
+        P.ncols = 2 * ncols;
+        P.kblocks = kblocks;
+        P.mtiles = (2 * S + 255) / 256;
+        P.ntiles = (P.ncols + TN - 1) / TN;
+        const int64_t tiles = (int64_t)P.mtiles * P.ntiles;
+        const int64_t cap_units = (int64_t)(p.bp_part_bytes / ((size_t)256 * TN * sizeof(float)));
+        P.nsplit = choose_split(tiles, kblocks, p.sm_count, p.tune_split, cap_units);
+        while (P.nsplit > 1 && (size_t)P.nsplit * P.ncols * 2 * S * sizeof(float) > p.bp_part_bytes) --P.nsplit;
+        P.b_row0 = 0;
+        P.ld = 2LL * S;
+        P.split_stride = (int64_t)P.ncols * 2 * S;
+        P.ang = q.ang;
+        P.nth = q.nth;
+        P.out_off = 0;
+        alignas(64) CUtensorMap omap;
+        const bool tma_out = (S % 2 == 0) && p.tune_drain == 0 &&
+                             make_out_map(part, S, P.ncols, P.nsplit, &omap, 32) == cudaSuccess;
+        if ((e = launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
+                                                tma_out ? &omap : nullptr, s, nullptr, p.tmap_bpair)) != cudaSuccess)
+            return e;
+        const dim3 fgrid(ncols, (S + kFoldBins - 1) / kFoldBins);
+        k_pair_fold<false><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, q.p0, q.nbins, dc, gy,
+                                                       ncols, static_cast<float2 *>(out) + q.off_out, p.err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 3;
+    }
+    p.last_variant = 2;
+    p.last_tile = 256;
+    return cudaSuccess;
 }
 
 cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
                                    int *launches) {
+    if (p.npair > 0 && p.tune_pair != 1) return batched_pair_calls(p, surv, ref, out, s, launches);
     const BatchedLayout BL = batched_layout(p.ncpi, p.nwork);
     unsigned char *wd = reinterpret_cast<unsigned char *>(p.work_dev);
     const Problem *probs = reinterpret_cast<const Problem *>(wd + BL.probs);

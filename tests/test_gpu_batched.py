@@ -50,10 +50,15 @@ def small_scenes():
             for n, l, b in ((1000, 70, 64), (1536, 5, 96), (777, 130, 33), (2048, 300, 128), (1111, 1, 7))]
 
 
-def test_batched_ternary_small(api):
+@pytest.mark.parametrize("pairing", [0, 1])
+def test_batched_ternary_small(api, pairing):
+    """The tensor-core batch as conjugate-paired calls per CPI (the default
+    when every window pairs) and as one persistent unpaired contraction over
+    all CPIs (tuning key 6 = 1), each CPI against the oracle."""
     scs = small_scenes()
     surv, ref, cpis, total = pack(scs)
     bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    bp.set_tuning(6, pairing)
     out = torch.zeros(total, dtype=torch.complex64, device="cuda")
     bp(dev(surv), dev(ref), out)
     bp.query_error()
@@ -64,16 +69,19 @@ def test_batched_ternary_small(api):
         assert np.max(np.abs(g - want)) / np.max(np.abs(want)) < TOL
 
 
-def test_batched_ternary_uniform_bins(api):
+@pytest.mark.parametrize("pairing", [0, 1])
+def test_batched_ternary_uniform_bins(api, pairing):
     """CPIs that share an even nbins use one output tensor map for the bulk-copy
-    fold-out; lag counts that are not multiples of 16 end in column groups that
-    are written element by element (so no CPI's copy runs into the next
-    surface).  Long CPIs make several accumulation chains per unit."""
+    fold-out of the unpaired contraction; lag counts that are not multiples of
+    16 end in column groups that are written element by element (so no CPI's
+    copy runs into the next surface).  Long CPIs make several accumulation
+    chains per unit.  Paired per-CPI calls (default) and unpaired (key 6 = 1)."""
     rng = np.random.default_rng(37)
     scs = [scenes.radar_scene(N=int(n), nlags=int(l), nbins=40, rng=rng)
            for n, l in ((9000, 5), (1536, 17), (12000, 33), (2048, 300), (700, 1), (16384, 16))]
     surv, ref, cpis, total = pack(scs)
     bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    bp.set_tuning(6, pairing)
     out = torch.zeros(total, dtype=torch.complex64, device="cuda")
     guard = torch.full((total + 64,), complex(7.0, -7.0), dtype=torch.complex64, device="cuda")
     bp(dev(surv), dev(ref), guard[:total])
