@@ -3260,8 +3260,11 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
     if (pairs && bp_rows < (1LL << 31)) {
         p.bp_b_bytes = ((size_t)bp_rows * 128 + 1023) & ~(size_t)1023;
         p.bp_part_bytes = (bp_part + 1023) & ~(size_t)1023;
-        p.bp_dc_bytes = (bp_dc + 255) & ~(size_t)255;
-        ws = std::max(ws, p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes);
+        p.bp_dc_bytes = (bp_dc + 1023) & ~(size_t)1023;
+        // two such slices: consecutive CPIs run on the call's stream and a
+        // plan-owned side stream, so one's packing and fold overlap the other's
+        // contraction
+        ws = std::max(ws, 2 * (p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes));
         p.pair_cpis = new (std::nothrow) PairCpi[pc.size()];
         if (!p.pair_cpis) return cudaErrorMemoryAllocation;
         std::copy(pc.begin(), pc.end(), p.pair_cpis);
@@ -3276,23 +3279,41 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
         cudaSuccess)
         return e;
     if (p.npair > 0) {
-        p.tmap_bpair = std::aligned_alloc(64, sizeof(CUtensorMap));
+        const size_t slice = p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes;
+        p.tmap_bpair = std::aligned_alloc(64, 2 * sizeof(CUtensorMap));
         if (!p.tmap_bpair) return cudaErrorMemoryAllocation;
-        if ((e = make_tmap(p.ws, bp_rows, static_cast<CUtensorMap *>(p.tmap_bpair))) != cudaSuccess) return e;
+        CUtensorMap *m = static_cast<CUtensorMap *>(p.tmap_bpair);
+        if ((e = make_tmap(p.ws, bp_rows, &m[0])) != cudaSuccess) return e;
+        if ((e = make_tmap(static_cast<unsigned char *>(p.ws) + slice, bp_rows, &m[1])) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// The batched plan's CPIs one after another as conjugate-paired calls (the
-// single-surface path with generated A rows): per CPI the paired packing,
-// the contraction and the fold into its surface.
-static cudaError_t batched_pair_calls(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
+// The batched plan's CPIs as conjugate-paired calls (the single-surface path
+// with generated A rows): per CPI the paired packing, the contraction and the
+// fold into its surface.  CPIs alternate, longest first, between the call's
+// stream and the plan's side stream, each with its own workspace slice; the
+// side stream forks from and joins back into the call's stream (so stream
+// order and CUDA-graph capture are kept).
+static cudaError_t batched_pair_calls(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s0,
                                       int *launches) {
-    unsigned char *ws = static_cast<unsigned char *>(p.ws);
-    float *part = reinterpret_cast<float *>(ws + p.bp_b_bytes);
-    float2 *dc = reinterpret_cast<float2 *>(ws + p.bp_b_bytes + p.bp_part_bytes);
+    const bool two = p.side && p.npair > 1;
+    cudaError_t e;
+    if (two) {
+        if ((e = cudaEventRecord(p.ev_fork, s0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess) return e;
+    }
     const bool caf = true;
     for (int k = 0; k < p.npair; ++k) {
+        const int sl = two ? (k & 1) : 0;
+        const cudaStream_t s = sl ? p.side : s0;
+        unsigned char *ws = static_cast<unsigned char *>(p.ws) + sl * (p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes);
+        float *part = reinterpret_cast<float *>(ws + p.bp_b_bytes);
+        float2 *dc = reinterpret_cast<float2 *>(ws + p.bp_b_bytes + p.bp_part_bytes);
+        const CUtensorMap *bmap = static_cast<const CUtensorMap *>(p.tmap_bpair) + sl;
         const PairCpi &q = p.pair_cpis[k];
         const int N = q.n, S = q.slots, ncols = q.nlags;
         const int kblocks = pair_kblocks(N), gy = pair_pack_tiles(N);
@@ -3307,9 +3328,8 @@ static cudaError_t batched_pair_calls(Plan &p, const void *surv, const void *ref
         pp.row0 = 0;
         k_pack_pair<<<dim3((ncols + 31) / 32, std::min(gy, 65535)), 256, 0, s>>>(
             pp, p.d.flags, caf, static_cast<const float2 *>(surv), static_cast<const float2 *>(ref),
-            static_cast<uint4 *>(p.ws), dc, gy, p.err);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+            reinterpret_cast<uint4 *>(ws), dc, gy, p.err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         Problem P{};
         P.N = N;
         P.p0 = 1;
@@ -3332,13 +3352,17 @@ static cudaError_t batched_pair_calls(Plan &p, const void *surv, const void *ref
         const bool tma_out = (S % 2 == 0) && p.tune_drain == 0 &&
                              make_out_map(part, S, P.ncols, P.nsplit, &omap, 32) == cudaSuccess;
         if ((e = launch_gemm<2, false, 0, true>(p, P, nullptr, nullptr, tiles * P.nsplit, part,
-                                                tma_out ? &omap : nullptr, s, nullptr, p.tmap_bpair)) != cudaSuccess)
+                                                tma_out ? &omap : nullptr, s, nullptr, bmap)) != cudaSuccess)
             return e;
         const dim3 fgrid(ncols, (S + kFoldBins - 1) / kFoldBins);
         k_pair_fold<false><<<fgrid, kFoldBins, 0, s>>>(part, P.nsplit, P.split_stride, S, N, q.p0, q.nbins, dc, gy,
                                                        ncols, static_cast<float2 *>(out) + q.off_out, p.err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 3;
+    }
+    if (two) {
+        if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s0, p.ev_join, 0)) != cudaSuccess) return e;
     }
     p.last_variant = 2;
     p.last_tile = 256;
