@@ -120,6 +120,16 @@ def profile_other(args, api, scenes, dev):
                       "kernel_ms": ms / max(n, 1), "units_per_s": units / (ms / max(n, 1) / 1e3)}), flush=True)
 
 
+def adjoint_issued_flops(plan, N: int, nlags: int, nbins: int) -> float:
+    """Flop the last adjoint contraction issued: paired (query 1 = 2): rows = N
+    samples, columns = 2 per lag, K = 4 per frequency 0 .. S in blocks of 16;
+    unpaired: rows = 2N, columns = lags, K = 4 per bin in blocks of 16."""
+    if plan.query(1) == 2:
+        k = 4 * 16 * ((plan.query(0) + 1 + 15) // 16)
+        return 2.0 * N * (2 * nlags) * k
+    return 2.0 * (2 * N) * nlags * (4 * 16 * ((nbins + 15) // 16))
+
+
 def _time_ms(fn, reps: int, flush=None) -> float:
     """Mean device time of fn() over reps calls (CUDA events; L2 flushed before each when given)."""
     import torch
@@ -294,7 +304,7 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
         plan.caf_backward(ss, sr, 0, 512, dA, out=ds)
     bms, bn = plan.timer_read()
     bwd_ms = bms / max(bn, 1)
-    issued = 2.0 * (2 * sc.N) * 512 * (4 * 512)  # rows x lags x K (bins x hi/lo x re/im), 2 flop per MAC
+    issued = adjoint_issued_flops(plan, sc.N, 512, 512)
     out["caf_16384_fwd_bwd"] = {"ms": ms, "ms_cuda_graph": ms_graph, "cells": 512 * 512, "backward_kernel_ms": bwd_ms,
                                 "backward_issued_tflops": issued / (bwd_ms / 1e3) / 1e12}
     del plan, ss, sr, dA, ds
@@ -311,12 +321,20 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
     ms_b = _time_ms(lambda: ph.caf_backward_inputs(ss, sr, 0, 1024, dA), 5, flush)
     ph.timer_start(5)
     for _ in range(5):
-        ph.caf_backward_inputs(ss, sr, 0, 1024, dA)
+        ph.caf_backward(ss, sr, 0, 1024, dA, out=ds)
     cms, cn = ph.timer_read()
     c_ms = cms / max(cn, 1)
-    issued = 2.0 * (2 * 65536) * 1024 * (4 * 1024)
-    out["caf_65536_backward"] = {"surv_ms": ms_s, "surv_and_ref_ms": ms_b, "contraction_ms": c_ms,
-                                 "contraction_issued_tflops": issued / (c_ms / 1e3) / 1e12,
+    issued = adjoint_issued_flops(ph, 65536, 1024, 1024)
+    ph.timer_start(5)
+    for _ in range(5):
+        ph.caf_backward_inputs(ss, sr, 0, 1024, dA)
+    gms, gn = ph.timer_read()
+    g_ms = gms / max(gn, 1)
+    out["caf_65536_backward"] = {"surv_ms": ms_s, "surv_and_ref_ms": ms_b,
+                                 "surv_contraction_ms": c_ms,
+                                 "surv_contraction_issued_tflops": issued / (c_ms / 1e3) / 1e12,
+                                 "g_contraction_ms": g_ms,
+                                 "g_contraction_issued_tflops": issued / (g_ms / 1e3) / 1e12,
                                  "launches": ph.last_launches()}
     del ph, ss, sr, dA, ds
     # a stream of surfaces: two plans on two streams, so the lag-product packing of
