@@ -169,9 +169,18 @@ ndft_status nfft_exec(ndft_plan_t plan, const void *x, void *X, int64_t batch, c
 ndft_status caf_exec(ndft_plan_t plan, const void *s_surv, const void *s_ref, int32_t lag0,
                      int32_t nlags, void *A, cudaStream_t stream);
 
-/* Batched CAF over the plan's CPI list, all CPIs in one persistent launch
- * sequence: CPI c reads surv_base + off_surv, ref_base + off_ref and writes
- * out_base + off_out.  Offsets are in elements of the plan's precision. */
+/* Batched CAF over the plan's CPI list: CPI c reads surv_base + off_surv,
+ * ref_base + off_ref and writes out_base + off_out.  Offsets are in elements
+ * of the plan's precision.  The direct form runs one persistent launch over
+ * all CPIs.  The tensor-core form, when every CPI's window pairs, runs one
+ * conjugate-paired call per CPI (packing, contraction, fold; longest CPI
+ * first, alternating between `stream` and a plan-owned side stream that
+ * forks from and joins back into it, so capture in a CUDA graph works);
+ * otherwise, or with tuning key 6 = 1, it packs every CPI and runs one
+ * persistent unpaired contraction, which needs the whole batch's packed
+ * operand (16 bytes per sample and lag of every CPI): a paired plan keeps
+ * that only when it is at most 4 GiB, else key 6 = 1 gives
+ * NDFT_E_UNSUPPORTED. */
 ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void *ref_base,
                              void *out_base, cudaStream_t stream);
 

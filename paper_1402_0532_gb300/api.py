@@ -347,6 +347,12 @@ class BatchedPlan:
     def set_tuning(self, key: int, value: int):
         L.check(self.lib.ndft_set_tuning(self.handle, int(key), int(value)), "ndft_set_tuning")
 
+    def nbytes(self) -> int:
+        """Device bytes the plan holds (tables + workspace)."""
+        b = ctypes.c_int64()
+        L.check(self.lib.ndft_plan_bytes(self.handle, ctypes.byref(b)), "ndft_plan_bytes")
+        return b.value
+
     def signature(self) -> str:
         return self._sig
 

@@ -118,7 +118,8 @@ struct Plan {
     PairCpi *pair_cpis = nullptr;  // batched tensor-core plans: the CPIs, longest first, when all pair
     int32_t npair = 0;
     size_t bp_b_bytes = 0, bp_part_bytes = 0, bp_dc_bytes = 0;  // their workspace regions
-    void *tmap_bpair = nullptr;    // TMA descriptor of their packed B region
+    void *tmap_bpair = nullptr;    // TMA descriptors of their packed B regions (two slices)
+    bool bt_unpaired = true;       // the whole batch's unpaired operand fits the workspace
     int32_t bt_nbins = 0;
     int64_t bt_rows = 0;
 };

@@ -616,8 +616,10 @@ ndft_status caf_exec_batched(ndft_plan_t plan, const void *surv_base, const void
     Plan &p = plan->p;
     p.last_launches = 0;
     p.last_variant = p.last_nsplit = p.last_tile = 0;
-    if (p.d.form == NDFT_FORM_TERNARY_GEMM)
-        return from_cuda(launch_ternary_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));
+    if (p.d.form == NDFT_FORM_TERNARY_GEMM) {
+        const cudaError_t e = launch_ternary_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches);
+        return e == cudaErrorNotSupported ? NDFT_E_UNSUPPORTED : from_cuda(e);
+    }
     return from_cuda(launch_direct_batched(p, surv_base, ref_base, out_base, stream, &p.last_launches));
 }
 

@@ -3151,6 +3151,10 @@ cudaError_t launch_ternary_adjoint_g(Plan &p, int nc, const void *dA, const floa
 // Batched CPIs: per-CPI angle tables, packed-B regions and a work list of
 // (cpi, m-tile, n-tile) units, longest CPI first, built once here.  No split
 // of the sample axis: the CPIs supply thousands of units.
+// Largest whole-batch unpaired operand a paired batched plan keeps beside its
+// two paired workspace slices (for tuning key 6 = 1).
+constexpr size_t kUnpairedBatchBytes = (size_t)4 << 30;
+
 cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaStream_t s) {
     std::vector<Problem> probs(ncpi);
     std::vector<PackProb> packs(ncpi);
@@ -3257,6 +3261,7 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
         bp_dc = std::max(bp_dc, (size_t)pair_pack_tiles(q.n) * q.nlags * sizeof(float2));
     }
     size_t ws = p.b_bytes;
+    p.bt_unpaired = true;
     if (pairs && bp_rows < (1LL << 31)) {
         p.bp_b_bytes = ((size_t)bp_rows * 128 + 1023) & ~(size_t)1023;
         p.bp_part_bytes = (bp_part + 1023) & ~(size_t)1023;
@@ -3264,7 +3269,11 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
         // two such slices: consecutive CPIs run on the call's stream and a
         // plan-owned side stream, so one's packing and fold overlap the other's
         // contraction
-        ws = std::max(ws, 2 * (p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes));
+        // the whole batch's unpaired operand (16 bytes per sample and lag of
+        // every CPI) is kept beside them for key 6 = 1 only while it is modest
+        const size_t slices = 2 * (p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes);
+        p.bt_unpaired = p.b_bytes <= kUnpairedBatchBytes;
+        ws = p.bt_unpaired ? std::max(ws, slices) : slices;
         p.pair_cpis = new (std::nothrow) PairCpi[pc.size()];
         if (!p.pair_cpis) return cudaErrorMemoryAllocation;
         std::copy(pc.begin(), pc.end(), p.pair_cpis);
@@ -3275,8 +3284,9 @@ cudaError_t ternary_batched_init(Plan &p, const ndft_cpi *cpis, int ncpi, cudaSt
     if ((e = cudaMalloc(&p.ws, p.ws_bytes)) != cudaSuccess) return e;
     p.tmap_host = std::aligned_alloc(64, sizeof(CUtensorMap));
     if (!p.tmap_host) return cudaErrorMemoryAllocation;
-    if ((e = make_tmap(p.ws, std::max<int64_t>(rows_total, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
-        cudaSuccess)
+    if (p.bt_unpaired &&
+        (e = make_tmap(p.ws, std::max<int64_t>(rows_total, 1), static_cast<CUtensorMap *>(p.tmap_host))) !=
+            cudaSuccess)
         return e;
     if (p.npair > 0) {
         const size_t slice = p.bp_b_bytes + p.bp_part_bytes + p.bp_dc_bytes;
@@ -3372,6 +3382,7 @@ static cudaError_t batched_pair_calls(Plan &p, const void *surv, const void *ref
 cudaError_t launch_ternary_batched(Plan &p, const void *surv, const void *ref, void *out, cudaStream_t s,
                                    int *launches) {
     if (p.npair > 0 && p.tune_pair != 1) return batched_pair_calls(p, surv, ref, out, s, launches);
+    if (!p.bt_unpaired) return cudaErrorNotSupported;  // its operand was not kept (see the plan's set-up)
     const BatchedLayout BL = batched_layout(p.ncpi, p.nwork);
     unsigned char *wd = reinterpret_cast<unsigned char *>(p.work_dev);
     const Problem *probs = reinterpret_cast<const Problem *>(wd + BL.probs);

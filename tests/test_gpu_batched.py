@@ -193,3 +193,28 @@ def test_full_256_cpi_batch_sampled(api, cpi256, form, prec):
             want = oracle.caf_cells(sc.s_surv, sc.s_ref, lags, bins, z32=True)
             peak = abs(oracle.caf_cells(sc.s_surv, sc.s_ref, [0], [0], z32=True)[0])
             assert np.max(np.abs(got[idx] - want)) / peak < TOL, c
+
+
+def test_batched_unpaired_operand_kept_only_when_modest(api, cpi256):
+    """A paired tensor-core batch keeps the whole batch's unpaired operand
+    beside its two paired slices only while it is at most 4 GiB: the 256-CPI
+    workload's (41 GB) is not kept, so key 6 = 1 is refused, and the plan
+    stays usable with the paired calls."""
+    from paper_1402_0532_gb300 import _lib as L
+    surv, ref, cpis, total = pack(cpi256[:4])
+    small = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    small.set_tuning(6, 1)
+    out = torch.zeros(total, dtype=torch.complex64, device="cuda")
+    small(dev(surv), dev(ref), out)  # small batch: the unpaired operand is kept
+    small.query_error()
+    surv, ref, cpis, total = pack(cpi256)
+    bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+    assert bp.nbytes() < 4 << 30
+    out = torch.zeros(total, dtype=torch.complex64, device="cuda")
+    bp.set_tuning(6, 1)
+    with pytest.raises(L.NdftError) as ex:
+        bp(dev(surv), dev(ref), out)
+    assert ex.value.status == L.E_UNSUPPORTED
+    bp.set_tuning(6, 0)
+    bp(dev(surv), dev(ref), out)
+    bp.query_error()
