@@ -177,6 +177,10 @@ __global__ void __launch_bounds__(256)
     const bool circ = flags & NDFT_F_CIRCULAR_LAG, noconj = flags & NDFT_F_NO_CONJ_REF;
     float2 gs = make_float2(0.f, 0.f), gr = make_float2(0.f, 0.f);
     if (t < N) {
+        // branch-free so that the unrolled iterations' loads are all in flight
+        // together: a pair outside the signals reads index 0 and weighs its
+        // term by 0 (adding an exact zero never changes these sums, which
+        // start at +0 and so never hold -0)
 #pragma unroll 4
         for (int a = w; a < nc; a += 8) {
             const int64_t l = (int64_t)lag_first + a;
@@ -186,18 +190,18 @@ __global__ void __launch_bounds__(256)
                     j %= N;
                     if (j < 0) j += N;
                 }
-                if (j >= 0 && j < N) {
-                    float2 g = g_at<PLANAR>(G, split_stride, N, a, t, 0);
-                    for (int sp = 1; sp < nsplit; ++sp) {
-                        const float2 h = g_at<PLANAR>(G, split_stride, N, a, t, sp);
-                        g.x += h.x;
-                        g.y += h.y;
-                    }
-                    const float2 r = __ldg(&s_ref[j]);
-                    const float cr = sgnf(r.x), ci = noconj ? sgnf(r.y) : -sgnf(r.y);  // sigma(c)
-                    gs.x += cr * g.x + ci * g.y;  // conj(sigma(c)) G
-                    gs.y += cr * g.y - ci * g.x;
+                const bool in = j >= 0 && j < N;
+                float2 g = g_at<PLANAR>(G, split_stride, N, a, t, 0);
+                for (int sp = 1; sp < nsplit; ++sp) {
+                    const float2 h = g_at<PLANAR>(G, split_stride, N, a, t, sp);
+                    g.x += h.x;
+                    g.y += h.y;
                 }
+                const float2 r = __ldg(&s_ref[in ? j : 0]);
+                const float cr = in ? sgnf(r.x) : 0.f;
+                const float ci = in ? (noconj ? sgnf(r.y) : -sgnf(r.y)) : 0.f;  // sigma(c)
+                gs.x += cr * g.x + ci * g.y;  // conj(sigma(c)) G
+                gs.y += cr * g.y - ci * g.x;
             }
             if (REF) {
                 int64_t i = t + l;  // the s_surv sample that meets s_ref[t] at lag l
@@ -205,19 +209,20 @@ __global__ void __launch_bounds__(256)
                     i %= N;
                     if (i < 0) i += N;
                 }
-                if (i >= 0 && i < N) {
-                    float2 g = g_at<PLANAR>(G, split_stride, N, a, i, 0);
-                    for (int sp = 1; sp < nsplit; ++sp) {
-                        const float2 h = g_at<PLANAR>(G, split_stride, N, a, i, sp);
-                        g.x += h.x;
-                        g.y += h.y;
-                    }
-                    const float2 sg = sigma2(__ldg(&s_surv[i]));
-                    const float dr = sg.x * g.x + sg.y * g.y;  // conj(sigma(s)) G = dL/dc
-                    const float di = sg.x * g.y - sg.y * g.x;
-                    gr.x += dr;
-                    gr.y += noconj ? di : -di;  // c = conj(s_ref): conjugate back
+                const bool in = i >= 0 && i < N;
+                const int64_t ic = in ? i : 0;
+                float2 g = g_at<PLANAR>(G, split_stride, N, a, ic, 0);
+                for (int sp = 1; sp < nsplit; ++sp) {
+                    const float2 h = g_at<PLANAR>(G, split_stride, N, a, ic, sp);
+                    g.x += h.x;
+                    g.y += h.y;
                 }
+                const float2 sv = __ldg(&s_surv[ic]);
+                const float2 sg = in ? sigma2(sv) : make_float2(0.f, 0.f);
+                const float dr = sg.x * g.x + sg.y * g.y;  // conj(sigma(s)) G = dL/dc
+                const float di = sg.x * g.y - sg.y * g.x;
+                gr.x += dr;
+                gr.y += noconj ? di : -di;  // c = conj(s_ref): conjugate back
             }
         }
     }
