@@ -177,52 +177,69 @@ __global__ void __launch_bounds__(256)
     const bool circ = flags & NDFT_F_CIRCULAR_LAG, noconj = flags & NDFT_F_NO_CONJ_REF;
     float2 gs = make_float2(0.f, 0.f), gr = make_float2(0.f, 0.f);
     if (t < N) {
-        // branch-free so that the unrolled iterations' loads are all in flight
-        // together: a pair outside the signals reads index 0 and weighs its
-        // term by 0 (adding an exact zero never changes these sums, which
-        // start at +0 and so never hold -0)
-#pragma unroll 4
-        for (int a = w; a < nc; a += 8) {
-            const int64_t l = (int64_t)lag_first + a;
-            if (SURV) {
-                int64_t j = t - l;  // the s_ref sample that meets s_surv[t] at lag l
+        // U lags at a time: every load of the group is issued before any of
+        // its terms is formed (the kernel is bound by load latency); a pair
+        // outside the signals reads index 0 and weighs its term by 0 (adding
+        // an exact zero never changes these sums, which start at +0 and so
+        // never hold -0)
+        constexpr int U = 4;
+        for (int a0 = w; a0 < nc; a0 += 8 * U) {
+            float2 gsv[U], grv[U], rv[U], sv[U];
+            bool ins[U], inr[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int a = a0 + 8 * u;
+                const bool live = a < nc;
+                const int ac = live ? a : w;
+                const int64_t l = (int64_t)lag_first + ac;
+                int64_t j = t - l, i = t + l;  // the s_ref / s_surv samples met at lag l
                 if (circ) {
                     j %= N;
                     if (j < 0) j += N;
-                }
-                const bool in = j >= 0 && j < N;
-                float2 g = g_at<PLANAR>(G, split_stride, N, a, t, 0);
-                for (int sp = 1; sp < nsplit; ++sp) {
-                    const float2 h = g_at<PLANAR>(G, split_stride, N, a, t, sp);
-                    g.x += h.x;
-                    g.y += h.y;
-                }
-                const float2 r = __ldg(&s_ref[in ? j : 0]);
-                const float cr = in ? sgnf(r.x) : 0.f;
-                const float ci = in ? (noconj ? sgnf(r.y) : -sgnf(r.y)) : 0.f;  // sigma(c)
-                gs.x += cr * g.x + ci * g.y;  // conj(sigma(c)) G
-                gs.y += cr * g.y - ci * g.x;
-            }
-            if (REF) {
-                int64_t i = t + l;  // the s_surv sample that meets s_ref[t] at lag l
-                if (circ) {
                     i %= N;
                     if (i < 0) i += N;
                 }
-                const bool in = i >= 0 && i < N;
-                const int64_t ic = in ? i : 0;
-                float2 g = g_at<PLANAR>(G, split_stride, N, a, ic, 0);
-                for (int sp = 1; sp < nsplit; ++sp) {
-                    const float2 h = g_at<PLANAR>(G, split_stride, N, a, ic, sp);
-                    g.x += h.x;
-                    g.y += h.y;
+                ins[u] = live && j >= 0 && j < N;
+                inr[u] = live && i >= 0 && i < N;
+                const int64_t ic = inr[u] ? i : 0;
+                if (SURV) {
+                    float2 g = g_at<PLANAR>(G, split_stride, N, ac, t, 0);
+                    for (int sp = 1; sp < nsplit; ++sp) {
+                        const float2 h = g_at<PLANAR>(G, split_stride, N, ac, t, sp);
+                        g.x += h.x;
+                        g.y += h.y;
+                    }
+                    gsv[u] = g;
+                    rv[u] = __ldg(&s_ref[ins[u] ? j : 0]);
                 }
-                const float2 sv = __ldg(&s_surv[ic]);
-                const float2 sg = in ? sigma2(sv) : make_float2(0.f, 0.f);
-                const float dr = sg.x * g.x + sg.y * g.y;  // conj(sigma(s)) G = dL/dc
-                const float di = sg.x * g.y - sg.y * g.x;
-                gr.x += dr;
-                gr.y += noconj ? di : -di;  // c = conj(s_ref): conjugate back
+                if (REF) {
+                    float2 g = g_at<PLANAR>(G, split_stride, N, ac, ic, 0);
+                    for (int sp = 1; sp < nsplit; ++sp) {
+                        const float2 h = g_at<PLANAR>(G, split_stride, N, ac, ic, sp);
+                        g.x += h.x;
+                        g.y += h.y;
+                    }
+                    grv[u] = g;
+                    sv[u] = __ldg(&s_surv[ic]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (SURV) {
+                    const float2 g = gsv[u], r = rv[u];
+                    const float cr = ins[u] ? sgnf(r.x) : 0.f;
+                    const float ci = ins[u] ? (noconj ? sgnf(r.y) : -sgnf(r.y)) : 0.f;  // sigma(c)
+                    gs.x += cr * g.x + ci * g.y;  // conj(sigma(c)) G
+                    gs.y += cr * g.y - ci * g.x;
+                }
+                if (REF) {
+                    const float2 g = grv[u];
+                    const float2 sg = inr[u] ? sigma2(sv[u]) : make_float2(0.f, 0.f);
+                    const float dr = sg.x * g.x + sg.y * g.y;  // conj(sigma(s)) G = dL/dc
+                    const float di = sg.x * g.y - sg.y * g.x;
+                    gr.x += dr;
+                    gr.y += noconj ? di : -di;  // c = conj(s_ref): conjugate back
+                }
             }
         }
     }
