@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(256)
                 if (l < nlags && i < N) part[(int64_t)l * N + i] = acc[q][j];
             }
         }
-        return;
-    }
+    } else {
     // multiply by conj(sigma(c_l[i])) and fold this thread's 4 lags
     float2 fold[4];
 #pragma unroll
@@ -142,6 +141,7 @@ __global__ void __launch_bounds__(256)
         }
         const int i = i0 + tid;
         if (i < N) part[(int64_t)blockIdx.y * N + i] = t;
+    }
     }
 }
 

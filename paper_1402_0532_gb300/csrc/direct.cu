@@ -78,7 +78,6 @@ struct PrecF32 {
         acc.y = __fmaf_rn(ws.y, __fmaf_rn(vs.x, wm.y, vv.x), acc.y);
         acc.y = __fmaf_rn(ws.x, __fmaf_rn(vs.y, wm.x, vv.y), acc.y);
     }
-    __device__ static float2 out(const Acc &a) { return a; }
     using Out = float2;
 };
 
