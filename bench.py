@@ -62,15 +62,60 @@ def parse():
     ap.add_argument("--parts", type=int, default=-1,
                     help="tensor-core column parts (tuning key 5: 1 one part, the default; 0 two parts); "
                          "implies --no-tune")
-    ap.add_argument("--profile-form", default="ternary", choices=["ternary", "direct", "direct-q14", "nfft", "adjoint"],
+    ap.add_argument("--profile-form", default="ternary",
+                    choices=["ternary", "direct", "direct-q14", "nfft", "adjoint", "batched"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
 
 
+def cpi_batch_arrays(scenes):
+    """The 256-CPI workload laid out for a batched plan: the CPIs' signals one
+    after another (each padded to a multiple of 4 samples), their surfaces one
+    after another.  Returns (surv, ref, Q1.14 surv, Q1.14 ref, cpis, cells, units)."""
+    import numpy as np
+    scs = scenes.cpi_batch()
+    surv, ref, qsurv, qref, cpis, oo, so = [], [], [], [], [], 0, 0
+    for sc in scs:
+        pad = (-sc.N) % 4
+        cpis.append(dict(off_surv=so, off_ref=so, off_out=oo, n=sc.N, lag0=0, nlags=sc.nlags, p0=sc.p0,
+                         nbins=sc.nbins))
+        surv += [sc.s_surv, np.zeros(pad, np.complex64)]
+        ref += [sc.s_ref, np.zeros(pad, np.complex64)]
+        qsurv += [scenes.quantize_q14(sc.s_surv, 0.25), np.zeros((pad, 2), np.int16)]
+        qref += [scenes.quantize_q14(sc.s_ref, 0.25), np.zeros((pad, 2), np.int16)]
+        so += sc.N + pad
+        oo += sc.nlags * sc.nbins
+    units = sum(c["nlags"] * c["nbins"] * c["n"] for c in cpis)
+    return (np.concatenate(surv), np.concatenate(ref), np.concatenate(qsurv), np.concatenate(qref), cpis, oo,
+            units)
+
+
 def profile_other(args, api, scenes, dev):
-    """--profile with the direct form (the CAF surface of the workload) or the NFFT
-    (65536 vectors of 1024 points): K timed steps, one JSON line."""
+    """--profile with the direct form (the CAF surface of the workload), the NFFT
+    (65536 vectors of 1024 points), the adjoint or the 256-CPI tensor-core batch:
+    K timed steps, one JSON line."""
     import torch
+    if args.profile_form == "batched":
+        # the 256-CPI workload on the tensor cores, eager calls (the launch list of
+        # its per-CPI packing, contraction and fold)
+        surv, ref, _, _, cpis, oo, units = cpi_batch_arrays(scenes)
+        ds, dr = torch.from_numpy(surv).to(dev), torch.from_numpy(ref).to(dev)
+        bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
+        out = torch.empty(oo, dtype=torch.complex64, device=dev)
+        for _ in range(max(3, args.warmup)):
+            bp(ds, dr, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            bp(ds, dr, out)
+        e1.record()
+        torch.cuda.synchronize()
+        bp.query_error()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        print(json.dumps({"mode": "profile", "form": "batched", "workload": "256 CPIs, tensor cores, eager",
+                          "steps": args.steps, "batch_ms": ms, "cells_per_s": oo / (ms / 1e3)}), flush=True)
+        return
     if args.profile_form == "direct":
         scene = scenes.radar_scene(N=N)
         ss = torch.from_numpy(scene.s_surv).to(dev)
@@ -189,21 +234,9 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
         out[f"ndft_64_x4096_{form}"] = {"ms": ms, "vectors_per_s": 4096 / (ms / 1e3)}
     # 256 CPIs: the tensor-core form as one captured CUDA graph (a conjugate-paired
     # call per CPI), the plain form in fp32 and Q1.14 (eager, one run)
-    scs = scenes.cpi_batch()
-    surv, ref, qsurv, qref, cpis, oo, so = [], [], [], [], [], 0, 0
-    for sc in scs:
-        pad = (-sc.N) % 4
-        cpis.append(dict(off_surv=so, off_ref=so, off_out=oo, n=sc.N, lag0=0, nlags=sc.nlags, p0=sc.p0,
-                         nbins=sc.nbins))
-        surv += [sc.s_surv, np.zeros(pad, np.complex64)]
-        ref += [sc.s_ref, np.zeros(pad, np.complex64)]
-        qsurv += [scenes.quantize_q14(sc.s_surv, 0.25), np.zeros((pad, 2), np.int16)]
-        qref += [scenes.quantize_q14(sc.s_ref, 0.25), np.zeros((pad, 2), np.int16)]
-        so += sc.N + pad
-        oo += sc.nlags * sc.nbins
-    units = sum(c["nlags"] * c["nbins"] * c["n"] for c in cpis)
-    ds = torch.from_numpy(np.concatenate(surv)).to(dev)
-    dr = torch.from_numpy(np.concatenate(ref)).to(dev)
+    surv, ref, qsurv, qref, cpis, oo, units = cpi_batch_arrays(scenes)
+    ds = torch.from_numpy(surv).to(dev)
+    dr = torch.from_numpy(ref).to(dev)
     bp = api.BatchedPlan(cpis, form="ternary", prec="bf16x2")
     A = torch.empty(oo, dtype=torch.complex64, device=dev)
     tuned_b = autotune.tune_batched(bp, ds, dr, A) if tune else {}
@@ -224,8 +257,8 @@ def other_workloads(api, scenes, dev, hbm_peak_gbs, tune=True):
     for prec in ("fp32", "q14"):
         q = prec == "q14"
         bq = api.BatchedPlan(cpis, form="direct", prec=prec)
-        xs = torch.from_numpy(np.concatenate(qsurv if q else surv)).to(dev)
-        xr = torch.from_numpy(np.concatenate(qref if q else ref)).to(dev)
+        xs = torch.from_numpy(qsurv if q else surv).to(dev)
+        xr = torch.from_numpy(qref if q else ref).to(dev)
         Aq = torch.empty((oo, 2) if q else (oo,), dtype=torch.int32 if q else torch.complex64, device=dev)
         ms = _time_ms(lambda: bq(xs, xr, Aq), 1)
         out[f"caf_256_cpis_direct_{prec}"] = {"ms": ms, "cells_per_s": oo / (ms / 1e3),
