@@ -205,6 +205,27 @@ def test_identity_decomposition(oracle):
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * N)
 
 
+def test_conjugate_pairing_identity(oracle):
+    """Bins +c and -c from one pair of real contractions (Eq. 8 with
+    W^(-ci) = conj W^(ci) and the odd sign cases of Eq. 2): with F = W^(ci),
+    U = sgn(Re F) v + Re F sigma(v) and V = sgn(Im F) v + Im F sigma(v)
+    (real matrices times the complex v), X[+c] = U + jV and X[-c] = U - jV;
+    the tensor-core form computes exactly these four real products."""
+    rng = np.random.default_rng(16)
+    for N in (7, 16, 45, 64):
+        v = scenes.cn(rng, (3, N))
+        v[:, ::4] = v[:, ::4].real  # exact zeros in the imaginary part
+        F = _tw(N)
+        sv = _sig(v)
+        X = oracle.ndft(v)
+        for c in range(1, N // 2 + 1):
+            Fr, Fi = F[c].real, F[c].imag
+            U = v @ np.sign(Fr) + sv @ Fr
+            V = v @ np.sign(Fi) + sv @ Fi
+            np.testing.assert_allclose(X[:, c], U + 1j * V, rtol=0, atol=1e-11 * N)
+            np.testing.assert_allclose(X[:, (N - c) % N], U - 1j * V, rtol=0, atol=1e-11 * N)
+
+
 def test_ndft_invariants(oracle):
     rng = np.random.default_rng(14)
     N = 40
