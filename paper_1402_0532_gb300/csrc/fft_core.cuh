@@ -286,6 +286,46 @@ __device__ __forceinline__ int swz(int p) { return p ^ ((p >> 4) & 15) ^ ((p >> 
 
 __device__ __forceinline__ int rev3(int j) { return ((j & 1) << 2) | (j & 2) | ((j >> 2) & 1); }
 
+template <int LOGN>
+struct RegCfg {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int V = N >= 4096 ? 1 : 4096 / N;  // sub-vectors per block
+    static constexpr int threads = V * (N / 8);          // 512
+    static constexpr size_t smem = (size_t)N * sizeof(float4) + (size_t)V * N * sizeof(float2);
+};
+
+// Barrier over the N/8 threads of the calling thread's sub-vector.  Each
+// sub-vector exchanges through a shared-memory region of its own, so the
+// sub-vectors of a block need not wait for one another: __syncwarp when a
+// sub-vector lies within one warp (N <= 256), else named barrier 1 + v over
+// its warps (V <= 8 of them there; the ids are immediates so that the
+// kernel reserves only the barriers it uses), the whole block when V = 1.
+template <int ID, int TPV>
+__device__ __forceinline__ void named_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(TPV) : "memory");
+}
+template <int LOGN>
+__device__ __forceinline__ void vec_sync() {
+    constexpr int tpv = (1 << LOGN) / 8, V = RegCfg<LOGN>::V;
+    static_assert(V == 1 || tpv <= 32 || V <= 8, "one named barrier per sub-vector");
+    if constexpr (V == 1) {
+        __syncthreads();
+    } else if constexpr (tpv <= 32) {
+        __syncwarp();
+    } else {
+        switch (threadIdx.x / tpv) {  // uniform over each sub-vector's threads
+            case 0: named_sync<1, tpv>(); break;
+            case 1: named_sync<2, tpv>(); break;
+            case 2: if constexpr (V > 2) named_sync<3, tpv>(); break;
+            case 3: if constexpr (V > 3) named_sync<4, tpv>(); break;
+            case 4: if constexpr (V > 4) named_sync<5, tpv>(); break;
+            case 5: if constexpr (V > 5) named_sync<6, tpv>(); break;
+            case 6: if constexpr (V > 6) named_sync<7, tpv>(); break;
+            default: if constexpr (V > 7) named_sync<8, tpv>(); break;
+        }
+    }
+}
+
 // Stages b = B_HI - 1 .. B_LO (DIF, descending) or B_LO .. B_HI - 1 (DIT) on
 // the thread's 8 points r[j] (positions base | j << W); tlow = base mod 2^W.
 // tab holds the per-stage tables, stage b's 2^b entries starting at 2^b - 1.
@@ -347,7 +387,7 @@ __device__ __forceinline__ void dit_passes(float2 (&r)[8], float2 *s, int t, con
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
-            __syncthreads();  // pass results visible before the next pass reads them
+            vec_sync<LOGN>();  // pass results visible before the next pass reads them
             dit_passes<Op, LOGN, SB, B0 + 3>(r, s, t, tab, src, dst, q, live);
         }
     }
@@ -383,19 +423,11 @@ __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, con
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
-            __syncthreads();  // pass results visible before the next pass reads them
+            vec_sync<LOGN>();  // pass results visible before the next pass reads them
             dif_passes<Op, LOGN, SB, W>(r, s, t, tab, src, dst, q, live);
         }
     }
 }
-
-template <int LOGN>
-struct RegCfg {
-    static constexpr int N = 1 << LOGN;
-    static constexpr int V = N >= 4096 ? 1 : 4096 / N;  // sub-vectors per block
-    static constexpr int threads = V * (N / 8);          // 512
-    static constexpr size_t smem = (size_t)N * sizeof(float4) + (size_t)V * N * sizeof(float2);
-};
 
 template <class Op, bool DIF, int LOGN, int SB, class Src, class Dst>
 __global__ void __launch_bounds__(512, 2) k_fft_reg(Src src, Dst dst, const float2 *__restrict__ tw, int64_t nsub) {
@@ -411,9 +443,10 @@ __global__ void __launch_bounds__(512, 2) k_fft_reg(Src src, Dst dst, const floa
         tab[e] = Op::prep(__ldg(&tw[(k << (LOGN - 1 - b)) << SB]));
     }
     float2 r[8];
+    __syncthreads();  // tables written
     for (int64_t g = blockIdx.x; g * V < nsub; g += gridDim.x) {
         const int64_t q = g * V + v;
-        __syncthreads();  // tables written; previous group's shared reads done
+        vec_sync<LOGN>();  // the sub-vector's reads of the previous group done
         if constexpr (DIF) dif_passes<Op, LOGN, SB, LOGN>(r, s, t, tab, src, dst, q, q < nsub);
         else dit_passes<Op, LOGN, SB, 0>(r, s, t, tab, src, dst, q, q < nsub);
     }
