@@ -261,7 +261,10 @@ __global__ void k_fft_tiny(Src src, Dst dst, const float2 *__restrict__ tw, int 
 // so every stage whose butterfly distance 2^b lies in that window pairs two of
 // the thread's own points.  DIT passes take windows upwards (W = 0, 3, ...,
 // the last one clamped to LOGN - 3 and skipping stages already done), DIF
-// passes downwards (W = LOGN - 3, LOGN - 6, ..., the last clamped to 0).
+// passes downwards (the first one with W = LOGN - 3 taking only the top
+// LOGN mod 3 stages when that is not 0, then W = ..., 3, 0), so that in both
+// orders the stages b < 3 run in the W = 0 pass, where every twiddle index is
+// a compile-time constant.
 //
 // Sub-vectors: with SB > 0 the kernel runs the 2^LOGN-point part of an NFFT of
 // length 2^(LOGN+SB).  DIT: sub-vector q = o 2^SB + c is the transform of
@@ -291,7 +294,12 @@ struct RegCfg {
     static constexpr int N = 1 << LOGN;
     static constexpr int V = N >= 4096 ? 1 : 4096 / N;  // sub-vectors per block
     static constexpr int threads = V * (N / 8);          // 512
-    static constexpr size_t smem = (size_t)N * sizeof(float4) + (size_t)V * N * sizeof(float2);
+    // exchange regions: two per sub-vector, used by alternate groups, where a
+    // sub-vector's barrier is a named one over several warps and two blocks
+    // per SM still fit (512 <= N <= 2048), else one (the loop-top barrier is
+    // a __syncwarp for N <= 256, and measured cheaper than a second region)
+    static constexpr int NB = N >= 512 && N <= 2048 ? 2 : 1;
+    static constexpr size_t smem = (size_t)N * sizeof(float4) + (size_t)NB * V * N * sizeof(float2);
 };
 
 // Barrier over the N/8 threads of the calling thread's sub-vector.  Each
@@ -393,14 +401,16 @@ __device__ __forceinline__ void dit_passes(float2 (&r)[8], float2 *s, int t, con
     }
 }
 
-// DIF: pass ending below stage bit B1 (stages B1 - 1 .. max(B1 - 3, 0)).
+// DIF: pass ending below stage bit B1 (stages B1 - 1 .. LO).
 template <class Op, int LOGN, int SB, int B1, class Src, class Dst>
 __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, const float4 *__restrict__ tab,
                                            const Src &src, const Dst &dst, int64_t q, bool live) {
     if constexpr (B1 > 0) {
         constexpr int N = 1 << LOGN;
+        constexpr bool first = B1 == LOGN;
         constexpr int W = B1 >= 3 ? B1 - 3 : 0;  // window of 3 index bits
-        constexpr bool first = B1 == LOGN, last = W == 0;
+        constexpr int LO = first && LOGN % 3 != 0 ? LOGN - LOGN % 3 : W;
+        constexpr bool last = LO == 0;
         // positions base | j << W; the last pass remaps threads (see above)
         const int base = last ? 8 * (int)bitrev((uint32_t)t, LOGN - 3)
                               : (t & ((1 << W) - 1)) | ((t >> W) << (W + 3));
@@ -411,7 +421,7 @@ __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, con
 #pragma unroll
             for (int j = 0; j < 8; ++j) r[j] = s[swz(base) ^ swz(j << W)];
         }
-        reg_stages<Op, true, W, W, B1>(r, base & ((1 << W) - 1), tab);
+        reg_stages<Op, true, W, LO, B1>(r, base & ((1 << W) - 1), tab);
         if constexpr (last) {
             // position 8 rev(t) + j holds bin rev(8 rev(t) + j) = rev3(j) N/8 + t
             if (live) {
@@ -424,7 +434,7 @@ __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, con
 #pragma unroll
             for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
             vec_sync<LOGN>();  // pass results visible before the next pass reads them
-            dif_passes<Op, LOGN, SB, W>(r, s, t, tab, src, dst, q, live);
+            dif_passes<Op, LOGN, SB, LO>(r, s, t, tab, src, dst, q, live);
         }
     }
 }
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(512, 2) k_fft_reg(Src src, Dst dst, const floa
     extern __shared__ __align__(16) float4 smem_fft[];
     float4 *tab = smem_fft;  // N - 1 entries used
     const int v = threadIdx.x / tpv, t = threadIdx.x - v * tpv;
-    float2 *s = reinterpret_cast<float2 *>(smem_fft + N) + v * N;
+    float2 *const s0 = reinterpret_cast<float2 *>(smem_fft + N) + v * N;
     // per-stage tables: entry 2^b - 1 + k holds W_2^(b+1)^k = tw[k 2^(LOGN+SB-1-b)]
     for (int e = threadIdx.x; e < N - 1; e += blockDim.x) {
         const int b = 31 - __clz(e + 1), k = e + 1 - (1 << b);
@@ -444,9 +454,16 @@ __global__ void __launch_bounds__(512, 2) k_fft_reg(Src src, Dst dst, const floa
     }
     float2 r[8];
     __syncthreads();  // tables written
-    for (int64_t g = blockIdx.x; g * V < nsub; g += gridDim.x) {
+    int it = 0;
+    for (int64_t g = blockIdx.x; g * V < nsub; g += gridDim.x, ++it) {
         const int64_t q = g * V + v;
-        vec_sync<LOGN>();  // the sub-vector's reads of the previous group done
+        // With two regions, group it writes the one that group it - 2 read,
+        // and every thread of the sub-vector has passed group it - 1's pass
+        // barriers since (LOGN > 3: at least two passes); with one region the
+        // sub-vector waits here for its reads of the previous group.
+        float2 *s = s0;
+        if constexpr (C::NB == 2) s += (it & 1) * V * N;
+        else vec_sync<LOGN>();
         if constexpr (DIF) dif_passes<Op, LOGN, SB, LOGN>(r, s, t, tab, src, dst, q, q < nsub);
         else dit_passes<Op, LOGN, SB, 0>(r, s, t, tab, src, dst, q, q < nsub);
     }
