@@ -136,15 +136,10 @@ __device__ __forceinline__ float sgnf(float v) {
     return __fsub_rn(g, l);
 }
 
-// sgn(v) in two instructions: 1.0f where v != 0 (set.ne), with v's sign bit
-// copied in; a zero v gives a zero of v's sign.  cox_ready only multiplies it
-// by a twiddle magnitude and adds v back, and its outer fmas' +0 addends turn
-// every zero into +0, so the result has the same bits as with sgnf.
-__device__ __forceinline__ float sgn_mul(float v) {
-    float nz;
-    asm("set.ne.f32.f32 %0, %1, 0f00000000;" : "=f"(nz) : "f"(v));
-    return __uint_as_float(__float_as_uint(nz) | (__float_as_uint(v) & 0x80000000u));
-}
+// (sgn_mul, the two-instruction sgn of a data operand, is in internal.cuh:
+// cox_ready only multiplies it by a twiddle magnitude and adds the operand
+// back, and its outer fmas' +0 addends turn every zero into +0, so the result
+// has the same bits as with sgnf.)
 
 // Eq. 6 with the twiddle in "ready" form (|Re|, |Im|, sgn Re, sgn Im).  Each
 // real a (x) b = sgn(a) sgn(b) (|a| + |b|) starts as the inner
