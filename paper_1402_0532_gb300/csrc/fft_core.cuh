@@ -95,7 +95,49 @@ struct SrcLagComb {
         return cox_f32(ssT[(n & cmask) * ld + (n >> sb)], ref);
     }
     SrcLagComb shift(int64_t a) const { return SrcLagComb{ssT, srT, N, (int)(lag0 + a), flags, sb}; }
+
+    // One vector's elements n = rc + m 2^sb, m < N / 2^sb, as a row over m:
+    // both combs and the reference offset are fixed per vector.  With
+    // d = rc - (lag0 + v), the reference element n - (lag0 + v) = d + m 2^sb
+    // lies on comb d mod 2^sb at index floor(d / 2^sb) + m, and is in range
+    // iff 0 <= floor(d / 2^sb) + m < N / 2^sb (circular lags: d taken mod N
+    // first and the index wrapped mod N / 2^sb).  Same values as operator().
+    struct Row {
+        const float2 *s, *r;  // s_surv's comb rc; the reference's comb for this lag
+        int off, ld;          // reference index m + off; comb length
+        bool circ, conj;
+        __device__ float2 operator()(int m) const {
+            float2 ref = make_float2(0.f, 0.f);
+            const int k = m + off;
+            if (circ || (unsigned)k < (unsigned)ld) {
+                ref = r[k & (ld - 1)];
+                if (conj) ref.y = -ref.y;
+            }
+            return cox_f32(s[m], ref);
+        }
+    };
+    __device__ Row row(int64_t v, int rc) const {
+        const int ld = N >> sb;
+        const bool circ = (flags & NDFT_F_CIRCULAR_LAG) != 0;
+        int64_t d = (int64_t)rc - ((int64_t)lag0 + v);
+        if (circ) {
+            d %= N;
+            if (d < 0) d += N;
+        }
+        const int64_t q = d >> sb;  // floor(d / 2^sb)
+        // beyond +-ld no m < ld reaches the reference (non-circular), so the
+        // clamp keeps the index in int32 without changing any test
+        const int off = (int)(q < -ld ? -ld : (q > ld ? ld : q));
+        return Row{ssT + (int64_t)rc * ld, srT + (d & ((1 << sb) - 1)) * ld, off, ld, circ,
+                   !(flags & NDFT_F_NO_CONJ_REF)};
+    }
 };
+
+// Sources that offer a per-vector row over the first DIT kernel's comb.
+template <class S>
+struct HasCombRow : std::false_type {};
+template <>
+struct HasCombRow<SrcLagComb> : std::true_type {};
 
 __global__ void k_comb_copy(const float2 *__restrict__ ss, const float2 *__restrict__ sr, float2 *__restrict__ ssT,
                             float2 *__restrict__ srT, int N, int sb) {
@@ -373,9 +415,15 @@ __device__ __forceinline__ void dit_passes(float2 (&r)[8], float2 *s, int t, con
             base = 8 * (int)bitrev((uint32_t)t, LOGN - 3);
             const int64_t o = q >> SB;
             const int rc = (int)bitrev((uint32_t)(q & ((1 << SB) - 1)), SB);
+            if constexpr (SB > 0 && HasCombRow<Src>::value) {
+                const auto row = src.row(o, rc);  // element rc + m 2^SB at m
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                r[j] = live ? src(o, rc + ((t + rev3(j) * (N / 8)) << SB)) : make_float2(0.f, 0.f);
+                for (int j = 0; j < 8; ++j) r[j] = live ? row(t + rev3(j) * (N / 8)) : make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    r[j] = live ? src(o, rc + ((t + rev3(j) * (N / 8)) << SB)) : make_float2(0.f, 0.f);
+            }
         } else {
             base = (t & ((1 << W) - 1)) | ((t >> W) << (W + 3));
 #pragma unroll

@@ -60,7 +60,10 @@ def test_nfft_form_bins(api, N, batch, p0, nbins):
     (4096, 100, 9, 7, 33, 1), (4096, 4000, 9, 0, 16, 2), (8192, 0, 21, -4096, 8192, 0),
     (16384, 37, 5, -512, 1024, 0), (65536, 0, 3, -512, 1024, 0), (65536, 65530, 9, 0, 64, 2),
     # the pruned tail at its limits: exactly 2^LA bins, and a window that wraps past bin 0
-    (8192, 5, 7, 100, 1024, 0), (16384, -2, 6, -300, 700, 1)])
+    (8192, 5, 7, 100, 1024, 0), (16384, -2, 6, -300, 700, 1),
+    # the two-kernel path's comb rows: lags past -N (exact zeros), negative
+    # circular lags, circular lags without the conjugate
+    (8192, -9000, 4, -64, 128, 0), (8192, -3, 5, -64, 128, 2), (32768, 12345, 4, -512, 1024, 3)])
 def test_nfft_form_caf(api, N, lag0, nlags, p0, nbins, flags):
     sc = scenes.radar_scene(N=N, nlags=max(nlags, 1), nbins=min(N, 64), seed=60 + N % 97)
     nb = nbins or N
@@ -82,6 +85,27 @@ def test_nfft_form_caf_full_size_sampled(api):
     for lag in (0, 1, 37, 63, 64, 120, 127, 128, 301, 555, 1023):
         want = oracle.caf_nfft(sc.s_surv, sc.s_ref, lag, 1, -512, 1024, f32=True)
         assert same_bits(A[lag:lag + 1], want), lag
+
+
+@pytest.mark.parametrize("N", [8192, 65536])
+def test_nfft_form_comb_rows_at_the_int32_limits(api, N):
+    """The two-kernel path forms each vector's lag products from one comb row
+    of each input (the reference offset fixed per lag): windows ending at
+    INT32_MAX or starting at INT32_MIN give an exactly zero surface, and with
+    F_CIRCULAR_LAG the surface of the window reduced modulo N, bit for bit."""
+    nl = 3
+    rng = np.random.default_rng(86)
+    ss = dev(scenes.cn(rng, (N,)).astype(np.complex64))
+    sr = dev(scenes.cn(rng, (N,)).astype(np.complex64))
+    for lag0 in (2**31 - nl, -2**31):
+        p = api.Plan(N, p0=-64, nbins=128, max_lags=nl, form="nfft", prec="fp32")
+        assert torch.count_nonzero(p.caf(ss, sr, lag0, nl)).item() == 0
+        pc = api.Plan(N, p0=-64, nbins=128, max_lags=nl, form="nfft", prec="fp32", flags=api.F_CIRCULAR_LAG)
+        got = pc.caf(ss, sr, lag0, nl).cpu().numpy()
+        ref = pc.caf(ss, sr, lag0 % N, nl).cpu().numpy()  # lag0 % N + nl <= N: no wrap inside
+        pc.query_error()
+        assert same_bits(got, ref)
+        assert np.count_nonzero(got) > 0
 
 
 def test_nfft_form_unsupported(api):
