@@ -88,6 +88,20 @@ def test_nfft_dif_caf(api, N, lag0, nlags, p0, nbins):
     assert same_bits(q.ndft(dev(x)).cpu().numpy(), oracle.nfft_f32(x, dif=True)[:, (p0 + np.arange(nb)) % N])
 
 
+@pytest.mark.parametrize("N,lag0,nlags,p0,nbins,flags", [(8192, -3, 4, -64, 128, 2), (16384, 20000, 3, 0, 64, 3),
+                                                         (8192, -9000, 3, -64, 128, 0), (65536, 65533, 3, -512, 1024, 2)])
+def test_nfft_dif_caf_lag_flags(api, N, lag0, nlags, p0, nbins, flags):
+    """The DIF path's first kernel forms each vector's lag products from a row
+    with the reference offset fixed per lag: circular and unconjugated lags,
+    and lags past +-N (exact zeros), bit for bit."""
+    sc = scenes.radar_scene(N=N, nlags=nlags, nbins=min(N, 64), seed=71 + N % 89)
+    want = oracle.caf_nfft(sc.s_surv, sc.s_ref, lag0, nlags, p0, nbins, flags=flags, f32=True, dif=True)
+    p = api.Plan(N, p0=p0, nbins=nbins, max_lags=nlags, form="nfft", prec="fp32", flags=flags | api.F_NFFT_DIF)
+    got = p.caf(dev(sc.s_surv), dev(sc.s_ref), lag0, nlags).cpu().numpy()
+    p.query_error()
+    assert same_bits(got, want)
+
+
 @pytest.mark.parametrize("N,batch,p0,nbins", [(1, 4, 0, 0), (2, 3, 0, 0), (4, 5, -1, 3), (8, 100, 0, 0),
                                               (1024, 50, -512, 1024), (4096, 7, 3, 100), (8192, 3, 0, 0),
                                               (65536, 2, -512, 1024)])

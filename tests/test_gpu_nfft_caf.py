@@ -87,20 +87,22 @@ def test_nfft_form_caf_full_size_sampled(api):
         assert same_bits(A[lag:lag + 1], want), lag
 
 
-@pytest.mark.parametrize("N", [8192, 65536])
-def test_nfft_form_comb_rows_at_the_int32_limits(api, N):
-    """The two-kernel path forms each vector's lag products from one comb row
-    of each input (the reference offset fixed per lag): windows ending at
-    INT32_MAX or starting at INT32_MIN give an exactly zero surface, and with
-    F_CIRCULAR_LAG the surface of the window reduced modulo N, bit for bit."""
+@pytest.mark.parametrize("N,dif", [(8192, False), (65536, False), (8192, True), (65536, True)])
+def test_nfft_form_lag_rows_at_the_int32_limits(api, N, dif):
+    """The two-kernel paths form each vector's lag products from one row of
+    each input with the reference offset fixed per lag (DIT: one comb row;
+    DIF: the natural row): windows ending at INT32_MAX or starting at
+    INT32_MIN give an exactly zero surface, and with F_CIRCULAR_LAG the
+    surface of the window reduced modulo N, bit for bit."""
     nl = 3
     rng = np.random.default_rng(86)
     ss = dev(scenes.cn(rng, (N,)).astype(np.complex64))
     sr = dev(scenes.cn(rng, (N,)).astype(np.complex64))
+    f = api.F_NFFT_DIF if dif else 0
     for lag0 in (2**31 - nl, -2**31):
-        p = api.Plan(N, p0=-64, nbins=128, max_lags=nl, form="nfft", prec="fp32")
+        p = api.Plan(N, p0=-64, nbins=128, max_lags=nl, form="nfft", prec="fp32", flags=f)
         assert torch.count_nonzero(p.caf(ss, sr, lag0, nl)).item() == 0
-        pc = api.Plan(N, p0=-64, nbins=128, max_lags=nl, form="nfft", prec="fp32", flags=api.F_CIRCULAR_LAG)
+        pc = api.Plan(N, p0=-64, nbins=128, max_lags=nl, form="nfft", prec="fp32", flags=f | api.F_CIRCULAR_LAG)
         got = pc.caf(ss, sr, lag0, nl).cpu().numpy()
         ref = pc.caf(ss, sr, lag0 % N, nl).cpu().numpy()  # lag0 % N + nl <= N: no wrap inside
         pc.query_error()
