@@ -63,7 +63,7 @@ def parse():
                     help="tensor-core column parts (tuning key 5: 1 one part, the default; 0 two parts); "
                          "implies --no-tune")
     ap.add_argument("--profile-form", default="ternary",
-                    choices=["ternary", "direct", "direct-q14", "nfft", "adjoint", "batched"],
+                    choices=["ternary", "direct", "direct-q14", "nfft", "caf-nfft", "adjoint", "batched"],
                     help="with --profile: which kernel's steps to run (profiling only)")
     return ap.parse_args()
 
@@ -91,9 +91,9 @@ def cpi_batch_arrays(scenes):
 
 
 def profile_other(args, api, scenes, dev):
-    """--profile with the direct form (the CAF surface of the workload), the NFFT
-    (65536 vectors of 1024 points), the adjoint or the 256-CPI tensor-core batch:
-    K timed steps, one JSON line."""
+    """--profile with the direct form (the CAF surface of the workload), the
+    NFFT-form CAF on the same surface, the NFFT (65536 vectors of 1024 points),
+    the adjoint or the 256-CPI tensor-core batch: K timed steps, one JSON line."""
     import torch
     if args.profile_form == "batched":
         # the 256-CPI workload on the tensor cores, eager calls (the launch list of
@@ -135,6 +135,18 @@ def profile_other(args, api, scenes, dev):
         step = lambda: plan.caf(ss, sr, 0, NLAGS, out=out)  # noqa: E731
         units = NLAGS * NBINS
         what = f"direct-form CAF in Q1.14, N={N}, {NLAGS} lags x {NBINS} bins"
+    elif args.profile_form == "caf-nfft":
+        # Eq. 12a through the Sec. 3 NFFT on the workload's surface (comb copy,
+        # then per lag chunk the register kernel over the lag products and the
+        # pruned tail)
+        scene = scenes.radar_scene(N=N)
+        ss = torch.from_numpy(scene.s_surv).to(dev)
+        sr = torch.from_numpy(scene.s_ref).to(dev)
+        plan = api.Plan(N, p0=P0, nbins=NBINS, max_lags=NLAGS, form="nfft", prec="fp32", device=dev)
+        out = torch.empty(NLAGS, NBINS, dtype=torch.complex64, device=dev)
+        step = lambda: plan.caf(ss, sr, 0, NLAGS, out=out)  # noqa: E731
+        units = NLAGS * NBINS
+        what = f"NFFT-form CAF, N={N}, {NLAGS} lags x {NBINS} bins"
     elif args.profile_form == "adjoint":
         # both gradients of the workload's surface on the tensor cores (the
         # G-storing adjoint contraction and the fold)
