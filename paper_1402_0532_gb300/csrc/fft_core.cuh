@@ -371,6 +371,38 @@ __device__ __forceinline__ void vec_sync() {
     }
 }
 
+// The barrier between two passes.  A position's writer and reader share
+// their thread index above bit log2 G, with G = 2^W of the reader's window
+// (DIT, after a pass other than the first) or of the writer's (DIF, before a
+// pass other than the last): the exchange then closes over groups of G
+// consecutive threads.  Where such a group is smaller than the sub-vector
+// (G = 64 for 1024 <= N <= 4096: two warps) it may wait on named barrier
+// 8 + g, above the sub-vector barriers 1 .. V (V <= 4 there); otherwise the
+// sub-vector barrier.  Exchanges through the bit-reversed first (DIT) or
+// last (DIF) pass span the sub-vector.  Measured on 2^26 points: N = 1024
+// DIT 0.255 -> 0.250 ms (DIF unchanged), but N = 4096 0.297 -> 0.318 ms and
+// the 4096-point passes of the 65536-point forms slower too, so only
+// N = 1024 takes the group barriers.
+template <int LOGN, int G>
+__device__ __forceinline__ void pass_sync() {
+    constexpr int tpv = (1 << LOGN) / 8, V = RegCfg<LOGN>::V;
+    if constexpr (G >= tpv || LOGN != 10) {
+        vec_sync<LOGN>();
+    } else {
+        static_assert(G == 64 && V <= 7 && RegCfg<LOGN>::threads / G <= 8, "group barriers 8 .. 15");
+        switch (threadIdx.x / G) {  // uniform over each group's threads
+            case 0: named_sync<8, G>(); break;
+            case 1: named_sync<9, G>(); break;
+            case 2: named_sync<10, G>(); break;
+            case 3: named_sync<11, G>(); break;
+            case 4: named_sync<12, G>(); break;
+            case 5: named_sync<13, G>(); break;
+            case 6: named_sync<14, G>(); break;
+            default: named_sync<15, G>(); break;
+        }
+    }
+}
+
 // Stages b = B_HI - 1 .. B_LO (DIF, descending) or B_LO .. B_HI - 1 (DIT) on
 // the thread's 8 points r[j] (positions base | j << W); tlow = base mod 2^W.
 // tab holds the per-stage tables, stage b's 2^b entries starting at 2^b - 1.
@@ -438,7 +470,9 @@ __device__ __forceinline__ void dit_passes(float2 (&r)[8], float2 *s, int t, con
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
-            vec_sync<LOGN>();  // pass results visible before the next pass reads them
+            // pass results visible before the next pass (window WN) reads them
+            constexpr int WN = B0 + 6 <= LOGN ? B0 + 3 : LOGN - 3;
+            pass_sync<LOGN, first ? (1 << (LOGN - 3)) : (1 << WN)>();
             dit_passes<Op, LOGN, SB, B0 + 3>(r, s, t, tab, src, dst, q, live);
         }
     }
@@ -476,7 +510,10 @@ __device__ __forceinline__ void dif_passes(float2 (&r)[8], float2 *s, int t, con
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) s[swz(base) ^ swz(j << W)] = r[j];
-            vec_sync<LOGN>();  // pass results visible before the next pass reads them
+            // pass results visible before the next pass reads them (that pass is
+            // the last, bit-reversed one when its window starts at bit 0)
+            constexpr bool next_last = LO <= 3;
+            pass_sync<LOGN, next_last ? (1 << (LOGN - 3)) : (1 << W)>();
             dif_passes<Op, LOGN, SB, LO>(r, s, t, tab, src, dst, q, live);
         }
     }
